@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of the FR-SG stage on GB300: DOF-stage updates per second.
+
+A "step" is one SSP-RK3 time step (three fused stage launches: z-evaluation, flux,
+Galerkin projection, FR derivative with LLF + Radau correction, SSP combination,
+detector and filter) of the stochastic Burgers workload: 1024 elements, P = 3,
+N = 8, Q = 16 (36,864 DOF), exponential filter switched by the detector, CFL 0.1.
+DOF = elements x solution points x gPC modes x variables; one step is 3 DOF-stages
+per DOF.  Both the plain FP64 form and the FP32 form are measured; the line reports
+the faster form whose error against the FP64 oracle meets its stated bound.
+
+Timing: W untimed steps, then K steps each bracketed by CUDA events on the solver's
+stream, with a 256 MiB memset between timed steps to flush the 129 MB L2 (the state
+is 0.3 MB, so every timed step starts from HBM).  Max over ranks under torchrun
+(N > 1 runs independent replicas: "weak" scaling, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (numpy, one core) on the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2112_05946_gb300 import workloads  # noqa: E402
+
+METRIC = "DOF-stage updates/s"
+UNIT = "DOF-stage/s"
+ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5}     # relative L2 vs the FP64 oracle after the accuracy run
+ACC_STEPS = 50
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="burgers", choices=sorted(workloads.ALL))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_sizes(wl):
+    s = wl["solver"]
+    n1 = s["P"] + 1
+    E = s["nx"] * (s.get("ny", 1) if s.get("dim", 1) == 2 else 1)
+    Np = n1 ** s.get("dim", 1)
+    M = s["N"] + 1
+    S = 1 if s["equation"] != "euler" else (3 if s.get("dim", 1) == 1 else 4)
+    return E, Np, M, S
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracle_ref):
+    E, Np, M, S = workload_sizes(wl)
+    dof = E * Np * M * S
+    s = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
+    x, z = s.nodes()
+    u0 = workloads.nodal_values(wl["ic"], x, z)
+    dx = (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"]
+    dt = wl["cfl"] * dx / wl["lam0"]
+    esz = 8 if precision == "fp64" else 4
+
+    # accuracy run against the FP64 oracle
+    s.set_initial_nodal(u0)
+    s.rk_step(dt, ACC_STEPS, graph=True)
+    s.check()
+    got = s.get_state()
+    err = float(np.linalg.norm(got - oracle_ref) / np.linalg.norm(oracle_ref))
+
+    # throughput: per-step events with an L2 flush between steps
+    s.set_initial_nodal(u0)
+    with torch.cuda.stream(stream):
+        s.rk_step(dt, warmup, graph=True)
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        l0 = s.launch_count()
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record(stream)
+            s.rk_step(dt, 1, graph=True)
+            ends[i].record(stream)
+        stream.synchronize()
+        launches = s.launch_count() - l0
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+        # kernel durations: the three stage launches timed one by one (same flush)
+        kst = min(steps, 200)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kst)]
+        for i in range(kst):
+            flush.zero_()
+            evs[i][0].record(stream)
+            for st in range(3):
+                s.stage(st, dt)
+                evs[i][st + 1].record(stream)
+        stream.synchronize()
+        stage_ms = [[evs[i][st].elapsed_time(evs[i][st + 1]) for st in range(3)] for i in range(kst)]
+
+        # steady state: back-to-back graph replays, state resident in L2 (context only)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.rk_step(dt, steps, graph=True)
+        ev1.record(stream)
+        stream.synchronize()
+        steady_ms = ev0.elapsed_time(ev1) / steps
+    s.check()
+
+    # end to end through the public API with host buffers: pinned host state in, step, state out
+    h_in = torch.empty((E, Np, M, S), dtype=torch.float64, pin_memory=True)
+    h_in.copy_(torch.from_numpy(got))
+    h_out = torch.empty_like(h_in)
+    e2e_steps = min(steps, 200)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(h_in.numpy())
+        s.rk_step(dt, 1, graph=True)
+        s.get_state(h_out.numpy())
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    s.close()
+
+    ms = float(np.mean(step_ms))
+    mean_stage = np.mean(np.array(stage_ms), axis=0)           # ms per stage launch
+    arrays = [2, 3, 3]                                         # state arrays read+written per stage
+    alg_bytes = [a * esz * dof for a in arrays]
+    achieved = sum(alg_bytes) / (sum(mean_stage) * 1e-3) / 1e9  # GB/s over the stage kernels
+    return dict(
+        precision=precision, value=dof * 3 / (ms * 1e-3), ms_per_step=ms, err_vs_oracle=err,
+        err_bound=ERR_BOUND[precision], dof=dof, launches=launches, steady_ms=steady_ms,
+        stage_us=[float(v * 1e3) for v in mean_stage], achieved_gbs=achieved,
+        alg_bytes_per_step=sum(alg_bytes), e2e_value=dof * 3 / e2e_s, e2e_ms=e2e_s * 1e3,
+        h2d=dof * 8, d2h=dof * 8,
+    )
+
+
+def cpu_baseline(wl, seconds):
+    import oracle
+    from oracle import integrate, tables
+    kw = dict(wl["solver"])
+    prob = oracle.Problem(**kw)
+    tabs = prob.tabs()
+    u = integrate.project_initial(prob, wl["ic"])
+    dt = wl["cfl"] * prob.dx / wl["lam0"]
+    E, Np, M, S = workload_sizes(wl)
+    dof = E * Np * M * S
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n < 2:
+        u = integrate.ssp_rk3_step(prob, tabs, u, dt)
+        n += 1
+    t = time.perf_counter() - t0
+    del tables
+    return dict(value=dof * 3 * n / t, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{n} SSP-RK3 steps of the full {wl['name']} workload from t=0 "
+                       f"(numpy FP64 oracle, single thread), {t:.1f} s")
+
+
+def oracle_reference(wl, nsteps):
+    import oracle
+    from oracle import integrate
+    prob = oracle.Problem(**wl["solver"])
+    u = integrate.project_initial(prob, wl["ic"])
+    dt = wl["cfl"] * prob.dx / wl["lam0"]
+    return integrate.run(prob, u, dt, nsteps)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2112_05946_gb300 import build as _b
+    from paper_2112_05946_gb300 import frsg
+    if rank == 0 or not os.path.exists(frsg.LIB_PATH):
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    frsg.load_library()
+    wl = workloads.ALL[args.workload]()
+    ref = oracle_reference(wl, ACC_STEPS)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    forms = {}
+    for prec in ("fp64", "fp32"):
+        forms[prec] = measure_form(torch, frsg, wl, prec, args.steps, args.warmup, stream, flush, ref)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+
+    ok = [f for f in forms.values() if f["err_vs_oracle"] <= f["err_bound"]]
+    chosen = max(ok, key=lambda f: f["value"]) if ok else forms["fp64"]
+    ms = chosen["ms_per_step"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * chosen["dof"] * 3 / (ms * 1e-3)
+
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as f:
+            peaks = json.load(f)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "hbm", "achieved": round(chosen["achieved_gbs"], 2), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(chosen["achieved_gbs"] / hbm_peak, 5), "traffic": None,
+                "kernel": "stage1d_kernel", "peak_source": "measured" if peaks else "fallback",
+                "alg_bytes_per_step": chosen["alg_bytes_per_step"], "stage_us": chosen["stage_us"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cpu_seconds)
+
+    E, Np, M, S = workload_sizes(wl)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if chosen["precision"] == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "elements": E, "P": wl["solver"]["P"], "N": wl["solver"]["N"],
+                   "Q": wl["solver"]["Q"], "S": S, "dof": E * Np * M * S, "filter": "exp+detector",
+                   "l2": "256 MiB memset between timed steps (state 0.3 MB < L2)",
+                   "parallelism": f"replicas x{world}"},
+        "chosen": chosen["precision"],
+        "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "rel_l2_vs_oracle": v["err_vs_oracle"],
+                      "err_bound": v["err_bound"], "steady_ms_per_step": v["steady_ms"],
+                      "stage_us": v["stage_us"]} for k, v in forms.items()},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": chosen["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": chosen["h2d"],
+                "d2h_bytes_per_step": chosen["d2h"], "ms_per_step": chosen["e2e_ms"]},
+        "gpu_launches": chosen["launches"],
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from oracle import integrate
+    wl = workloads.ALL[args.workload]()
+    prob = oracle.Problem(**wl["solver"])
+    tabs = prob.tabs()
+    u = integrate.project_initial(prob, wl["ic"])
+    dt = wl["cfl"] * prob.dx / wl["lam0"]
+    E, Np, M, S = workload_sizes(wl)
+    dof = E * Np * M * S
+    for _ in range(args.warmup):
+        u = integrate.ssp_rk3_step(prob, tabs, u, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = integrate.ssp_rk3_step(prob, tabs, u, dt)
+    t = time.perf_counter() - t0
+    value = dof * 3 * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "elements": E, "P": wl["solver"]["P"], "N": wl["solver"]["N"],
+                   "Q": wl["solver"]["Q"], "S": S, "dof": dof},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed SSP-RK3 steps of the full {wl['name']} workload "
+                                   f"after {args.warmup} warm-up steps (numpy FP64 oracle, single thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * frsg.h - C ABI of the GB300 flux reconstruction stochastic Galerkin (FR-SG) library.
+ *
+ * The library advances the stochastic Galerkin system of a hyperbolic conservation law
+ * (Xiao, Kusch, Koellermeier, Frank, arXiv 2112.05946, §2.1, Eq. 6) discretised in
+ * physical space by flux reconstruction (§3) with the Radau (DG) correction, in random
+ * space by an orthonormal Legendre gPC expansion of one uniform variable z ~ U(-1, 1)
+ * with Gauss quadrature (§2.1, Eqs. 2-5), stabilised by the detector-switched modal
+ * filter (§4.1-4.2) and the positivity-preserving limiter (§4.3), in time by the
+ * three-stage strong-stability-preserving Runge-Kutta scheme.
+ *
+ * Conventions shared by every call:
+ *  - State layout ("uhat"): element x solution point x gPC mode x variable, row major,
+ *    uhat[((e * Np + j) * M + k) * S + s], Np = (P+1)^dim, M = N + 1.  In 2D the element
+ *    index is e = ey * nx + ex and the point index j = b * (P+1) + a (a along x).
+ *    Nodal-in-z arrays use the same order with Q quadrature nodes in place of M modes.
+ *  - A context owns every device buffer it allocates; caller pointers are borrowed for
+ *    the duration of the call only.  DEVICE pointers must live on the context's device;
+ *    work is stream-ordered on the context's stream (no hidden device synchronisation,
+ *    except in calls that return host data, which synchronise that stream).
+ *  - Errors are returned as frsg_status; nothing throws across the ABI.  The message of
+ *    the last error is kept in the context (fr_sg_last_error).  Errors found by kernels
+ *    (non-finite values, inadmissible element means) are latched in a device word and
+ *    reported by the next call that synchronises (fr_sg_check, or any call with host output).
+ *  - Precision: FRSG_FP64 keeps the state in double; FRSG_FP32 keeps it in float and
+ *    computes the residual in float, with the limiter, the time-step reduction and the
+ *    moments in double.  Calls that take "void*" state use the context's precision;
+ *    calls that take "double*" always use double.
+ */
+#ifndef FRSG_H
+#define FRSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct frsg_ctx frsg_ctx;
+
+typedef enum {
+    FRSG_OK = 0,
+    FRSG_E_INVAL = 1,        /* bad argument or unsupported combination of sizes */
+    FRSG_E_NOMEM = 2,        /* device or host allocation failed */
+    FRSG_E_CUDA = 3,         /* a CUDA runtime call failed */
+    FRSG_E_NONFINITE = 4,    /* a kernel produced NaN or Inf */
+    FRSG_E_POSITIVITY = 5,   /* an element mean has rho <= 0 or p <= 0 (§4.3 cannot apply) */
+    FRSG_E_TIMEOUT = 6,      /* a bounded device wait gave up */
+    FRSG_E_UNSUPPORTED = 7   /* valid request the library does not implement */
+} frsg_status;
+
+enum { FRSG_BC_PERIODIC = 0, FRSG_BC_DIRICHLET = 1, FRSG_BC_OUTFLOW = 2, FRSG_BC_REFLECT = 3 };
+enum { FRSG_EQ_ADVECTION = 0, FRSG_EQ_BURGERS = 1, FRSG_EQ_EULER = 2 };
+enum { FRSG_FILTER_NONE = 0, FRSG_FILTER_EXP = 1, FRSG_FILTER_L2 = 2 };
+enum { FRSG_FP64 = 0, FRSG_FP32 = 1 };
+enum { FRSG_HOST = 0, FRSG_DEVICE = 1 };
+
+/* Problem description.  Plain old data; struct_size must be sizeof(frsg_config). */
+typedef struct {
+    uint32_t struct_size;
+    int32_t dim;              /* 1 or 2 */
+    int32_t nx, ny;           /* elements along x (and y); uniform mesh (§3.1, line and quad maps) */
+    double x0, x1, y0, y1;    /* domain [x0, x1] (x [y0, y1]) */
+    int32_t bc[4];            /* x-left, x-right, y-bottom, y-top: FRSG_BC_*; periodic pairs must match */
+    int32_t P;                /* polynomial degree in x: P+1 Gauss-Legendre solution points (§3.2) */
+    int32_t N;                /* gPC degree: M = N+1 orthonormal Legendre modes (§2.1, Eq. 2) */
+    int32_t Q;                /* Gauss points in z for the Galerkin projection (§2.1, Eq. 5) */
+    int32_t equation;         /* FRSG_EQ_* */
+    double adv_speed;         /* advection speed a (FRSG_EQ_ADVECTION) */
+    double gamma;             /* ratio of specific heats (FRSG_EQ_EULER) */
+    int32_t filter;           /* FRSG_FILTER_*: exponential (§4.1.1) or L2 (§4.1.2) */
+    int32_t sensor;           /* 1: filter only elements with theta < 0.99 (§4.2); 0: every element */
+    double f_alpha, f_s;      /* exponential filter strength alpha and order s (N_* = 0) */
+    double f_eps1, f_eps2;    /* L2 filter damping of the last physical / random mode (§4.1.2, Eq. 39) */
+    double s0, kappa;         /* detector parameters (§4.2, Eq. 47), log10 scale */
+    int32_t limiter;          /* 1: positivity-preserving limiter on every stage input (§4.3) */
+    int32_t precision;        /* FRSG_FP64 or FRSG_FP32 */
+} frsg_config;
+
+/* Create a context: validates the configuration, builds the tables of §2.1 and §3 on
+ * the host (Gauss-Legendre points and weights, Lagrange derivative matrix, Radau
+ * correction derivatives, gPC evaluation and projection matrices, Vandermonde),
+ * uploads them, allocates the state and two stage buffers on the current device.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Limits: dim 1 with 1 <= P <= 4, or dim 2 with 1 <= P <= 3; 0 <= N <= 15; 1 <= Q <= 32;
+ * nx, ny >= 1 (>= 2 along a periodic direction).
+ * Returns FRSG_E_INVAL (with *out = NULL) for anything else. */
+frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out);
+
+/* Release every resource of the context.  NULL is accepted. */
+void fr_sg_destroy(frsg_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none).  Owned by the context. */
+const char* fr_sg_last_error(const frsg_ctx* ctx);
+
+/* Sizes: E elements, Np points per element, M modes, S variables, Q z-nodes.
+ * Any output pointer may be NULL. */
+frsg_status fr_sg_sizes(const frsg_ctx* ctx, int* E, int* Np, int* M, int* S, int* Q);
+
+/* Replace the stream used by all later calls. */
+frsg_status fr_sg_set_stream(frsg_ctx* ctx, void* stream);
+
+/* Host copies of the node coordinates the library uses: x[E*Np] (and y[E*Np] in 2D, else
+ * ignored; may be NULL) of the solution points, z[Q] of the random-space nodes.  A caller
+ * evaluates initial or boundary data at these nodes for the two projection calls below. */
+frsg_status fr_sg_get_nodes(const frsg_ctx* ctx, double* x, double* y, double* z);
+
+/* Dirichlet ghost state of one boundary side (0..3 as in cfg->bc), given as host values
+ * g[Q][S] at the z-nodes; projected onto the gPC modes like the initial data (§2.1, Eq. 6,
+ * third line).  The ghost state is constant along the side. */
+frsg_status fr_sg_set_boundary_nodal(frsg_ctx* ctx, int side, const double* g);
+
+/* Initial condition from values at the solution points and z-nodes: u0[E][Np][Q][S]
+ * (double, HOST or DEVICE per `where`), projected on the device:
+ * uhat_k(x_j) = sum_q w_q u0(x_j, z_q) Phi_k(z_q)   (§2.1, Eq. 6, third line, with Eq. 5). */
+frsg_status fr_sg_set_initial_nodal(frsg_ctx* ctx, const double* u0, int where);
+
+/* Copy the state in (set) or out (get) in the canonical double layout [E][Np][M][S],
+ * converting from or to float in FRSG_FP32 contexts.  HOST variants synchronise. */
+frsg_status fr_sg_set_state(frsg_ctx* ctx, const double* uhat, int where);
+frsg_status fr_sg_get_state(frsg_ctx* ctx, double* uhat, int where);
+
+/* Semi-discrete residual dudt = L(u) of the FR-SG system, no limiter and no filter:
+ * z-evaluation (§2.1, Eq. 2), flux (§3.2, Eq. 15), Galerkin projection (Eq. 6), face
+ * interpolation and local Lax-Friedrichs interface flux (§3.3), total-flux derivative
+ * with the Radau correction (§3.4, Eq. 21; 2D §3.5, Eq. 24).  u and dudt: DEVICE arrays
+ * [E][Np][M][S] in the context's precision; they must not overlap.  Boundary ghost
+ * states come from the context. */
+frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt);
+
+/* Advance the context's state by nsteps steps of size dt of the SSP-RK3 scheme, each
+ * stage being: limit the stage input (§4.3, if enabled), Euler update with the residual,
+ * SSP combination, detector and filter (§4.1-4.2, if enabled) - the forward-Euler
+ * sequence of §4.3, Eq. 53 applied per stage.  The exponential filter uses dt (§4.1.1).
+ * Asynchronous; errors found on the device are reported by fr_sg_check.
+ * use_graph = 1 replays the three stage launches from a captured CUDA graph. */
+frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph);
+
+/* Issue stage `stage` (0, 1, 2) of one SSP-RK3 step of size dt: stage 0 reads the state
+ * and writes the first stage buffer, stage 1 reads it and writes the second, stage 2 reads
+ * the second and writes the state.  Calling stages 0, 1, 2 in order is one
+ * fr_sg_rk_step(ctx, dt, 1, 0); separate calls let a caller time or interleave stages. */
+frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt);
+
+/* Detector + filter (§4.1-4.2) on the current state with step size dt. */
+frsg_status fr_sg_filter(frsg_ctx* ctx, double dt);
+
+/* Positivity-preserving limiter (§4.3, Eqs. 48-52) on the current state (Euler only). */
+frsg_status fr_sg_limit(frsg_ctx* ctx);
+
+/* Mean and variance over z at each solution point: mean = uhat_0, var = sum_{k>=1} uhat_k^2
+ * (orthonormal basis, §2.1, Eq. 3).  mean, var: double [E][Np][S], HOST or DEVICE. */
+frsg_status fr_sg_moments(frsg_ctx* ctx, double* mean, double* var, int where);
+
+/* dt = cfl * h / lambda_max, lambda_max the largest flux-Jacobian spectral radius over
+ * solution points and z-nodes of the current state, h the smallest element width.
+ * Synchronises; *dt is a host double. */
+frsg_status fr_sg_cfl_dt(frsg_ctx* ctx, double cfl, double* dt);
+
+/* Decisions of the three stages of the last fr_sg_rk_step step (or of the last
+ * fr_sg_filter / fr_sg_limit call, in row 0): filter_on[3][E] (1 = detector flagged the
+ * element and the filter ran), beta[3][E] (limiter scaling, 1 = untouched).  Host arrays;
+ * either may be NULL.  Synchronises. */
+frsg_status fr_sg_get_decisions(frsg_ctx* ctx, uint8_t* filter_on, double* beta);
+
+/* Replay mode: when flags is non-NULL, the next stages take their filter decisions from
+ * flags[nstages][E] (host array, copied) in order instead of the detector, one row per
+ * stage, until the rows run out; NULL switches replay off.  Graph replay is disabled
+ * while rows remain. */
+frsg_status fr_sg_set_replay(frsg_ctx* ctx, const uint8_t* flags, int nstages);
+
+/* Synchronise the context's stream and report (and clear) errors latched by kernels. */
+frsg_status fr_sg_check(frsg_ctx* ctx);
+
+/* Elements per CTA of the stage kernel (the tile): te >= 1 sets it, te = 0 restores the
+ * automatic choice.  Returns FRSG_E_INVAL when the tile does not fit in shared memory or
+ * exceeds 512 threads.  *te_out (may be NULL) receives the tile in use. */
+frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out);
+
+/* Number of kernel launches issued on this context since creation (graph replays count
+ * each captured kernel).  Host counter; never synchronises. */
+uint64_t fr_sg_launch_count(const frsg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRSG_H */

@@ -1,0 +1,686 @@
+// C ABI of the FR-SG library: context lifetime, data movement and the stage driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "frsg.h"
+#include "internal.h"
+
+namespace frsg {
+size_t stage1d_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S);
+size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S);
+}  // namespace frsg
+
+struct frsg_ctx {
+    frsg_config cfg{};
+    cudaStream_t stream = nullptr;
+    int E = 0, Np = 0, M = 0, Q = 0, S = 0, n1 = 0;
+    bool fp64 = true;
+    size_t esz = 8;
+    frsg::HostTables ht;
+    frsg::TabOff off{};
+    std::vector<double> htab;
+    double* d_tab = nullptr;
+    double* d_ghost = nullptr;
+    void* d_u = nullptr;
+    void* d_u1 = nullptr;
+    void* d_u2 = nullptr;
+    double* d_conv = nullptr;     // FP32 contexts: double staging buffer for set/get_state
+    uint8_t* d_flags = nullptr;   // [3][E]
+    double* d_beta = nullptr;     // [3][E]
+    unsigned* d_err = nullptr;
+    unsigned long long* d_speed = nullptr;
+    uint8_t* d_replay = nullptr;
+    int replay_rows = 0, replay_pos = 0;
+    std::string last_error;
+    uint64_t launches = 0;
+    int TE = 1, TE_lim = 1;
+    cudaGraphExec_t graph_exec = nullptr;
+    double graph_dt = 0.0;
+    int graph_kernels = 0;
+};
+
+namespace {
+
+using frsg::StageArgs;
+using frsg::LimitArgs;
+
+frsg_status fail(frsg_ctx* c, frsg_status st, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return st;
+}
+
+frsg_status cuda_fail(frsg_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, FRSG_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t e__ = (call);                                         \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #call);        \
+    } while (0)
+
+bool periodic_pair_ok(const frsg_config& c) {
+    if ((c.bc[0] == FRSG_BC_PERIODIC) != (c.bc[1] == FRSG_BC_PERIODIC)) return false;
+    if (c.dim == 2 && (c.bc[2] == FRSG_BC_PERIODIC) != (c.bc[3] == FRSG_BC_PERIODIC)) return false;
+    return true;
+}
+
+std::string validate(const frsg_config& c) {
+    if (c.struct_size != sizeof(frsg_config)) return "struct_size does not match sizeof(frsg_config)";
+    if (c.dim != 1 && c.dim != 2) return "dim must be 1 or 2";
+    if (c.dim == 1 && (c.P < 1 || c.P > 4)) return "1D needs 1 <= P <= 4";
+    if (c.dim == 2 && (c.P < 1 || c.P > 3)) return "2D needs 1 <= P <= 3";
+    if (c.N < 0 || c.N + 1 > frsg::kMaxM) return "N out of range (0..15)";
+    if (c.Q < 1 || c.Q > frsg::kMaxQ) return "Q out of range (1..32)";
+    if (c.nx < 1 || (c.dim == 2 && c.ny < 1)) return "need at least one element per direction";
+    if (c.bc[0] == FRSG_BC_PERIODIC && c.nx < 2) return "periodic x needs nx >= 2";
+    if (c.dim == 2 && c.bc[2] == FRSG_BC_PERIODIC && c.ny < 2) return "periodic y needs ny >= 2";
+    if (!(c.x1 > c.x0) || (c.dim == 2 && !(c.y1 > c.y0))) return "empty domain";
+    if (c.equation < FRSG_EQ_ADVECTION || c.equation > FRSG_EQ_EULER) return "unknown equation";
+    if (c.filter < FRSG_FILTER_NONE || c.filter > FRSG_FILTER_L2) return "unknown filter";
+    if (c.precision != FRSG_FP64 && c.precision != FRSG_FP32) return "unknown precision";
+    if (c.limiter && c.equation != FRSG_EQ_EULER) return "the positivity limiter is defined for Euler only";
+    if (c.dim == 2 && c.equation != FRSG_EQ_EULER) return "2D supports the Euler equations only";
+    for (int i = 0; i < (c.dim == 1 ? 2 : 4); ++i)
+        if (c.bc[i] < FRSG_BC_PERIODIC || c.bc[i] > FRSG_BC_REFLECT) return "unknown boundary kind";
+    if (!periodic_pair_ok(c)) return "periodic boundaries must come in pairs";
+    if (c.equation == FRSG_EQ_EULER && !(c.gamma > 1.0)) return "gamma must exceed 1";
+    if (c.filter == FRSG_FILTER_L2 && (!(c.f_eps1 > 0) || !(c.f_eps2 > 0))) return "L2 filter needs eps1, eps2 > 0";
+    if (c.filter != FRSG_FILTER_NONE && c.sensor && !(c.kappa > 0)) return "detector needs kappa > 0";
+    return "";
+}
+
+// Device table block: FR tables, gPC tables, limiter point matrix and averaging weights.
+void build_device_tables(frsg_ctx* c) {
+    const frsg::HostTables& t = c->ht;
+    const int n1 = t.n1, Np = c->Np;
+    std::vector<double>& v = c->htab;
+    v.clear();
+    auto put = [&](const std::vector<double>& a) {
+        int o = (int)v.size();
+        v.insert(v.end(), a.begin(), a.end());
+        return o;
+    };
+    c->off.D = put(t.D);
+    c->off.lm = put(t.lm);
+    c->off.lp = put(t.lp);
+    c->off.dhL = put(t.dhL);
+    c->off.dhR = put(t.dhR);
+    c->off.Vx = put(t.Vx);
+    c->off.Vxinv = put(t.Vxinv);
+    c->off.VzT = put(t.VzT);
+    c->off.Pz = put(t.Pz);
+    // averaging weights of the element mean over r (and s): w_j / 2^dim
+    std::vector<double> wavg(Np);
+    if (c->cfg.dim == 1) {
+        for (int j = 0; j < n1; ++j) wavg[j] = 0.5 * t.w[j];
+    } else {
+        for (int b = 0; b < n1; ++b)
+            for (int a = 0; a < n1; ++a) wavg[b * n1 + a] = 0.25 * t.w[a] * t.w[b];
+    }
+    c->off.w = put(wavg);
+    // limiter points: solution points, then flux points on the faces (§4.3)
+    std::vector<double> L;
+    if (c->cfg.dim == 1) {
+        c->off.NL = n1 + 2;
+        L.assign((size_t)(n1 + 2) * n1, 0.0);
+        for (int j = 0; j < n1; ++j) L[j * n1 + j] = 1.0;
+        for (int j = 0; j < n1; ++j) {
+            L[n1 * n1 + j] = t.lm[j];
+            L[(n1 + 1) * n1 + j] = t.lp[j];
+        }
+    } else {
+        c->off.NL = Np + 4 * n1;
+        L.assign((size_t)c->off.NL * Np, 0.0);
+        for (int j = 0; j < Np; ++j) L[(size_t)j * Np + j] = 1.0;
+        int row = Np;
+        for (int face = 0; face < 4; ++face)
+            for (int i = 0; i < n1; ++i, ++row)
+                for (int b = 0; b < n1; ++b)
+                    for (int a = 0; a < n1; ++a) {
+                        double val = 0.0;
+                        if (face == 0) val = (b == i) ? t.lm[a] : 0.0;       // r = -1, s = s_i
+                        else if (face == 1) val = (b == i) ? t.lp[a] : 0.0;  // r = +1
+                        else if (face == 2) val = (a == i) ? t.lm[b] : 0.0;  // s = -1, r = r_i
+                        else val = (a == i) ? t.lp[b] : 0.0;                 // s = +1
+                        L[(size_t)row * Np + b * n1 + a] = val;
+                    }
+    }
+    c->off.Lpts = put(L);
+    c->off.total = (int)v.size();
+}
+
+StageArgs base_args(frsg_ctx* c) {
+    StageArgs A{};
+    A.E = c->E;
+    A.nx = c->cfg.nx;
+    A.ny = c->cfg.dim == 2 ? c->cfg.ny : 1;
+    A.M = c->M;
+    A.Q = c->Q;
+    A.invJx = 2.0 * c->cfg.nx / (c->cfg.x1 - c->cfg.x0);
+    A.invJy = c->cfg.dim == 2 ? 2.0 * c->cfg.ny / (c->cfg.y1 - c->cfg.y0) : 0.0;
+    A.tab = c->d_tab;
+    A.off = c->off;
+    A.ghost = c->d_ghost;
+    for (int i = 0; i < 4; ++i) A.bc[i] = c->cfg.bc[i];
+    A.adv = c->cfg.adv_speed;
+    A.gamma = c->cfg.gamma;
+    A.filter = c->cfg.filter;
+    A.sensor = c->cfg.sensor;
+    A.f_alpha = c->cfg.f_alpha;
+    A.f_s = c->cfg.f_s;
+    A.f_eps1 = c->cfg.f_eps1;
+    A.f_eps2 = c->cfg.f_eps2;
+    A.s0 = c->cfg.s0;
+    A.kappa = c->cfg.kappa;
+    A.err = c->d_err;
+    A.TE = c->TE;
+    return A;
+}
+
+cudaError_t launch_stage(frsg_ctx* c, const StageArgs& A) {
+    c->launches += 1;
+    if (c->cfg.dim == 1) return frsg::launch_stage1d(c->cfg, c->fp64, A, c->stream);
+    return frsg::launch_stage2d(c->cfg, c->fp64, A, c->stream);
+}
+
+cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
+    LimitArgs L{};
+    L.u = u;
+    L.E = c->E;
+    L.M = c->M;
+    L.Q = c->Q;
+    L.S = c->S;
+    L.Np = c->Np;
+    L.tab = c->d_tab;
+    L.off = c->off;
+    L.gamma = c->cfg.gamma;
+    L.beta = beta;
+    L.err = c->d_err;
+    L.dim = c->cfg.dim;
+    L.TE = c->TE_lim;
+    c->launches += 1;
+    return frsg::launch_limit(c->fp64, L, c->stream);
+}
+
+// Stage s of an SSP-RK3 step (Shu-Osher form): limit the stage input, then
+// uout = a_s u^n + b_s (uin + dt L(uin)) followed by detector + filter.
+//   s = 0: u -> u1,  s = 1: u1 -> u2,  s = 2: u2 -> u (in place on u^n, element-local).
+cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
+    const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
+    void* bufs_in[3] = {c->d_u, c->d_u1, c->d_u2};
+    void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    if (c->cfg.limiter) {
+        cudaError_t e = launch_limiter(c, bufs_in[s], c->d_beta + (size_t)s * c->E);
+        if (e != cudaSuccess) return e;
+    }
+    StageArgs A = base_args(c);
+    A.uin = bufs_in[s];
+    A.ubase = c->d_u;
+    A.uout = bufs_out[s];
+    A.a = ca[s];
+    A.b = cb[s];
+    A.c = cb[s] * dt;
+    A.dt_filter = dt;
+    A.do_filter = filt ? 1 : 0;
+    A.flags = c->d_flags + (size_t)s * c->E;
+    A.replay = nullptr;
+    if (use_replay && c->replay_pos < c->replay_rows) {
+        A.replay = c->d_replay + (size_t)c->replay_pos * c->E;
+        c->replay_pos += 1;
+    }
+    return launch_stage(c, A);
+}
+
+cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
+    for (int s = 0; s < 3; ++s) {
+        cudaError_t e = issue_stage(c, s, dt, use_replay);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int choose_tile_1d(const frsg_ctx* c) {
+    const int Q = c->Q;
+    int te = std::max(1, c->E / (2 * 152));
+    te = std::min(te, std::max(1, 512 / Q));
+    while (te > 1 && frsg::stage1d_smem_bytes(c->fp64, te, c->Np, c->M, Q, c->S) > 200 * 1024) --te;
+    return te;
+}
+
+int choose_tile_2d(const frsg_ctx* c) {
+    int te = 1;
+    while (te < 8 && frsg::stage2d_smem_bytes(c->fp64, te * 2, c->n1, c->M, c->Q, c->S) <= 100 * 1024 &&
+           te * 2 * c->Q * c->n1 <= 512 && c->E / (te * 2) >= 2 * 152)
+        te *= 2;
+    return te;
+}
+
+}  // namespace
+
+extern "C" {
+
+frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
+    if (!out) return FRSG_E_INVAL;
+    *out = nullptr;
+    if (!cfg) return FRSG_E_INVAL;
+    std::string why = validate(*cfg);
+    if (!why.empty()) {
+        std::fprintf(stderr, "fr_sg_init: %s\n", why.c_str());
+        return FRSG_E_INVAL;
+    }
+    frsg_ctx* ctx = new (std::nothrow) frsg_ctx();
+    if (!ctx) return FRSG_E_NOMEM;
+    ctx->cfg = *cfg;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->n1 = cfg->P + 1;
+    ctx->Np = cfg->dim == 1 ? ctx->n1 : ctx->n1 * ctx->n1;
+    ctx->E = cfg->nx * (cfg->dim == 2 ? cfg->ny : 1);
+    ctx->M = cfg->N + 1;
+    ctx->Q = cfg->Q;
+    ctx->S = cfg->equation == FRSG_EQ_EULER ? (cfg->dim == 1 ? 3 : 4) : 1;
+    ctx->fp64 = cfg->precision == FRSG_FP64;
+    ctx->esz = ctx->fp64 ? sizeof(double) : sizeof(float);
+    frsg::build_tables(cfg->P, cfg->N, cfg->Q, &ctx->ht);
+    build_device_tables(ctx);
+    const size_t nstate = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    auto cleanup_fail = [&](cudaError_t e, const char* where) {
+        std::fprintf(stderr, "fr_sg_init: %s: %s\n", where, cudaGetErrorString(e));
+        fr_sg_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? FRSG_E_NOMEM : FRSG_E_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&ctx->d_tab, sizeof(double) * ctx->off.total)) != cudaSuccess) return cleanup_fail(e, "tables");
+    if ((e = cudaMalloc(&ctx->d_ghost, sizeof(double) * 4 * ctx->M * ctx->S)) != cudaSuccess) return cleanup_fail(e, "ghost");
+    if ((e = cudaMalloc(&ctx->d_u, ctx->esz * nstate)) != cudaSuccess) return cleanup_fail(e, "state");
+    if ((e = cudaMalloc(&ctx->d_u1, ctx->esz * nstate)) != cudaSuccess) return cleanup_fail(e, "stage 1");
+    if ((e = cudaMalloc(&ctx->d_u2, ctx->esz * nstate)) != cudaSuccess) return cleanup_fail(e, "stage 2");
+    if (!ctx->fp64 && (e = cudaMalloc(&ctx->d_conv, sizeof(double) * nstate)) != cudaSuccess)
+        return cleanup_fail(e, "conversion buffer");
+    if ((e = cudaMalloc(&ctx->d_flags, 3 * (size_t)ctx->E)) != cudaSuccess) return cleanup_fail(e, "flags");
+    if ((e = cudaMalloc(&ctx->d_beta, 3 * sizeof(double) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "beta");
+    if ((e = cudaMalloc(&ctx->d_err, sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "err");
+    if ((e = cudaMalloc(&ctx->d_speed, sizeof(unsigned long long))) != cudaSuccess) return cleanup_fail(e, "speed");
+    e = cudaMemcpyAsync(ctx->d_tab, ctx->htab.data(), sizeof(double) * ctx->off.total, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_ghost, 0, sizeof(double) * 4 * ctx->M * ctx->S, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_u, 0, ctx->esz * nstate, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flags, 0, 3 * (size_t)ctx->E, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream);
+    if (e == cudaSuccess) {
+        std::vector<double> ones(3 * (size_t)ctx->E, 1.0);
+        e = cudaMemcpyAsync(ctx->d_beta, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
+    if (e != cudaSuccess) return cleanup_fail(e, "upload");
+    ctx->TE = cfg->dim == 1 ? choose_tile_1d(ctx) : 1;
+    ctx->TE_lim = std::max(1, 256 / ctx->Q);
+    if (cfg->dim == 2) {
+        if (frsg::stage2d_smem_bytes(ctx->fp64, 1, ctx->n1, ctx->M, ctx->Q, ctx->S) > 200 * 1024) {
+            fr_sg_destroy(ctx);
+            return FRSG_E_INVAL;
+        }
+        ctx->TE = choose_tile_2d(ctx);
+        while (ctx->TE_lim > 1 && sizeof(double) * (size_t)ctx->TE_lim * ctx->Np * ctx->S * ctx->Q > 96 * 1024)
+            ctx->TE_lim /= 2;
+    }
+    *out = ctx;
+    return FRSG_OK;
+}
+
+void fr_sg_destroy(frsg_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    cudaFree(ctx->d_tab);
+    cudaFree(ctx->d_ghost);
+    cudaFree(ctx->d_u);
+    cudaFree(ctx->d_u1);
+    cudaFree(ctx->d_u2);
+    cudaFree(ctx->d_conv);
+    cudaFree(ctx->d_flags);
+    cudaFree(ctx->d_beta);
+    cudaFree(ctx->d_err);
+    cudaFree(ctx->d_speed);
+    cudaFree(ctx->d_replay);
+    delete ctx;
+}
+
+const char* fr_sg_last_error(const frsg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+frsg_status fr_sg_sizes(const frsg_ctx* ctx, int* E, int* Np, int* M, int* S, int* Q) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (E) *E = ctx->E;
+    if (Np) *Np = ctx->Np;
+    if (M) *M = ctx->M;
+    if (S) *S = ctx->S;
+    if (Q) *Q = ctx->Q;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_set_stream(frsg_ctx* ctx, void* stream) {
+    if (!ctx) return FRSG_E_INVAL;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_get_nodes(const frsg_ctx* ctx, double* x, double* y, double* z) {
+    if (!ctx) return FRSG_E_INVAL;
+    const frsg_config& c = ctx->cfg;
+    const int n1 = ctx->n1;
+    const double dx = (c.x1 - c.x0) / c.nx;
+    const double dy = c.dim == 2 ? (c.y1 - c.y0) / c.ny : 0.0;
+    if (x || y) {
+        for (int e = 0; e < ctx->E; ++e) {
+            const int ex = e % c.nx, ey = e / c.nx;
+            for (int j = 0; j < ctx->Np; ++j) {
+                const int a = j % n1, b = j / n1;
+                if (c.dim == 1) {
+                    if (x) x[(size_t)e * ctx->Np + j] = c.x0 + dx * e + 0.5 * dx * (ctx->ht.r[j] + 1.0);
+                } else {
+                    if (x) x[(size_t)e * ctx->Np + j] = c.x0 + dx * ex + 0.5 * dx * (ctx->ht.r[a] + 1.0);
+                    if (y) y[(size_t)e * ctx->Np + j] = c.y0 + dy * ey + 0.5 * dy * (ctx->ht.r[b] + 1.0);
+                }
+            }
+        }
+    }
+    if (z)
+        for (int q = 0; q < ctx->Q; ++q) z[q] = ctx->ht.z[q];
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_set_boundary_nodal(frsg_ctx* ctx, int side, const double* g) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (side < 0 || side > 3 || !g) return fail(ctx, FRSG_E_INVAL, "bad side or null values");
+    std::vector<double> modes((size_t)ctx->M * ctx->S, 0.0);
+    for (int k = 0; k < ctx->M; ++k)
+        for (int s = 0; s < ctx->S; ++s) {
+            double acc = 0.0;
+            for (int q = 0; q < ctx->Q; ++q) acc += ctx->ht.Pz[k * ctx->Q + q] * g[q * ctx->S + s];
+            modes[k * ctx->S + s] = acc;
+        }
+    CK(cudaMemcpyAsync(ctx->d_ghost + (size_t)side * ctx->M * ctx->S, modes.data(), sizeof(double) * modes.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_set_initial_nodal(frsg_ctx* ctx, const double* u0, int where) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!u0) return fail(ctx, FRSG_E_INVAL, "null input");
+    const size_t n = (size_t)ctx->E * ctx->Np * ctx->Q * ctx->S;
+    const double* src = u0;
+    double* tmp = nullptr;
+    if (where == FRSG_HOST) {
+        CK(cudaMalloc(&tmp, sizeof(double) * n));
+        cudaError_t e = cudaMemcpyAsync(tmp, u0, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(ctx, e, "copy initial data");
+        }
+        src = tmp;
+    }
+    ctx->launches += 1;
+    cudaError_t e = frsg::launch_project(ctx->fp64, src, ctx->d_u, ctx->E, ctx->Np, ctx->M, ctx->Q, ctx->S, ctx->d_tab,
+                                         ctx->off, ctx->stream);
+    if (tmp) {
+        cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+        cudaFree(tmp);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project initial data");
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_set_state(frsg_ctx* ctx, const double* uhat, int where) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!uhat) return fail(ctx, FRSG_E_INVAL, "null state");
+    const size_t n = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    const cudaMemcpyKind kind = where == FRSG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (ctx->fp64) {
+        CK(cudaMemcpyAsync(ctx->d_u, uhat, sizeof(double) * n, kind, ctx->stream));
+    } else {
+        cudaError_t e = cudaMemcpyAsync(ctx->d_conv, uhat, sizeof(double) * n, kind, ctx->stream);
+        if (e == cudaSuccess) e = frsg::launch_convert(ctx->d_conv, ctx->d_u, n, true, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "set_state");
+        ctx->launches += 1;
+    }
+    if (where == FRSG_HOST) CK(cudaStreamSynchronize(ctx->stream));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_get_state(frsg_ctx* ctx, double* uhat, int where) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!uhat) return fail(ctx, FRSG_E_INVAL, "null state");
+    const size_t n = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    const cudaMemcpyKind kind = where == FRSG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (ctx->fp64) {
+        CK(cudaMemcpyAsync(uhat, ctx->d_u, sizeof(double) * n, kind, ctx->stream));
+    } else {
+        cudaError_t e = frsg::launch_convert(ctx->d_u, ctx->d_conv, n, false, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(uhat, ctx->d_conv, sizeof(double) * n, kind, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "get_state");
+        ctx->launches += 1;
+    }
+    if (where == FRSG_HOST) CK(cudaStreamSynchronize(ctx->stream));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!u || !dudt || u == dudt) return fail(ctx, FRSG_E_INVAL, "rhs needs distinct, non-null buffers");
+    StageArgs A = base_args(ctx);
+    A.uin = u;
+    A.ubase = nullptr;
+    A.uout = dudt;
+    A.a = 0.0;
+    A.b = 0.0;
+    A.c = 1.0;
+    A.do_filter = 0;
+    CK(launch_stage(ctx, A));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
+    const int kernels_per_step = 3 * (ctx->cfg.limiter ? 2 : 1);
+    for (int n = 0; n < nsteps; ++n) {
+        const bool replaying = ctx->replay_pos < ctx->replay_rows;
+        if (use_graph && !replaying) {
+            if (!ctx->graph_exec || ctx->graph_dt != dt) {
+                if (ctx->graph_exec) {
+                    cudaGraphExecDestroy(ctx->graph_exec);
+                    ctx->graph_exec = nullptr;
+                }
+                cudaStream_t cap = ctx->stream;
+                bool own = false;
+                if (cap == nullptr) {
+                    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+                    own = true;
+                }
+                cudaStream_t saved = ctx->stream;
+                ctx->stream = cap;
+                const uint64_t before = ctx->launches;
+                cudaGraph_t graph = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e1 = issue_step(ctx, dt, false);
+                    e = cudaStreamEndCapture(cap, &graph);
+                    if (e1 != cudaSuccess) e = e1;
+                }
+                ctx->launches = before;
+                ctx->stream = saved;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (own) {
+                    cudaStreamSynchronize(cap);
+                    cudaStreamDestroy(cap);
+                }
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+                ctx->graph_dt = dt;
+                ctx->graph_kernels = kernels_per_step;
+            }
+            CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+            ctx->launches += ctx->graph_kernels;
+        } else {
+            CK(issue_step(ctx, dt, true));
+        }
+    }
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt))
+        return fail(ctx, FRSG_E_INVAL, "need stage in 0..2 and dt > 0");
+    CK(issue_stage(ctx, stage, dt, true));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_filter(frsg_ctx* ctx, double dt) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (ctx->cfg.filter == FRSG_FILTER_NONE) return FRSG_OK;
+    StageArgs A = base_args(ctx);
+    A.uin = ctx->d_u;
+    A.ubase = nullptr;
+    A.uout = ctx->d_u1;
+    A.a = 0.0;
+    A.b = 1.0;
+    A.c = 0.0;
+    A.dt_filter = dt;
+    A.do_filter = 1;
+    A.flags = ctx->d_flags;
+    if (ctx->replay_pos < ctx->replay_rows) {
+        A.replay = ctx->d_replay + (size_t)ctx->replay_pos * ctx->E;
+        ctx->replay_pos += 1;
+    }
+    CK(launch_stage(ctx, A));
+    const size_t n = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    CK(cudaMemcpyAsync(ctx->d_u, ctx->d_u1, ctx->esz * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_limit(frsg_ctx* ctx) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (ctx->cfg.equation != FRSG_EQ_EULER) return fail(ctx, FRSG_E_UNSUPPORTED, "limiter needs the Euler equations");
+    CK(launch_limiter(ctx, ctx->d_u, ctx->d_beta));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_moments(frsg_ctx* ctx, double* mean, double* var, int where) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!mean || !var) return fail(ctx, FRSG_E_INVAL, "null output");
+    const size_t n = (size_t)ctx->E * ctx->Np * ctx->S;
+    double* dm = mean;
+    double* dv = var;
+    if (where == FRSG_HOST) {
+        CK(cudaMalloc(&dm, 2 * sizeof(double) * n));
+        dv = dm + n;
+    }
+    ctx->launches += 1;
+    cudaError_t e = frsg::launch_moments(ctx->fp64, ctx->d_u, dm, dv, ctx->E, ctx->Np, ctx->M, ctx->S, ctx->stream);
+    if (where == FRSG_HOST) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(mean, dm, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(var, dv, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        cudaFree(dm);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "moments");
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_cfl_dt(frsg_ctx* ctx, double cfl, double* dt) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!dt || !(cfl > 0.0)) return fail(ctx, FRSG_E_INVAL, "need cfl > 0 and an output");
+    CK(cudaMemsetAsync(ctx->d_speed, 0, sizeof(unsigned long long), ctx->stream));
+    ctx->launches += 1;
+    CK(frsg::launch_max_speed(ctx->fp64, ctx->d_u, ctx->E, ctx->Np, ctx->M, ctx->Q, ctx->S, ctx->cfg.dim,
+                              ctx->cfg.equation, ctx->cfg.adv_speed, ctx->cfg.gamma, ctx->d_tab, ctx->off,
+                              ctx->d_speed, ctx->stream));
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, ctx->d_speed, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double lam;
+    std::memcpy(&lam, &bits, sizeof(lam));
+    if (!(lam > 0.0) || !std::isfinite(lam)) return fail(ctx, FRSG_E_NONFINITE, "no finite positive wave speed");
+    const frsg_config& c = ctx->cfg;
+    double h = (c.x1 - c.x0) / c.nx;
+    if (c.dim == 2) h = std::min(h, (c.y1 - c.y0) / c.ny);
+    *dt = cfl * h / lam;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_get_decisions(frsg_ctx* ctx, uint8_t* filter_on, double* beta) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (filter_on) CK(cudaMemcpyAsync(filter_on, ctx->d_flags, 3 * (size_t)ctx->E, cudaMemcpyDeviceToHost, ctx->stream));
+    if (beta) CK(cudaMemcpyAsync(beta, ctx->d_beta, 3 * sizeof(double) * ctx->E, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_set_replay(frsg_ctx* ctx, const uint8_t* flags, int nstages) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (ctx->d_replay) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->d_replay);
+        ctx->d_replay = nullptr;
+    }
+    ctx->replay_rows = 0;
+    ctx->replay_pos = 0;
+    if (!flags || nstages <= 0) return FRSG_OK;
+    const size_t n = (size_t)nstages * ctx->E;
+    CK(cudaMalloc(&ctx->d_replay, n));
+    CK(cudaMemcpyAsync(ctx->d_replay, flags, n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->replay_rows = nstages;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_check(frsg_ctx* ctx) {
+    if (!ctx) return FRSG_E_INVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) {
+        CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+        if (err & frsg::kErrPositivity) return fail(ctx, FRSG_E_POSITIVITY, "an element mean has rho <= 0 or p <= 0");
+        if (err & frsg::kErrNonFinite) return fail(ctx, FRSG_E_NONFINITE, "a kernel produced a non-finite value");
+        if (err & frsg::kErrTimeout) return fail(ctx, FRSG_E_TIMEOUT, "a bounded device wait gave up");
+    }
+    return FRSG_OK;
+}
+
+uint64_t fr_sg_launch_count(const frsg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (te < 0) return fail(ctx, FRSG_E_INVAL, "tile must be >= 0");
+    int want = te;
+    if (te == 0) {
+        want = ctx->cfg.dim == 1 ? choose_tile_1d(ctx) : choose_tile_2d(ctx);
+    } else if (ctx->cfg.dim == 1) {
+        if (te * ctx->Q > 512 || frsg::stage1d_smem_bytes(ctx->fp64, te, ctx->Np, ctx->M, ctx->Q, ctx->S) > 220 * 1024)
+            return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
+    } else {
+        if (te * ctx->Q * ctx->n1 > 512 ||
+            frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) > 220 * 1024)
+            return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
+    }
+    if (want != ctx->TE && ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    ctx->TE = want;
+    if (te_out) *te_out = ctx->TE;
+    return FRSG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// Internal declarations of the FR-SG library: host tables, device table layout,
+// kernel argument blocks and launch wrappers.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "frsg.h"
+
+namespace frsg {
+
+constexpr int kMaxM = 16;   // gPC modes (N <= 15)
+constexpr int kMaxQ = 32;   // z-nodes (one warp of lanes per element row at most)
+
+// Error bits latched by kernels in the context's device word.
+enum : unsigned { kErrNonFinite = 1u, kErrPositivity = 2u, kErrTimeout = 4u };
+
+// Host tables for degree P in x, gPC degree N and Q z-nodes (§2.1, §3, §4 Eq. 28).
+struct HostTables {
+    int n1 = 0, M = 0, Q = 0;
+    std::vector<double> r, w;        // n1 Gauss-Legendre points / weights on [-1, 1]
+    std::vector<double> D;           // n1*n1, D[j*n1+m] = ell_m'(r_j)
+    std::vector<double> lm, lp;      // n1, ell_j(-1), ell_j(+1)
+    std::vector<double> dhL, dhR;    // n1, Radau correction derivatives at r_j
+    std::vector<double> Vx, Vxinv;   // n1*n1, Vx[j*n1+m] = Psi_m(r_j), Vxinv[m*n1+j]
+    std::vector<double> z, wz;       // Q nodes, probability weights (sum 1)
+    std::vector<double> VzT;         // M*Q, VzT[k*Q+q] = Phi_k(z_q)
+    std::vector<double> Pz;          // M*Q, Pz[k*Q+q] = wz_q Phi_k(z_q)
+};
+void build_tables(int P, int N, int Q, HostTables* t);
+
+// Offsets (in doubles) of each table inside the single device table block.
+struct TabOff {
+    int D, lm, lp, dhL, dhR, Vx, Vxinv, VzT, Pz, w, Lpts, total;
+    int NL;   // rows of Lpts: solution points then face flux points (limiter, §4.3)
+};
+
+// Everything a stage kernel needs, passed by value.
+struct StageArgs {
+    const void* uin;       // stage input [E][Np][M][S]
+    const void* ubase;     // u^n of the SSP combination (unused when a == 0)
+    void* uout;            // output
+    double a, b, c;        // uout = a*ubase + b*uin + c*L(uin)
+    double dt_filter;      // step size entering the exponential filter
+    int E, nx, ny, M, Q;
+    double invJx, invJy;   // 2 / element width, 2 / element height
+    const double* tab;     // device table block
+    TabOff off;
+    const double* ghost;   // [4][M][S] ghost gPC states of Dirichlet sides
+    int bc[4];
+    double adv, gamma;
+    int do_filter, filter, sensor;
+    double f_alpha, f_s, f_eps1, f_eps2, s0, kappa;
+    const uint8_t* replay; // [E] filter decisions to use instead of the detector, or null
+    uint8_t* flags;        // [E] filter decisions taken, or null
+    unsigned* err;
+    int TE;                // elements per block
+};
+
+struct LimitArgs {
+    void* u;               // state limited in place
+    int E, M, Q, S, Np;
+    const double* tab;
+    TabOff off;
+    double gamma;
+    double* beta;          // [E] recorded scaling (beta1*beta2), or null
+    unsigned* err;
+    int dim;
+    int TE;
+};
+
+// Launch wrappers (kern1d.cu / kern2d.cu / kmisc.cu).  Return cudaGetLastError().
+cudaError_t launch_stage1d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st);
+cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st);
+cudaError_t launch_limit(bool fp64, const LimitArgs& A, cudaStream_t st);
+cudaError_t launch_project(bool fp64, const double* u0, void* uhat, int E, int Np, int M, int Q, int S,
+                           const double* tab, TabOff off, cudaStream_t st);
+cudaError_t launch_moments(bool fp64, const void* uhat, double* mean, double* var, int E, int Np, int M,
+                           int S, cudaStream_t st);
+cudaError_t launch_max_speed(bool fp64, const void* uhat, int E, int Np, int M, int Q, int S, int dim,
+                             int equation, double adv, double gamma, const double* tab, TabOff off,
+                             unsigned long long* out_bits, cudaStream_t st);
+cudaError_t launch_convert(const void* src, void* dst, size_t n, bool to_float, cudaStream_t st);
+
+}  // namespace frsg

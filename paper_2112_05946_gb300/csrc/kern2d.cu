@@ -1,0 +1,460 @@
+// Fused FR-SG stage kernel on a uniform, axis-aligned quad mesh (tensor-product FR, §3.5).
+//
+// One CTA owns TE consecutive elements of one mesh row; thread (q, l, te) owns z-node q,
+// line l of element te.  As row thread (l = b) it evaluates the gPC expansion on the
+// points (a, b), a = 0..P, and runs the x-direction FR operator along that row; as
+// column thread (l = a) it runs the y-direction operator down column a.  Per element
+// and stage:
+//   a2  u(r_a, s_b, z_q) = sum_k Phi_k(z_q) uhat_(b,a),k          (§2.1, Eq. 2)
+//   a5  traces on the four faces by ell(+-1) along rows / columns (§3.3)
+//   a6  LLF fluxes on x-faces (f, |v_x| + c) and y-faces (g, |v_y| + c); the right/left
+//       neighbours' x-traces come from the tile or from halo threads, the y-neighbours'
+//       traces are recomputed by each column thread from global memory
+//   a3/a7 total-flux derivative per direction with the 1D Radau correction along each
+//       line (§3.5, Eq. 24, minus sign of Eq. 12): -(1/Jx) df/dr - (1/Jy) dg/ds
+//   a4  projection of the nodal residual onto the modes (§2.1, Eq. 6)
+//   a8  SSP combination; a9 detector on density with the tensor modal basis
+//       Psi_ma(r) Psi_mb(s) Phi_k(z) (§4.2); a10 filter of flagged elements (§4.1, Eq. 34)
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "physics.cuh"
+
+namespace frsg {
+namespace {
+
+template <typename T>
+__host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int S) {
+    const int Np = n1 * n1;
+    size_t n = 0;
+    n += (size_t)TE * Np * M * S;           // U (coefficients, later the new state)
+    n += (size_t)TE * Np * S * Q;           // Un (nodal values)
+    n += (size_t)TE * Np * S * Q;           // G (nodal residual)
+    n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][s][q]
+    n += 2 * (size_t)M * Q;                 // Vz, Pz
+    n += (size_t)n1 * n1 + 4 * n1;          // D, lm, lp, dhL, dhR
+    n += (size_t)M * Np * Np;               // F (filter per gPC mode)
+    n += (size_t)2 * TE * n1 * Q;           // Red
+    return n;
+}
+
+template <typename T>
+size_t smem2d_bytes_t(int TE, int n1, int M, int Q, int S) {
+    return smem2d_elems<T>(TE, n1, M, Q, S) * sizeof(T) + (size_t)TE * sizeof(int) + 16;
+}
+
+__device__ inline double filter_strength_2d(int filter, int ma, int mb, int k, int P, int N, double alpha, double s,
+                                            double dt, double eps1, double eps2) {
+    if (filter == FRSG_FILTER_EXP) {
+        double e = 0.0;
+        if (P > 0) e += pow((double)ma / P, s) + pow((double)mb / P, s);
+        if (N > 0) e += pow((double)k / N, s);
+        return exp(-alpha * dt * e);
+    }
+    const double n1 = P + 1;
+    const double a1 = n1 > 1 ? 1.0 / (eps1 * n1 * n1 * (n1 - 1) * (n1 - 1)) : 0.0;
+    const double a2 = N > 0 ? 1.0 / (eps2 * (double)N * N * (N + 1.0) * (N + 1.0)) : 0.0;
+    return 1.0 / (1.0 + a1 * ((double)ma * ma * (ma + 1.0) * (ma + 1.0) + (double)mb * mb * (mb + 1.0) * (mb + 1.0)) +
+                  a2 * (double)k * k * (k + 1.0) * (k + 1.0));
+}
+
+__device__ inline bool detector_flags_2d(double top, double total, double s0, double kappa) {
+    if (!(total > 0.0) || !(top > 0.0)) return false;
+    const double se = log10(top / total);
+    double theta;
+    if (se < s0 - kappa) theta = 1.0;
+    else if (se > s0 + kappa) theta = 0.0;
+    else theta = 0.5 * (1.0 - sin(M_PI * (se - s0) / (2.0 * kappa)));
+    return theta < 0.99;
+}
+
+// Trace of element `e` at z-node q along a line: sum over the n1 points of the line of
+// w[i] * sum_k Phi_k(z_q) uhat[point(i)][k][s].  Row line (fixed b) or column (fixed a).
+template <typename T, int N1, int S>
+__device__ inline void line_trace(const T* ue, int M, const T* Vzq_stride, int Q, const T* w, bool column, int line,
+                                  T (&out)[S]) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) out[s] = T(0);
+    for (int k = 0; k < M; ++k) {
+        const T v = Vzq_stride[k * Q];
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const int j = column ? (i * N1 + line) : (line * N1 + i);
+            const T wv = w[i] * v;
+#pragma unroll
+            for (int s = 0; s < S; ++s) out[s] += wv * ue[(j * M + k) * S + s];
+        }
+    }
+}
+
+template <typename T, int N1, int S>
+__global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
+    constexpr int NP = N1 * N1;
+    constexpr int EQ = FRSG_EQ_EULER;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Q = A.Q, M = A.M, TE = A.TE;
+    const int tq = threadIdx.x, tl = threadIdx.y, te = threadIdx.z;
+    const int tid = (te * N1 + tl) * Q + tq, nthr = Q * N1 * TE;
+    const int nx = A.nx, ny = A.ny;
+    const int ey = blockIdx.y;
+    const int ex0 = blockIdx.x * TE;
+    const int ne = min(TE, nx - ex0);
+    const int e0 = ey * nx + ex0;
+    const int elsz = NP * M * S;
+    const T gamma = (T)A.gamma, adv = (T)A.adv;
+    const T* uin = static_cast<const T*>(A.uin);
+
+    T* p = reinterpret_cast<T*>(smem_raw);
+    T* sU = p; p += (size_t)TE * elsz;
+    T* sUn = p; p += (size_t)TE * NP * S * Q;
+    T* sG = p; p += (size_t)TE * NP * S * Q;
+    T* sTx = p; p += (size_t)(TE + 2) * 2 * N1 * S * Q;
+    T* sVz = p; p += M * Q;
+    T* sPz = p; p += M * Q;
+    T* sD = p; p += N1 * N1;
+    T* slm = p; p += N1;
+    T* slp = p; p += N1;
+    T* sdhL = p; p += N1;
+    T* sdhR = p; p += N1;
+    T* sF = p; p += (size_t)M * NP * NP;
+    T* sRed = p; p += 2 * TE * N1 * Q;
+    int* sFlag = reinterpret_cast<int*>(p);
+
+    const double* tab = A.tab;
+    for (int i = tid; i < M * Q; i += nthr) {
+        sVz[i] = (T)tab[A.off.VzT + i];
+        sPz[i] = (T)tab[A.off.Pz + i];
+    }
+    for (int i = tid; i < N1 * N1; i += nthr) sD[i] = (T)tab[A.off.D + i];
+    for (int i = tid; i < N1; i += nthr) {
+        slm[i] = (T)tab[A.off.lm + i];
+        slp[i] = (T)tab[A.off.lp + i];
+        sdhL[i] = (T)tab[A.off.dhL + i];
+        sdhR[i] = (T)tab[A.off.dhR + i];
+    }
+    if (A.do_filter) {
+        // F_k[(b,a)][(b',a')] = sum_{ma,mb} Vx[a][ma] Vx[b][mb] Lambda[ma][mb][k] Vxinv[ma][a'] Vxinv[mb][b']
+        for (int i = tid; i < M * NP * NP; i += nthr) {
+            const int k = i / (NP * NP), jo = (i / NP) % NP, ji = i % NP;
+            const int a = jo % N1, b = jo / N1, ap = ji % N1, bp = ji / N1;
+            double acc = 0.0;
+            for (int mb = 0; mb < N1; ++mb)
+                for (int ma = 0; ma < N1; ++ma)
+                    acc += tab[A.off.Vx + a * N1 + ma] * tab[A.off.Vx + b * N1 + mb] *
+                           filter_strength_2d(A.filter, ma, mb, k, N1 - 1, M - 1, A.f_alpha, A.f_s, A.dt_filter,
+                                              A.f_eps1, A.f_eps2) *
+                           tab[A.off.Vxinv + ma * N1 + ap] * tab[A.off.Vxinv + mb * N1 + bp];
+            sF[i] = (T)acc;
+        }
+    }
+    {
+        const T* src = uin + (size_t)e0 * elsz;
+        const int n = ne * elsz;
+        for (int i = tid; i < n; i += nthr) sU[i] = src[i];
+    }
+    __syncthreads();
+
+    const bool active = te < ne;
+    const int ex = ex0 + te;
+    const int e = e0 + te;
+    T u[N1][S];                     // row b = tl: values at (a, b), a = 0..N1-1
+    T ybot[S], ytop[S];             // column a = tl: neighbours' facing traces (y)
+    if (active) {
+        const T* ue = sU + te * elsz;
+        const int b = tl;
+#pragma unroll
+        for (int a = 0; a < N1; ++a)
+#pragma unroll
+            for (int s = 0; s < S; ++s) u[a][s] = T(0);
+        for (int k = 0; k < M; ++k) {
+            const T v = sVz[k * Q + tq];
+#pragma unroll
+            for (int a = 0; a < N1; ++a)
+#pragma unroll
+                for (int s = 0; s < S; ++s) u[a][s] += v * ue[((b * N1 + a) * M + k) * S + s];
+        }
+#pragma unroll
+        for (int a = 0; a < N1; ++a)
+#pragma unroll
+            for (int s = 0; s < S; ++s) sUn[((te * NP + b * N1 + a) * S + s) * Q + tq] = u[a][s];
+        // own x-traces on row b
+        T tL[S], tR[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            T l = T(0), r = T(0);
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                l += slm[a] * u[a][s];
+                r += slp[a] * u[a][s];
+            }
+            tL[s] = l;
+            tR[s] = r;
+            sTx[((((te + 1) * 2 + 0) * N1 + b) * S + s) * Q + tq] = l;
+            sTx[((((te + 1) * 2 + 1) * N1 + b) * S + s) * Q + tq] = r;
+        }
+        // x-halo on row b
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const bool edge = side == 0 ? (te == 0) : (te == ne - 1);
+            if (!edge) continue;
+            int nbx = side == 0 ? ex - 1 : ex + 1;
+            const int bc = side == 0 ? A.bc[0] : A.bc[1];
+            if ((nbx < 0 || nbx >= nx) && bc == FRSG_BC_PERIODIC) nbx = side == 0 ? nx - 1 : 0;
+            T g[S];
+            if (nbx >= 0 && nbx < nx) {
+                const T* un = uin + ((size_t)ey * nx + nbx) * elsz;
+                line_trace<T, N1, S>(un, M, sVz + tq, Q, side == 0 ? slp : slm, false, b, g);
+            } else if (bc == FRSG_BC_DIRICHLET) {
+                const double* gh = A.ghost + (size_t)side * M * S;
+#pragma unroll
+                for (int s = 0; s < S; ++s) g[s] = T(0);
+                for (int k = 0; k < M; ++k) {
+                    const T v = sVz[k * Q + tq];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) g[s] += v * (T)gh[k * S + s];
+                }
+            } else if (side == 0) {
+                ghost_from_interior<T, EQ, S, 0>(bc, tL, g);
+            } else {
+                ghost_from_interior<T, EQ, S, 0>(bc, tR, g);
+            }
+            const int row = side == 0 ? 0 : ne + 1;
+            const int nside = side == 0 ? 1 : 0;
+#pragma unroll
+            for (int s = 0; s < S; ++s) sTx[(((row * 2 + nside) * N1 + b) * S + s) * Q + tq] = g[s];
+        }
+        // y-neighbours' facing traces on column a = tl (ghosts of walls are formed later)
+        const int a = tl;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            int nby = side == 0 ? ey - 1 : ey + 1;
+            const int bc = side == 0 ? A.bc[2] : A.bc[3];
+            if ((nby < 0 || nby >= ny) && bc == FRSG_BC_PERIODIC) nby = side == 0 ? ny - 1 : 0;
+            T g[S];
+            if (nby >= 0 && nby < ny) {
+                const T* un = uin + ((size_t)nby * nx + ex) * elsz;
+                line_trace<T, N1, S>(un, M, sVz + tq, Q, side == 0 ? slp : slm, true, a, g);
+            } else if (bc == FRSG_BC_DIRICHLET) {
+                const double* gh = A.ghost + (size_t)(2 + side) * M * S;
+#pragma unroll
+                for (int s = 0; s < S; ++s) g[s] = T(0);
+                for (int k = 0; k < M; ++k) {
+                    const T v = sVz[k * Q + tq];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) g[s] += v * (T)gh[k * S + s];
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) g[s] = T(0);   // outflow / reflect: from the own trace below
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                if (side == 0) ybot[s] = g[s];
+                else ytop[s] = g[s];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- x-sweep on row b = tl
+    if (active) {
+        const int b = tl;
+        T f[N1][S];
+#pragma unroll
+        for (int a = 0; a < N1; ++a) phys_flux<T, EQ, S, 2, 0>(u[a], f[a], adv, gamma);
+        T fDL[S], fDR[S], tL[S], tR[S], nL[S], nR[S], fIL[S], fIR[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            T l = T(0), r = T(0), ul = T(0), ur = T(0);
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+                l += slm[a] * f[a][s];
+                r += slp[a] * f[a][s];
+                ul += slm[a] * u[a][s];
+                ur += slp[a] * u[a][s];
+            }
+            fDL[s] = l;
+            fDR[s] = r;
+            tL[s] = ul;
+            tR[s] = ur;
+            nL[s] = sTx[(((te * 2 + 1) * N1 + b) * S + s) * Q + tq];
+            nR[s] = sTx[((((te + 2) * 2 + 0) * N1 + b) * S + s) * Q + tq];
+        }
+        llf<T, EQ, S, 2, 0>(nL, tL, fIL, adv, gamma);
+        llf<T, EQ, S, 2, 0>(tR, nR, fIR, adv, gamma);
+        const T invJ = (T)A.invJx;
+#pragma unroll
+        for (int a = 0; a < N1; ++a)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                T d = (fIL[s] - fDL[s]) * sdhL[a] + (fIR[s] - fDR[s]) * sdhR[a];
+#pragma unroll
+                for (int m = 0; m < N1; ++m) d += sD[a * N1 + m] * f[m][s];
+                sG[((te * NP + b * N1 + a) * S + s) * Q + tq] = -invJ * d;
+            }
+    }
+    __syncthreads();
+
+    // ---- y-sweep on column a = tl
+    if (active) {
+        const int a = tl;
+        T v[N1][S];
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int s = 0; s < S; ++s) v[b][s] = sUn[((te * NP + b * N1 + a) * S + s) * Q + tq];
+        T g[N1][S];
+#pragma unroll
+        for (int b = 0; b < N1; ++b) phys_flux<T, EQ, S, 2, 1>(v[b], g[b], adv, gamma);
+        T gDB[S], gDT[S], tB[S], tT[S], gIB[S], gIT[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            T l = T(0), r = T(0), ul = T(0), ur = T(0);
+#pragma unroll
+            for (int b = 0; b < N1; ++b) {
+                l += slm[b] * g[b][s];
+                r += slp[b] * g[b][s];
+                ul += slm[b] * v[b][s];
+                ur += slp[b] * v[b][s];
+            }
+            gDB[s] = l;
+            gDT[s] = r;
+            tB[s] = ul;
+            tT[s] = ur;
+        }
+        if (ey == 0 && A.bc[2] != FRSG_BC_PERIODIC && A.bc[2] != FRSG_BC_DIRICHLET)
+            ghost_from_interior<T, EQ, S, 1>(A.bc[2], tB, ybot);
+        if (ey == ny - 1 && A.bc[3] != FRSG_BC_PERIODIC && A.bc[3] != FRSG_BC_DIRICHLET)
+            ghost_from_interior<T, EQ, S, 1>(A.bc[3], tT, ytop);
+        llf<T, EQ, S, 2, 1>(ybot, tB, gIB, adv, gamma);
+        llf<T, EQ, S, 2, 1>(tT, ytop, gIT, adv, gamma);
+        const T invJ = (T)A.invJy;
+#pragma unroll
+        for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                T d = (gIB[s] - gDB[s]) * sdhL[b] + (gIT[s] - gDT[s]) * sdhR[b];
+#pragma unroll
+                for (int m = 0; m < N1; ++m) d += sD[b * N1 + m] * g[m][s];
+                sG[((te * NP + b * N1 + a) * S + s) * Q + tq] -= invJ * d;
+            }
+    }
+    __syncthreads();
+
+    // ---- projection + SSP combination
+    const T ca = (T)A.a, cb = (T)A.b, cc = (T)A.c;
+    const T* ubase = static_cast<const T*>(A.ubase);
+    T* uout = static_cast<T*>(A.uout);
+    const size_t gbase = (size_t)e0 * elsz;
+    const int nout = ne * elsz;
+    bool bad = false;
+    for (int o = tid; o < nout; o += nthr) {
+        const int el = o / elsz, rr = o - el * elsz;
+        const int j = rr / (M * S), k = (rr / S) % M, s = rr % S;
+        const T* gq = sG + ((el * NP + j) * S + s) * Q;
+        const T* pz = sPz + k * Q;
+        T acc = T(0);
+        for (int q = 0; q < Q; ++q) acc += pz[q] * gq[q];
+        T val = cb * sU[o] + cc * acc;
+        if (ca != T(0)) val += ca * ubase[gbase + o];
+        if (A.do_filter) {
+            sU[o] = val;
+        } else {
+            uout[gbase + o] = val;
+            bad |= !finite_val(val);
+        }
+    }
+    if (A.do_filter) {
+        __syncthreads();
+        const int lt = tl * Q + tq, nlt = N1 * Q;   // thread index inside the element
+        if (active) {
+            double tot = 0.0, top = 0.0;
+            const T* ue = sU + te * elsz;
+            for (int i = lt; i < NP * M; i += nlt) {
+                const int mm = i / M, k = i % M;
+                const int ma = mm % N1, mb = mm / N1;
+                double um = 0.0;
+#pragma unroll
+                for (int b = 0; b < N1; ++b)
+#pragma unroll
+                    for (int a = 0; a < N1; ++a)
+                        um += tab[A.off.Vxinv + mb * N1 + b] * tab[A.off.Vxinv + ma * N1 + a] *
+                              (double)ue[((b * N1 + a) * M + k) * S];
+                tot += um * um;
+                if (ma == N1 - 1 || mb == N1 - 1 || k == M - 1) top += um * um;
+            }
+            sRed[(te * nlt + lt) * 2 + 0] = (T)tot;
+            sRed[(te * nlt + lt) * 2 + 1] = (T)top;
+        }
+        __syncthreads();
+        if (active && lt == 0) {
+            double tot = 0.0, top = 0.0;
+            for (int i = 0; i < nlt; ++i) {
+                tot += (double)sRed[(te * nlt + i) * 2 + 0];
+                top += (double)sRed[(te * nlt + i) * 2 + 1];
+            }
+            int fl;
+            if (A.replay) fl = A.replay[e] ? 1 : 0;
+            else if (!A.sensor) fl = 1;
+            else fl = detector_flags_2d(top, tot, A.s0, A.kappa) ? 1 : 0;
+            sFlag[te] = fl;
+            if (A.flags) A.flags[e] = (uint8_t)fl;
+        }
+        __syncthreads();
+        for (int o = tid; o < nout; o += nthr) {
+            const int el = o / elsz, rr = o - el * elsz;
+            T val;
+            if (sFlag[el]) {
+                const int j = rr / (M * S), k = (rr / S) % M, s = rr % S;
+                const T* Fk = sF + ((size_t)k * NP + j) * NP;
+                const T* ue = sU + el * elsz + k * S + s;
+                val = T(0);
+#pragma unroll
+                for (int jp = 0; jp < NP; ++jp) val += Fk[jp] * ue[jp * M * S];
+            } else {
+                val = sU[o];
+            }
+            uout[gbase + o] = val;
+            bad |= !finite_val(val);
+        }
+    }
+    if (bad) atomicOr(A.err, kErrNonFinite);
+}
+
+template <typename T, int N1>
+cudaError_t launch2d_typed(const StageArgs& A, cudaStream_t st) {
+    const int TE = A.TE;
+    const size_t smem = smem2d_bytes_t<T>(TE, N1, A.M, A.Q, 4);
+    auto kern = stage2d_kernel<T, N1, 4>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 block(A.Q, N1, TE);
+    dim3 grid((A.nx + TE - 1) / TE, A.ny);
+    kern<<<grid, block, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch2d_np(const frsg_config& cfg, const StageArgs& A, cudaStream_t st) {
+    switch (cfg.P + 1) {
+        case 2: return launch2d_typed<T, 2>(A, st);
+        case 3: return launch2d_typed<T, 3>(A, st);
+        case 4: return launch2d_typed<T, 4>(A, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S) {
+    return fp64 ? smem2d_bytes_t<double>(TE, n1, M, Q, S) : smem2d_bytes_t<float>(TE, n1, M, Q, S);
+}
+
+cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st) {
+    if (cfg.equation != FRSG_EQ_EULER) return cudaErrorInvalidValue;
+    return fp64 ? launch2d_np<double>(cfg, A, st) : launch2d_np<float>(cfg, A, st);
+}
+
+}  // namespace frsg

@@ -1,0 +1,341 @@
+// Positivity limiter (§4.3), initial projection (§2.1), moments, time-step reduction and
+// precision conversion kernels.  The limiter, the reduction and the moments run in
+// double for either state precision.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "physics.cuh"
+
+namespace frsg {
+namespace {
+
+template <typename T>
+__device__ inline double ld(const T* p, size_t i) { return (double)p[i]; }
+
+// Euler pressure for 1D (S = 3) or 2D (S = 4) conserved states.
+template <int S>
+__device__ inline double pressure_d(const double* u, double gamma) {
+    double m2 = 0.0;
+#pragma unroll
+    for (int d = 1; d < S - 1; ++d) m2 += u[d] * u[d];
+    return (gamma - 1.0) * (u[S - 1] - 0.5 * m2 / u[0]);
+}
+
+// Smallest beta in [0, 1] with p(ubar + beta (ustar - ubar)) = eps (§4.3, Eq. 51).
+// rho p / (gamma - 1) = rho E - |m|^2 / 2 is quadratic in beta along the segment:
+// a beta^2 + b beta + c = 0 with c >= 0 at beta = 0 and a negative value at beta = 1.
+template <int S>
+__device__ inline double pressure_root(const double* ub, const double* us, double eps, double gamma) {
+    const double g1 = gamma - 1.0;
+    double d[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) d[s] = us[s] - ub[s];
+    double mm = 0.0, md = 0.0, dd = 0.0;
+#pragma unroll
+    for (int s = 1; s < S - 1; ++s) {
+        mm += ub[s] * ub[s];
+        md += ub[s] * d[s];
+        dd += d[s] * d[s];
+    }
+    const double a = g1 * (d[S - 1] * d[0] - 0.5 * dd);
+    const double b = g1 * (ub[S - 1] * d[0] + ub[0] * d[S - 1] - md) - eps * d[0];
+    const double c = g1 * (ub[S - 1] * ub[0] - 0.5 * mm) - eps * ub[0];
+    double beta;
+    if (fabs(a) < 1e-300) {
+        beta = -c / b;
+    } else {
+        const double disc = fmax(b * b - 4.0 * a * c, 0.0);
+        const double qq = -0.5 * (b + copysign(sqrt(disc), b));
+        const double r1 = qq / a;
+        const double r2 = qq != 0.0 ? c / qq : r1;
+        const bool ok1 = r1 >= 0.0 && r1 <= 1.0, ok2 = r2 >= 0.0 && r2 <= 1.0;
+        if (ok1 && ok2) beta = fmin(r1, r2);
+        else if (ok1) beta = r1;
+        else if (ok2) beta = r2;
+        else {
+            // both just outside [0, 1] by rounding: take the one nearest to the interval
+            const double d1 = fmin(fabs(r1), fabs(r1 - 1.0)), d2 = fmin(fabs(r2), fabs(r2 - 1.0));
+            beta = d1 < d2 ? r1 : r2;
+        }
+    }
+    return fmin(fmax(beta, 0.0), 1.0);
+}
+
+// Block (Q, TE): thread (q, te) owns z-node q of element te.
+template <typename T, int NPT, int S>
+__global__ void limit_kernel(const LimitArgs A) {
+    extern __shared__ double lsm[];
+    const int Q = A.Q, M = A.M, TE = A.TE, NL = A.off.NL;
+    const int tq = threadIdx.x, te = threadIdx.y;
+    const int e = blockIdx.x * TE + te;
+    const bool active = e < A.E;
+    double* un = lsm + (size_t)te * NPT * S * Q;          // nodal values [j][s][q]
+    double* red = lsm + (size_t)TE * NPT * S * Q;         // [TE][Q][2]
+    double* el = red + (size_t)TE * Q * 2;                // [TE][4]: rho_min, p_min, beta1, beta2
+    T* u = static_cast<T*>(A.u);
+    const size_t elsz = (size_t)NPT * M * S;
+    const double* tab = A.tab;
+    const double gamma = A.gamma;
+
+    double ubar[S];
+    double rho_bar = 1.0, p_bar = 1.0, eps = 0.0;
+    bool admissible = true;
+    double rmin = 1e300, pmin = 1e300;
+    if (active) {
+        const T* ue = u + (size_t)e * elsz;
+#pragma unroll
+        for (int s = 0; s < S; ++s) ubar[s] = 0.0;
+        for (int j = 0; j < NPT; ++j) {
+            const double wj = tab[A.off.w + j];
+#pragma unroll
+            for (int s = 0; s < S; ++s) ubar[s] += wj * ld(ue, (size_t)j * M * S + s);
+        }
+        rho_bar = ubar[0];
+        p_bar = pressure_d<S>(ubar, gamma);
+        admissible = rho_bar > 0.0 && p_bar > 0.0;
+        eps = fmin(1e-8, fmin(rho_bar, p_bar));
+        for (int j = 0; j < NPT; ++j)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                double acc = 0.0;
+                for (int k = 0; k < M; ++k) acc += tab[A.off.VzT + k * Q + tq] * ld(ue, ((size_t)j * M + k) * S + s);
+                un[(j * S + s) * Q + tq] = acc;
+            }
+        for (int l = 0; l < NL; ++l) {
+            double ul[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                double acc = 0.0;
+                for (int j = 0; j < NPT; ++j) acc += tab[A.off.Lpts + l * NPT + j] * un[(j * S + s) * Q + tq];
+                ul[s] = acc;
+            }
+            rmin = fmin(rmin, ul[0]);
+            pmin = fmin(pmin, pressure_d<S>(ul, gamma));
+        }
+        red[(te * Q + tq) * 2 + 0] = rmin;
+        red[(te * Q + tq) * 2 + 1] = pmin;
+    }
+    __syncthreads();
+    if (active && tq == 0) {
+        double a = 1e300, b = 1e300;
+        for (int i = 0; i < Q; ++i) {
+            a = fmin(a, red[(te * Q + i) * 2 + 0]);
+            b = fmin(b, red[(te * Q + i) * 2 + 1]);
+        }
+        el[te * 4 + 0] = a;
+        el[te * 4 + 1] = b;
+        double beta1 = 1.0;
+        if (rho_bar - a > 0.0) beta1 = fmin((rho_bar - eps) / (rho_bar - a), 1.0);
+        el[te * 4 + 2] = beta1;
+        if (!admissible) atomicOr(A.err, kErrPositivity);
+        if (!(a == a) || !(b == b)) atomicOr(A.err, kErrNonFinite);
+    }
+    __syncthreads();
+    const bool trig = active && admissible && fmin(el[te * 4 + 0], el[te * 4 + 1]) < eps;
+    if (trig) {
+        const double beta1 = el[te * 4 + 2];
+        double bmin = 1.0;
+        for (int l = 0; l < NL; ++l) {
+            double ul[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                double acc = 0.0;
+                for (int j = 0; j < NPT; ++j) acc += tab[A.off.Lpts + l * NPT + j] * un[(j * S + s) * Q + tq];
+                ul[s] = acc;
+            }
+            ul[0] = beta1 * (ul[0] - rho_bar) + rho_bar;
+            if (pressure_d<S>(ul, gamma) < eps) bmin = fmin(bmin, pressure_root<S>(ubar, ul, eps, gamma));
+        }
+        red[(te * Q + tq) * 2 + 0] = bmin;
+    }
+    __syncthreads();
+    if (trig && tq == 0) {
+        double b2 = 1.0;
+        for (int i = 0; i < Q; ++i) b2 = fmin(b2, red[(te * Q + i) * 2 + 0]);
+        el[te * 4 + 3] = b2;
+    }
+    __syncthreads();
+    if (active && A.beta && tq == 0) A.beta[e] = trig ? el[te * 4 + 2] * el[te * 4 + 3] : 1.0;
+    if (trig) {
+        // uhat <- ubar e_0 + scale (uhat - ubar e_0); density scaled by beta2*beta1, the rest by beta2
+        const double beta1 = el[te * 4 + 2], beta2 = el[te * 4 + 3];
+        T* ue = u + (size_t)e * elsz;
+        for (size_t o = tq; o < elsz; o += Q) {
+            const int s = (int)(o % S), k = (int)((o / S) % M);
+            const double sc = s == 0 ? beta2 * beta1 : beta2;
+            const double mean = k == 0 ? ubar[s] : 0.0;
+            ue[o] = (T)(mean + sc * (ld(ue, o) - mean));
+        }
+    }
+}
+
+__global__ void project_kernel_d(const double* u0, double* uhat, int E, int Np, int M, int Q, int S,
+                                 const double* Pz) {
+    const size_t n = (size_t)E * Np * M * S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = i % S, k = (i / S) % M;
+        const size_t ej = i / ((size_t)S * M);
+        double acc = 0.0;
+        for (int q = 0; q < Q; ++q) acc += Pz[k * Q + q] * u0[(ej * Q + q) * S + s];
+        uhat[i] = acc;
+    }
+}
+
+__global__ void project_kernel_f(const double* u0, float* uhat, int E, int Np, int M, int Q, int S,
+                                 const double* Pz) {
+    const size_t n = (size_t)E * Np * M * S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = i % S, k = (i / S) % M;
+        const size_t ej = i / ((size_t)S * M);
+        double acc = 0.0;
+        for (int q = 0; q < Q; ++q) acc += Pz[k * Q + q] * u0[(ej * Q + q) * S + s];
+        uhat[i] = (float)acc;
+    }
+}
+
+template <typename T>
+__global__ void moments_kernel(const T* uhat, double* mean, double* var, int E, int Np, int M, int S) {
+    const size_t n = (size_t)E * Np * S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = i % S;
+        const size_t ej = i / S;
+        const T* p = uhat + ej * M * S + s;
+        mean[i] = (double)p[0];
+        double v = 0.0;
+        for (int k = 1; k < M; ++k) {
+            const double c = (double)p[k * S];
+            v += c * c;
+        }
+        var[i] = v;
+    }
+}
+
+template <typename T, int EQ, int S, int DIM>
+__global__ void max_speed_kernel(const T* uhat, int E, int Np, int M, int Q, double adv, double gamma,
+                                 const double* VzT, unsigned long long* out) {
+    const size_t n = (size_t)E * Np * Q;
+    double best = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int q = i % Q;
+        const size_t ej = i / Q;
+        double u[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            double acc = 0.0;
+            for (int k = 0; k < M; ++k) acc += VzT[k * Q + q] * (double)uhat[(ej * M + k) * S + s];
+            u[s] = acc;
+        }
+        double lam = wave_speed<double, EQ, S, DIM, 0>(u, adv, gamma);
+        if constexpr (DIM == 2) lam = fmax(lam, wave_speed<double, EQ, S, DIM, 1>(u, adv, gamma));
+        best = (lam == lam) ? fmax(best, lam) : lam;
+        if (!(best == best)) break;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = (other == other && best == best) ? fmax(best, other) : (best == best ? other : best);
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, best);
+}
+
+__global__ void convert_kernel(const void* src, void* dst, size_t n, int to_float) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (to_float) static_cast<float*>(dst)[i] = (float)static_cast<const double*>(src)[i];
+        else static_cast<double*>(dst)[i] = (double)static_cast<const float*>(src)[i];
+    }
+}
+
+int grid_for(size_t n, int threads) {
+    size_t g = (n + threads - 1) / threads;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename T, int NPT, int S>
+cudaError_t limit_typed(const LimitArgs& A, cudaStream_t st) {
+    const size_t smem = sizeof(double) * ((size_t)A.TE * NPT * S * A.Q + (size_t)A.TE * A.Q * 2 + (size_t)A.TE * 4);
+    auto kern = limit_kernel<T, NPT, S>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 block(A.Q, A.TE);
+    dim3 grid((A.E + A.TE - 1) / A.TE);
+    kern<<<grid, block, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t limit_np(const LimitArgs& A, cudaStream_t st) {
+    if (A.dim == 1) {
+        switch (A.Np) {
+            case 2: return limit_typed<T, 2, 3>(A, st);
+            case 3: return limit_typed<T, 3, 3>(A, st);
+            case 4: return limit_typed<T, 4, 3>(A, st);
+            case 5: return limit_typed<T, 5, 3>(A, st);
+        }
+    } else {
+        switch (A.Np) {
+            case 4: return limit_typed<T, 4, 4>(A, st);
+            case 9: return limit_typed<T, 9, 4>(A, st);
+            case 16: return limit_typed<T, 16, 4>(A, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t max_speed_typed(const void* uhat, int E, int Np, int M, int Q, int S, int dim, int eq, double adv,
+                            double gamma, const double* VzT, unsigned long long* out, cudaStream_t st) {
+    const size_t n = (size_t)E * Np * Q;
+    const int g = grid_for(n, 256);
+    const T* u = static_cast<const T*>(uhat);
+    if (eq == FRSG_EQ_ADVECTION)
+        max_speed_kernel<T, FRSG_EQ_ADVECTION, 1, 1><<<g, 256, 0, st>>>(u, E, Np, M, Q, adv, gamma, VzT, out);
+    else if (eq == FRSG_EQ_BURGERS)
+        max_speed_kernel<T, FRSG_EQ_BURGERS, 1, 1><<<g, 256, 0, st>>>(u, E, Np, M, Q, adv, gamma, VzT, out);
+    else if (dim == 1)
+        max_speed_kernel<T, FRSG_EQ_EULER, 3, 1><<<g, 256, 0, st>>>(u, E, Np, M, Q, adv, gamma, VzT, out);
+    else
+        max_speed_kernel<T, FRSG_EQ_EULER, 4, 2><<<g, 256, 0, st>>>(u, E, Np, M, Q, adv, gamma, VzT, out);
+    (void)S;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_limit(bool fp64, const LimitArgs& A, cudaStream_t st) {
+    return fp64 ? limit_np<double>(A, st) : limit_np<float>(A, st);
+}
+
+cudaError_t launch_project(bool fp64, const double* u0, void* uhat, int E, int Np, int M, int Q, int S,
+                           const double* tab, TabOff off, cudaStream_t st) {
+    const size_t n = (size_t)E * Np * M * S;
+    const int g = grid_for(n, 256);
+    if (fp64) project_kernel_d<<<g, 256, 0, st>>>(u0, static_cast<double*>(uhat), E, Np, M, Q, S, tab + off.Pz);
+    else project_kernel_f<<<g, 256, 0, st>>>(u0, static_cast<float*>(uhat), E, Np, M, Q, S, tab + off.Pz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(bool fp64, const void* uhat, double* mean, double* var, int E, int Np, int M, int S,
+                           cudaStream_t st) {
+    const size_t n = (size_t)E * Np * S;
+    const int g = grid_for(n, 256);
+    if (fp64) moments_kernel<double><<<g, 256, 0, st>>>(static_cast<const double*>(uhat), mean, var, E, Np, M, S);
+    else moments_kernel<float><<<g, 256, 0, st>>>(static_cast<const float*>(uhat), mean, var, E, Np, M, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_speed(bool fp64, const void* uhat, int E, int Np, int M, int Q, int S, int dim,
+                             int equation, double adv, double gamma, const double* tab, TabOff off,
+                             unsigned long long* out_bits, cudaStream_t st) {
+    return fp64 ? max_speed_typed<double>(uhat, E, Np, M, Q, S, dim, equation, adv, gamma, tab + off.VzT, out_bits, st)
+                : max_speed_typed<float>(uhat, E, Np, M, Q, S, dim, equation, adv, gamma, tab + off.VzT, out_bits, st);
+}
+
+cudaError_t launch_convert(const void* src, void* dst, size_t n, bool to_float, cudaStream_t st) {
+    convert_kernel<<<grid_for(n, 256), 256, 0, st>>>(src, dst, n, to_float ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace frsg

@@ -1,0 +1,94 @@
+// Device physics of the FR-SG stage: pointwise fluxes (§3.2, Eq. 15; Euler §5.3-5.4),
+// flux-Jacobian spectral radius, local Lax-Friedrichs interface flux (§3.3).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "frsg.h"
+
+namespace frsg {
+
+// Physical flux along direction DIR (0 = x, 1 = y) of equation EQ with S variables.
+template <typename T, int EQ, int S, int DIM, int DIR>
+__device__ __forceinline__ void phys_flux(const T (&u)[S], T (&f)[S], T adv, T gamma) {
+    if constexpr (EQ == FRSG_EQ_ADVECTION) {
+        f[0] = adv * u[0];
+    } else if constexpr (EQ == FRSG_EQ_BURGERS) {
+        f[0] = T(0.5) * u[0] * u[0];
+    } else if constexpr (DIM == 1) {
+        const T rho = u[0], m = u[1], E = u[2];
+        const T v = m / rho;
+        const T p = (gamma - T(1)) * (E - T(0.5) * m * v);
+        f[0] = m;
+        f[1] = m * v + p;
+        f[2] = (E + p) * v;
+    } else {
+        const T rho = u[0], mx = u[1], my = u[2], E = u[3];
+        const T vx = mx / rho, vy = my / rho;
+        const T p = (gamma - T(1)) * (E - T(0.5) * (mx * vx + my * vy));
+        const T vn = DIR == 0 ? vx : vy;
+        f[0] = rho * vn;
+        f[1] = mx * vn;
+        f[2] = my * vn;
+        f[3] = (E + p) * vn;
+        f[1 + DIR] += p;
+    }
+}
+
+template <typename T, int EQ, int S, int DIM, int DIR>
+__device__ __forceinline__ T wave_speed(const T (&u)[S], T adv, T gamma) {
+    if constexpr (EQ == FRSG_EQ_ADVECTION) {
+        return fabs(adv);
+    } else if constexpr (EQ == FRSG_EQ_BURGERS) {
+        return fabs(u[0]);
+    } else if constexpr (DIM == 1) {
+        const T rho = u[0], m = u[1], E = u[2];
+        const T v = m / rho;
+        const T p = (gamma - T(1)) * (E - T(0.5) * m * v);
+        return fabs(v) + sqrt(gamma * p / rho);
+    } else {
+        const T rho = u[0], mx = u[1], my = u[2], E = u[3];
+        const T vx = mx / rho, vy = my / rho;
+        const T p = (gamma - T(1)) * (E - T(0.5) * (mx * vx + my * vy));
+        return fabs(DIR == 0 ? vx : vy) + sqrt(gamma * p / rho);
+    }
+}
+
+// f^I = (f(uL) + f(uR))/2 - alpha (uR - uL)/2, alpha = max(lambda(uL), lambda(uR)).
+template <typename T, int EQ, int S, int DIM, int DIR>
+__device__ __forceinline__ void llf(const T (&uL)[S], const T (&uR)[S], T (&fI)[S], T adv, T gamma) {
+    T fL[S], fR[S];
+    phys_flux<T, EQ, S, DIM, DIR>(uL, fL, adv, gamma);
+    phys_flux<T, EQ, S, DIM, DIR>(uR, fR, adv, gamma);
+    const T a = fmax(wave_speed<T, EQ, S, DIM, DIR>(uL, adv, gamma),
+                     wave_speed<T, EQ, S, DIM, DIR>(uR, adv, gamma));
+#pragma unroll
+    for (int s = 0; s < S; ++s) fI[s] = T(0.5) * (fL[s] + fR[s]) - T(0.5) * a * (uR[s] - uL[s]);
+}
+
+// Ghost state of a non-periodic side from the interior trace (nodal in z at one node).
+// Dirichlet ghosts are evaluated by the caller from the projected boundary modes.
+template <typename T, int EQ, int S, int DIR>
+__device__ __forceinline__ void ghost_from_interior(int bc, const T (&in)[S], T (&g)[S]) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) g[s] = in[s];
+    if (bc == FRSG_BC_REFLECT) {
+        if constexpr (EQ == FRSG_EQ_EULER) {
+            g[1 + DIR] = -g[1 + DIR];
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) g[s] = -g[s];
+        }
+    }
+}
+
+__device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
+
+// Max of non-negative doubles through their IEEE bit patterns (order-preserving for >= 0).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+    if (!(v >= 0.0)) v = __longlong_as_double(0x7ff8000000000000ULL);   // NaN wins
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace frsg

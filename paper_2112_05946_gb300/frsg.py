@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libfrsg (include/frsg.h).  Argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts Python values
+into the C structures and pointers the C ABI expects, and turns non-zero status
+codes into exceptions.  Device buffers are torch tensors (their data_ptr is passed),
+host buffers are numpy arrays.  The library must have been built (build.build());
+importing this module on a machine without it raises instead of falling back.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfrsg.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_POSITIVITY, E_TIMEOUT, E_UNSUPPORTED = range(8)
+BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
+EQUATION = {"advection": 0, "burgers": 1, "euler": 2}
+FILTER = {"none": 0, "exp": 1, "l2": 2}
+PRECISION = {"fp64": 0, "fp32": 1}
+HOST, DEVICE = 0, 1
+
+
+class FrsgError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"frsg status {status}: {message}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("dim", ctypes.c_int32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 4),
+        ("P", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("Q", ctypes.c_int32),
+        ("equation", ctypes.c_int32),
+        ("adv_speed", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("filter", ctypes.c_int32),
+        ("sensor", ctypes.c_int32),
+        ("f_alpha", ctypes.c_double), ("f_s", ctypes.c_double),
+        ("f_eps1", ctypes.c_double), ("f_eps2", ctypes.c_double),
+        ("s0", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("limiter", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point in include/frsg.h
+_SIGNATURES = [
+    ("fr_sg_init", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("fr_sg_destroy", None, [ctypes.c_void_p]),
+    ("fr_sg_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("fr_sg_sizes", ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 5),
+    ("fr_sg_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("fr_sg_get_nodes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fr_sg_set_boundary_nodal", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("fr_sg_set_initial_nodal", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fr_sg_rk_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_stage", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    ("fr_sg_filter", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    ("fr_sg_limit", ctypes.c_int, [ctypes.c_void_p]),
+    ("fr_sg_moments", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_cfl_dt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    ("fr_sg_get_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fr_sg_set_replay", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_check", ctypes.c_int, [ctypes.c_void_p]),
+    ("fr_sg_launch_count", ctypes.c_uint64, [ctypes.c_void_p]),
+    ("fr_sg_set_tile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+]
+
+
+def load_library(path=LIB_PATH):
+    """Load libfrsg.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: build it with paper_2112_05946_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_names():
+    return [s[0] for s in _SIGNATURES]
+
+
+def make_config(dim=1, nx=32, ny=1, x0=0.0, x1=2.0, y0=0.0, y1=1.0, bc=("periodic",) * 4, P=2, N=4, Q=8,
+                equation="advection", adv_speed=1.0, gamma=1.4, filter="none", sensor=True, f_alpha=36.0,
+                f_s=4.0, f_eps1=0.6, f_eps2=0.6, s0=0.0, kappa=4.0, limiter=False, precision="fp64"):
+    c = Config()
+    c.struct_size = ctypes.sizeof(Config)
+    c.dim, c.nx, c.ny = dim, nx, ny
+    c.x0, c.x1, c.y0, c.y1 = x0, x1, y0, y1
+    for i, b in enumerate(bc):
+        c.bc[i] = BC[b] if isinstance(b, str) else int(b)
+    c.P, c.N, c.Q = P, N, Q
+    c.equation = EQUATION[equation]
+    c.adv_speed, c.gamma = adv_speed, gamma
+    c.filter = FILTER[filter]
+    c.sensor = int(bool(sensor))
+    c.f_alpha, c.f_s, c.f_eps1, c.f_eps2, c.s0, c.kappa = f_alpha, f_s, f_eps1, f_eps2, s0, kappa
+    c.limiter = int(bool(limiter))
+    c.precision = PRECISION[precision]
+    return c
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data
+    return a.data_ptr()   # torch tensor
+
+
+class Solver:
+    """One FR-SG context (fr_sg_init ... fr_sg_destroy)."""
+
+    def __init__(self, stream=None, **cfg):
+        self.lib = load_library()
+        self.cfg_kwargs = dict(cfg)
+        self.cfg = make_config(**cfg)
+        h = ctypes.c_void_p()
+        st = self.lib.fr_sg_init(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != OK:
+            raise FrsgError(st, "fr_sg_init rejected the configuration (details on stderr)")
+        self.h = h
+        E, Np, M, S, Q = (ctypes.c_int() for _ in range(5))
+        self.lib.fr_sg_sizes(self.h, ctypes.byref(E), ctypes.byref(Np), ctypes.byref(M), ctypes.byref(S),
+                             ctypes.byref(Q))
+        self.E, self.Np, self.M, self.S, self.Q = E.value, Np.value, M.value, S.value, Q.value
+        self.fp64 = self.cfg.precision == 0
+
+    # ------------------------------------------------------------------ plumbing
+    def _ck(self, st, what):
+        if st != OK:
+            msg = self.lib.fr_sg_last_error(self.h)
+            raise FrsgError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fr_sg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def state_shape(self):
+        return (self.E, self.Np, self.M, self.S)
+
+    def set_stream(self, stream):
+        self._ck(self.lib.fr_sg_set_stream(self.h, ctypes.c_void_p(stream or 0)), "set_stream")
+
+    # ------------------------------------------------------------------ data
+    def nodes(self):
+        x = np.zeros((self.E, self.Np))
+        y = np.zeros((self.E, self.Np))
+        z = np.zeros(self.Q)
+        self._ck(self.lib.fr_sg_get_nodes(self.h, _ptr(x), _ptr(y), _ptr(z)), "get_nodes")
+        return (x, z) if self.cfg.dim == 1 else (x, y, z)
+
+    def set_boundary_nodal(self, side, g):
+        g = np.ascontiguousarray(g, dtype=np.float64).reshape(self.Q, self.S)
+        self._ck(self.lib.fr_sg_set_boundary_nodal(self.h, side, _ptr(g)), "set_boundary_nodal")
+
+    def set_initial_nodal(self, u0):
+        if isinstance(u0, np.ndarray):
+            u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(self.E, self.Np, self.Q, self.S)
+            self._ck(self.lib.fr_sg_set_initial_nodal(self.h, _ptr(u0), HOST), "set_initial_nodal")
+        else:
+            self._ck(self.lib.fr_sg_set_initial_nodal(self.h, _ptr(u0), DEVICE), "set_initial_nodal")
+
+    def set_state(self, uhat):
+        if isinstance(uhat, np.ndarray):
+            uhat = np.ascontiguousarray(uhat, dtype=np.float64).reshape(self.state_shape)
+            self._ck(self.lib.fr_sg_set_state(self.h, _ptr(uhat), HOST), "set_state")
+        else:
+            self._ck(self.lib.fr_sg_set_state(self.h, _ptr(uhat), DEVICE), "set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros(self.state_shape)
+            self._ck(self.lib.fr_sg_get_state(self.h, _ptr(out), HOST), "get_state")
+            return out
+        if isinstance(out, np.ndarray):
+            self._ck(self.lib.fr_sg_get_state(self.h, _ptr(out), HOST), "get_state")
+        else:
+            self._ck(self.lib.fr_sg_get_state(self.h, _ptr(out), DEVICE), "get_state")
+        return out
+
+    # ------------------------------------------------------------------ compute
+    def rhs(self, u, dudt):
+        """u, dudt: device tensors of the context's precision, shape [E, Np, M, S]."""
+        self._ck(self.lib.fr_sg_rhs(self.h, _ptr(u), _ptr(dudt)), "rhs")
+
+    def rk_step(self, dt, nsteps=1, graph=True):
+        self._ck(self.lib.fr_sg_rk_step(self.h, float(dt), int(nsteps), int(bool(graph))), "rk_step")
+
+    def stage(self, stage, dt):
+        self._ck(self.lib.fr_sg_stage(self.h, int(stage), float(dt)), "stage")
+
+    def filter(self, dt):
+        self._ck(self.lib.fr_sg_filter(self.h, float(dt)), "filter")
+
+    def limit(self):
+        self._ck(self.lib.fr_sg_limit(self.h), "limit")
+
+    def moments(self, mean=None, var=None):
+        if mean is None:
+            mean = np.zeros((self.E, self.Np, self.S))
+            var = np.zeros((self.E, self.Np, self.S))
+            self._ck(self.lib.fr_sg_moments(self.h, _ptr(mean), _ptr(var), HOST), "moments")
+        else:
+            where = HOST if isinstance(mean, np.ndarray) else DEVICE
+            self._ck(self.lib.fr_sg_moments(self.h, _ptr(mean), _ptr(var), where), "moments")
+        return mean, var
+
+    def cfl_dt(self, cfl):
+        dt = ctypes.c_double()
+        self._ck(self.lib.fr_sg_cfl_dt(self.h, float(cfl), ctypes.byref(dt)), "cfl_dt")
+        return dt.value
+
+    def decisions(self):
+        flags = np.zeros((3, self.E), dtype=np.uint8)
+        beta = np.zeros((3, self.E))
+        self._ck(self.lib.fr_sg_get_decisions(self.h, _ptr(flags), _ptr(beta)), "get_decisions")
+        return flags.astype(bool), beta
+
+    def set_replay(self, flags):
+        if flags is None:
+            self._ck(self.lib.fr_sg_set_replay(self.h, None, 0), "set_replay")
+            return
+        f = np.ascontiguousarray(np.asarray(flags, dtype=np.uint8).reshape(-1, self.E))
+        self._ck(self.lib.fr_sg_set_replay(self.h, _ptr(f), f.shape[0]), "set_replay")
+
+    def check(self):
+        self._ck(self.lib.fr_sg_check(self.h), "check")
+
+    def set_tile(self, te):
+        """Elements per CTA of the stage kernel (0 = automatic); returns the tile in use."""
+        out = ctypes.c_int()
+        self._ck(self.lib.fr_sg_set_tile(self.h, int(te), ctypes.byref(out)), "set_tile")
+        return out.value
+
+    def launch_count(self):
+        return int(self.lib.fr_sg_launch_count(self.h))

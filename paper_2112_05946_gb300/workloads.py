@@ -1,0 +1,160 @@
+"""Seeded synthetic workloads: the problem definitions both the CUDA path and the
+oracle are run on.
+
+This module holds problem data only - mesh, orders, equation and capturing
+parameters, initial and boundary data as functions of (x, z) or (x, y, z), and seeded
+random coefficient generators.  It contains none of the scheme's arithmetic: each
+side evaluates these functions at its own nodes and projects them itself.
+
+The five workloads follow the paper's experiment families (§5.1 advection, §5.2
+Burgers, §5.3 Sod, §5.4 shock-vortex) at the sizes of the benchmark configurations.
+"""
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def advection_1d():
+    """u_t + u_x = 0 on periodic [0, 2], u0 = 1 + 0.5 sin(pi (x + 0.2 z)), z ~ U(-1, 1);
+    P = 2, 32 elements, N = 4, Q = 8, LLF, CFL 0.1, t_end = 2."""
+    return dict(
+        name="advection_E32_P2_N4_Q8",
+        solver=dict(dim=1, nx=32, x0=0.0, x1=2.0, bc=("periodic",) * 4, P=2, N=4, Q=8,
+                    equation="advection", adv_speed=1.0, filter="none"),
+        ic=lambda x, z: (1.0 + 0.5 * np.sin(np.pi * (x + 0.2 * z)))[..., None],
+        exact=lambda t: (lambda x, z: (1.0 + 0.5 * np.sin(np.pi * (x - t + 0.2 * z)))[..., None]),
+        cfl=0.1, t_end=2.0, lam0=1.0,
+    )
+
+
+def burgers_1d(nx=1024, P=3, N=8, Q=16):
+    """u_t + (u^2/2)_x = 0 on periodic [0, 2], u0 = sin(pi x) + 0.1 z; P = 3, 1024 elements,
+    N = 8, Q = 16, detector + exponential filter (alpha = 36, order 4) in x and z,
+    s0 = -2 log10(P) (§5.2 table with N_p - 1 = P), kappa = 4, t_end = 1."""
+    return dict(
+        name=f"burgers_E{nx}_P{P}_N{N}_Q{Q}",
+        solver=dict(dim=1, nx=nx, x0=0.0, x1=2.0, bc=("periodic",) * 4, P=P, N=N, Q=Q,
+                    equation="burgers", filter="exp", sensor=True, f_alpha=36.0, f_s=4.0,
+                    s0=-2.0 * math.log10(P), kappa=4.0),
+        ic=lambda x, z: (np.sin(np.pi * x) + 0.1 * z)[..., None],
+        cfl=0.1, t_end=1.0, lam0=1.1,
+    )
+
+
+def _sod_state(x, z, left):
+    rho = (1.0 + 0.1 * z) * np.ones_like(x) if left else 0.125 * np.ones_like(x)
+    p = (1.0 if left else 0.1) * np.ones_like(x)
+    return np.stack([rho, 0.0 * x, p / (GAMMA - 1.0)], axis=-1)
+
+
+def sod_1d(nx=4096, P=3, N=6, Q=12):
+    """Stochastic Sod tube (§5.3, first case): x in [0, 1], rho_L = 1 + 0.1 z, u = 0,
+    p_L = 1; rho_R = 0.125, p_R = 0.1; interface at 0.5; Dirichlet ends holding the
+    initial states; P = 3, 4096 elements, N = 6, Q = 12; detector + exponential filter
+    (alpha = 36, order 4, s0 = -3 log10 P, kappa = 4) and the positivity limiter; t_end = 0.2."""
+    def ic(x, z):
+        left = _sod_state(x, z, True)
+        right = _sod_state(x, z, False)
+        return np.where((x < 0.5)[..., None], left, right)
+
+    return dict(
+        name=f"sod_E{nx}_P{P}_N{N}_Q{Q}",
+        solver=dict(dim=1, nx=nx, x0=0.0, x1=1.0, bc=("dirichlet", "dirichlet", "periodic", "periodic"),
+                    P=P, N=N, Q=Q, equation="euler", gamma=GAMMA, filter="exp", sensor=True,
+                    f_alpha=36.0, f_s=4.0, s0=-3.0 * math.log10(P), kappa=4.0, limiter=True),
+        ic=ic,
+        boundary={0: lambda z: _sod_state(np.zeros(1), z, True)[0],
+                  1: lambda z: _sod_state(np.zeros(1), z, False)[0]},
+        cfl=0.1, t_end=0.2, lam0=None,
+    )
+
+
+def _rh_downstream(ma, rho1=1.0, p1=1.0):
+    """Normal-shock jump for upstream Mach number ma (stationary shock, ideal gas)."""
+    g = GAMMA
+    c1 = math.sqrt(g * p1 / rho1)
+    u1 = ma * c1
+    rho2 = rho1 * (g + 1.0) * ma * ma / ((g - 1.0) * ma * ma + 2.0)
+    p2 = p1 * (1.0 + 2.0 * g / (g + 1.0) * (ma * ma - 1.0))
+    u2 = u1 * rho1 / rho2
+    return (rho1, u1, p1), (rho2, u2, p2)
+
+
+def shock_vortex_2d(nx=256, ny=128, P=3, N=4, Q=8, mach=1.1):
+    """Stochastic shock-vortex interaction (§5.4 family): [0, 2] x [0, 1], stationary
+    normal shock of upstream Mach 1.1 at x = 0.5 (upstream rho = 1, p = 1, T = p/rho;
+    downstream from the Rankine-Hugoniot jump), isentropic vortex at (0.25, 0.5), r_c = 0.05,
+    mu = 0.204, strength 0.3 (1 + 0.2 z) added on both sides (§5.4 perturbation with
+    delta S = 0); Dirichlet inflow / outflow states in x, reflecting walls in y.  Tensor
+    FR with P = 3, 256 x 128 elements, N = 4, Q = 8; detector + L2 filter (eps1 = 0.6,
+    eps2 = 1, s0 = -3 log10 2 as in the §5.4 table, kappa = 4)."""
+    up, down = _rh_downstream(mach)
+    g = GAMMA
+    xs, xc, yc, rc, mu = 0.5, 0.25, 0.5, 0.05, 0.204
+
+    def prim_to_cons(rho, u, v, p):
+        return np.stack([rho, rho * u, rho * v, p / (g - 1.0) + 0.5 * rho * (u * u + v * v)], axis=-1)
+
+    def ic(x, y, z):
+        left = x < xs
+        rho_b = np.where(left, up[0], down[0])
+        u_b = np.where(left, up[1], down[1])
+        p_b = np.where(left, up[2], down[2])
+        T_b = p_b / rho_b
+        zeta = 0.3 * (1.0 + 0.2 * z)
+        dx, dy = x - xc, y - yc
+        r = np.sqrt(dx * dx + dy * dy)
+        eta = r / rc
+        amp = zeta * eta * np.exp(mu * (1.0 - eta * eta))
+        # (sin theta, -cos theta) with theta the polar angle about the vortex centre
+        sin_t = np.where(r > 0, dy / np.where(r > 0, r, 1.0), 0.0)
+        cos_t = np.where(r > 0, dx / np.where(r > 0, r, 1.0), 0.0)
+        du, dv = amp * sin_t, -amp * cos_t
+        dT = -(g - 1.0) * zeta * zeta / (4.0 * mu * g) * np.exp(2.0 * mu * (1.0 - eta * eta))
+        T = T_b + dT
+        rho = rho_b * (T / T_b) ** (1.0 / (g - 1.0))
+        return prim_to_cons(rho, u_b + du, 0.0 * x + dv, rho * T)
+
+    def state(prim):
+        return lambda z: prim_to_cons(np.array(prim[0]), np.array(prim[1]), np.array(0.0), np.array(prim[2]))
+
+    return dict(
+        name=f"shock_vortex_{nx}x{ny}_P{P}_N{N}_Q{Q}",
+        solver=dict(dim=2, nx=nx, ny=ny, x0=0.0, x1=2.0, y0=0.0, y1=1.0,
+                    bc=("dirichlet", "dirichlet", "reflect", "reflect"), P=P, N=N, Q=Q, equation="euler",
+                    gamma=GAMMA, filter="l2", sensor=True, f_eps1=0.6, f_eps2=1.0,
+                    s0=-3.0 * math.log10(2.0), kappa=4.0, limiter=True),
+        ic=ic,
+        boundary={0: state(up), 1: state(down)},
+        cfl=0.1, t_end=1.0, lam0=None,
+    )
+
+
+ALL = {"advection": advection_1d, "burgers": burgers_1d, "sod": sod_1d, "shock_vortex": shock_vortex_2d}
+
+
+def nodal_values(fn, nodes_x, nodes_z, nodes_y=None):
+    """Evaluate an initial-data function at every (solution point, z-node): [E, Np, Q, S]."""
+    vals = []
+    for zq in nodes_z:
+        v = fn(nodes_x, zq) if nodes_y is None else fn(nodes_x, nodes_y, zq)
+        vals.append(np.asarray(v, dtype=np.float64))
+    return np.ascontiguousarray(np.stack(vals, axis=2))
+
+
+def boundary_values(fn, nodes_z):
+    """Evaluate a boundary-state function at the z-nodes: [Q, S]."""
+    return np.ascontiguousarray(np.stack([np.asarray(fn(zq), dtype=np.float64) for zq in nodes_z], 0))
+
+
+def random_state(shape, seed, base, amp, decay=2.0):
+    """Seeded gPC coefficients [E, Np, M, S]: mean `base[s]` in mode 0 plus Gaussian
+    perturbations of size amp[s] / (1 + k)^decay in every mode k."""
+    E, Np, M, S = shape
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal(shape) * np.asarray(amp, dtype=np.float64)[None, None, None, :]
+    u /= (1.0 + np.arange(M))[None, None, :, None] ** decay
+    u[:, :, 0, :] += np.asarray(base, dtype=np.float64)[None, None, :]
+    return u
