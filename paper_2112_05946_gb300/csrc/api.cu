@@ -32,6 +32,8 @@ struct frsg_ctx {
     void* d_u1 = nullptr;
     void* d_u2 = nullptr;
     double* d_conv = nullptr;     // FP32 contexts: double staging buffer for set/get_state
+    double* d_dt = nullptr;       // step size read by the stage kernels (graphs do not depend on dt)
+    double dt_set = -1.0;         // value last written to d_dt
     uint8_t* d_flags = nullptr;   // [3][E]
     double* d_beta = nullptr;     // [3][E]
     unsigned* d_err = nullptr;
@@ -42,7 +44,6 @@ struct frsg_ctx {
     uint64_t launches = 0;
     int TE = 1, TE_lim = 1;
     cudaGraphExec_t graph_exec = nullptr;
-    double graph_dt = 0.0;
     int graph_kernels = 0;
 };
 
@@ -97,11 +98,17 @@ std::string validate(const frsg_config& c) {
     return "";
 }
 
-// Device table block: FR tables, gPC tables, limiter point matrix and averaging weights.
-void build_device_tables(frsg_ctx* c) {
-    const frsg::HostTables& t = c->ht;
+// Device table block: FR tables, gPC tables, limiter point matrix, averaging weights,
+// element Vandermonde pair, top-mode mask and filter table.
+struct TableCtx {
+    frsg_config cfg;
+    int Np, M;
+    frsg::TabOff off;
+};
+
+void build_table_block(TableCtx* c, const frsg::HostTables& t, std::vector<double>* out) {
     const int n1 = t.n1, Np = c->Np;
-    std::vector<double>& v = c->htab;
+    std::vector<double>& v = *out;
     v.clear();
     auto put = [&](const std::vector<double>& a) {
         int o = (int)v.size();
@@ -154,7 +161,58 @@ void build_device_tables(frsg_ctx* c) {
                     }
     }
     c->off.Lpts = put(L);
+    // element Vandermonde (tensor product in 2D), top-mode mask and filter table (§4, §4.1)
+    const frsg_config& cf = c->cfg;
+    std::vector<double> Vf((size_t)Np * Np), Vfi((size_t)Np * Np), top(Np), lam((size_t)Np * c->M);
+    const int P = cf.P, N = cf.N;
+    for (int j = 0; j < Np; ++j)
+        for (int m = 0; m < Np; ++m) {
+            if (cf.dim == 1) {
+                Vf[(size_t)j * Np + m] = t.Vx[j * n1 + m];
+                Vfi[(size_t)m * Np + j] = t.Vxinv[m * n1 + j];
+            } else {
+                const int a = j % n1, b = j / n1, ma = m % n1, mb = m / n1;
+                Vf[(size_t)j * Np + m] = t.Vx[a * n1 + ma] * t.Vx[b * n1 + mb];
+                Vfi[(size_t)m * Np + j] = t.Vxinv[ma * n1 + a] * t.Vxinv[mb * n1 + b];
+            }
+        }
+    for (int m = 0; m < Np; ++m) {
+        const int ma = m % n1, mb = cf.dim == 1 ? 0 : m / n1;
+        top[m] = (ma == P || (cf.dim == 2 && mb == P)) ? 1.0 : 0.0;
+        for (int k = 0; k < c->M; ++k) {
+            double val = 0.0;
+            if (cf.filter == FRSG_FILTER_EXP) {
+                // Lambda = exp(-alpha dt val), val = sum over directions of eta^s (N_* = 0)
+                if (P > 0) {
+                    val += std::pow((double)ma / P, cf.f_s);
+                    if (cf.dim == 2) val += std::pow((double)mb / P, cf.f_s);
+                }
+                if (N > 0) val += std::pow((double)k / N, cf.f_s);
+            } else if (cf.filter == FRSG_FILTER_L2) {
+                const double np1 = n1;
+                const double a1 = n1 > 1 ? 1.0 / (cf.f_eps1 * np1 * np1 * (np1 - 1) * (np1 - 1)) : 0.0;
+                const double a2 = N > 0 ? 1.0 / (cf.f_eps2 * (double)N * N * (N + 1.0) * (N + 1.0)) : 0.0;
+                double pen = a1 * (double)ma * ma * (ma + 1.0) * (ma + 1.0);
+                if (cf.dim == 2) pen += a1 * (double)mb * mb * (mb + 1.0) * (mb + 1.0);
+                pen += a2 * (double)k * k * (k + 1.0) * (k + 1.0);
+                val = 1.0 / (1.0 + pen);
+            } else {
+                val = 0.0;
+            }
+            lam[(size_t)m * c->M + k] = val;
+        }
+    }
+    c->off.Vf = put(Vf);
+    c->off.Vfinv = put(Vfi);
+    c->off.top = put(top);
+    c->off.lam = put(lam);
     c->off.total = (int)v.size();
+}
+
+void build_device_tables(frsg_ctx* c) {
+    TableCtx tc{c->cfg, c->Np, c->M, {}};
+    build_table_block(&tc, c->ht, &c->htab);
+    c->off = tc.off;
 }
 
 StageArgs base_args(frsg_ctx* c) {
@@ -229,7 +287,8 @@ cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
     A.uout = bufs_out[s];
     A.a = ca[s];
     A.b = cb[s];
-    A.c = cb[s] * dt;
+    A.c = cb[s];
+    A.dtp = c->d_dt;
     A.dt_filter = dt;
     A.do_filter = filt ? 1 : 0;
     A.flags = c->d_flags + (size_t)s * c->E;
@@ -239,6 +298,14 @@ cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
         c->replay_pos += 1;
     }
     return launch_stage(c, A);
+}
+
+cudaError_t set_dt(frsg_ctx* c, double dt) {
+    if (dt == c->dt_set) return cudaSuccess;
+    // pageable source: staged by the driver before the call returns
+    cudaError_t e = cudaMemcpyAsync(c->d_dt, &dt, sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) c->dt_set = dt;
+    return e;
 }
 
 cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
@@ -266,6 +333,19 @@ int choose_tile_2d(const frsg_ctx* c) {
 }
 
 }  // namespace
+
+namespace frsg {
+std::string noalloc_validate(const frsg_config& c) { return validate(c); }
+
+void noalloc_tables(const frsg_config& c, std::vector<double>* tab, TabOff* off) {
+    HostTables ht;
+    build_tables(c.P, c.N, c.Q, &ht);
+    const int n1 = c.P + 1;
+    TableCtx tc{c, c.dim == 1 ? n1 : n1 * n1, c.N + 1, {}};
+    build_table_block(&tc, ht, tab);
+    *off = tc.off;
+}
+}  // namespace frsg
 
 extern "C" {
 
@@ -306,6 +386,7 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     if ((e = cudaMalloc(&ctx->d_u2, ctx->esz * nstate)) != cudaSuccess) return cleanup_fail(e, "stage 2");
     if (!ctx->fp64 && (e = cudaMalloc(&ctx->d_conv, sizeof(double) * nstate)) != cudaSuccess)
         return cleanup_fail(e, "conversion buffer");
+    if ((e = cudaMalloc(&ctx->d_dt, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "dt");
     if ((e = cudaMalloc(&ctx->d_flags, 3 * (size_t)ctx->E)) != cudaSuccess) return cleanup_fail(e, "flags");
     if ((e = cudaMalloc(&ctx->d_beta, 3 * sizeof(double) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "beta");
     if ((e = cudaMalloc(&ctx->d_err, sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "err");
@@ -322,7 +403,7 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     }
     if (e != cudaSuccess) return cleanup_fail(e, "upload");
     ctx->TE = cfg->dim == 1 ? choose_tile_1d(ctx) : 1;
-    ctx->TE_lim = std::max(1, 256 / ctx->Q);
+    ctx->TE_lim = std::max(1, 256 / ctx->Q);   // limit_kernel is built for at most 256 threads
     if (cfg->dim == 2) {
         if (frsg::stage2d_smem_bytes(ctx->fp64, 1, ctx->n1, ctx->M, ctx->Q, ctx->S) > 200 * 1024) {
             fr_sg_destroy(ctx);
@@ -345,6 +426,7 @@ void fr_sg_destroy(frsg_ctx* ctx) {
     cudaFree(ctx->d_u1);
     cudaFree(ctx->d_u2);
     cudaFree(ctx->d_conv);
+    cudaFree(ctx->d_dt);
     cudaFree(ctx->d_flags);
     cudaFree(ctx->d_beta);
     cudaFree(ctx->d_err);
@@ -492,14 +574,12 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     if (!ctx) return FRSG_E_INVAL;
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
     const int kernels_per_step = 3 * (ctx->cfg.limiter ? 2 : 1);
+    if (nsteps == 0) return FRSG_OK;
+    CK(set_dt(ctx, dt));
     for (int n = 0; n < nsteps; ++n) {
         const bool replaying = ctx->replay_pos < ctx->replay_rows;
         if (use_graph && !replaying) {
-            if (!ctx->graph_exec || ctx->graph_dt != dt) {
-                if (ctx->graph_exec) {
-                    cudaGraphExecDestroy(ctx->graph_exec);
-                    ctx->graph_exec = nullptr;
-                }
+            if (!ctx->graph_exec) {
                 cudaStream_t cap = ctx->stream;
                 bool own = false;
                 if (cap == nullptr) {
@@ -525,7 +605,6 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
                     cudaStreamDestroy(cap);
                 }
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
-                ctx->graph_dt = dt;
                 ctx->graph_kernels = kernels_per_step;
             }
             CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
@@ -541,6 +620,7 @@ frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt) {
     if (!ctx) return FRSG_E_INVAL;
     if (stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt))
         return fail(ctx, FRSG_E_INVAL, "need stage in 0..2 and dt > 0");
+    CK(set_dt(ctx, dt));
     CK(issue_stage(ctx, stage, dt, true));
     return FRSG_OK;
 }

@@ -35,6 +35,9 @@ void build_tables(int P, int N, int Q, HostTables* t);
 // Offsets (in doubles) of each table inside the single device table block.
 struct TabOff {
     int D, lm, lp, dhL, dhR, Vx, Vxinv, VzT, Pz, w, Lpts, total;
+    int Vf, Vfinv;   // Np x Np element Vandermonde (tensor product in 2D) and its inverse
+    int top;         // Np: 1 where the physical mode has degree P in some direction
+    int lam;         // Np x M: exponential filter exponent sum eta^s, or the L2 factor
     int NL;   // rows of Lpts: solution points then face flux points (limiter, §4.3)
 };
 
@@ -43,8 +46,9 @@ struct StageArgs {
     const void* uin;       // stage input [E][Np][M][S]
     const void* ubase;     // u^n of the SSP combination (unused when a == 0)
     void* uout;            // output
-    double a, b, c;        // uout = a*ubase + b*uin + c*L(uin)
-    double dt_filter;      // step size entering the exponential filter
+    double a, b, c;        // uout = a*ubase + b*uin + c*dt*L(uin), dt = *dtp (c alone if dtp is null)
+    double dt_filter;      // step size entering the exponential filter when dtp is null
+    const double* dtp;     // device step size, or null
     int E, nx, ny, M, Q;
     double invJx, invJy;   // 2 / element width, 2 / element height
     const double* tab;     // device table block

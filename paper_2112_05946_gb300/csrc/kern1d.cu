@@ -18,6 +18,7 @@
 //       and one coalesced store.
 #include <cuda_runtime.h>
 
+#include "epilogue.cuh"
 #include "internal.h"
 #include "physics.cuh"
 
@@ -26,7 +27,7 @@ namespace {
 
 template <typename T>
 struct Smem1d {
-    T *U, *G, *Tr, *Vz, *Pz, *D, *lm, *lp, *dhL, *dhR, *F, *Red;
+    T *U, *G, *Tr, *Vz, *Pz, *D, *lm, *lp, *dhL, *dhR, *Vf, *Vfinv, *Lam, *Top, *Red;
     int* flag;
 };
 
@@ -34,39 +35,13 @@ template <typename T>
 __host__ __device__ inline size_t smem1d_bytes(int TE, int NP, int M, int Q, int S) {
     size_t n = 0;
     n += (size_t)TE * NP * M * S;          // U
-    n += (size_t)TE * NP * S * Q;          // G
+    n += (size_t)TE * NP * S * (Q > M ? Q : M);   // G (nodal residual, later the modal coefficients)
     n += (size_t)(TE + 2) * 2 * S * Q;     // Tr
     n += 2 * (size_t)M * Q;                // Vz, Pz
     n += (size_t)NP * NP + 4 * NP;         // D, lm, lp, dhL, dhR
-    n += (size_t)M * NP * NP;              // F
+    n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;   // Vf, Vfinv, Lam, Top
     n += (size_t)2 * TE * Q;               // Red
     return n * sizeof(T) + (size_t)TE * sizeof(int) + 16;
-}
-
-// Per-mode filter strength Lambda[m][k] (§4.1.1 Eq. 32 with N_* = 0; §4.1.2 Eqs. 38-39).
-__device__ inline double filter_strength(int filter, int m, int k, int P, int N, double alpha, double s,
-                                         double dt, double eps1, double eps2) {
-    if (filter == FRSG_FILTER_EXP) {
-        double e = 0.0;
-        if (P > 0) e += pow((double)m / P, s);
-        if (N > 0) e += pow((double)k / N, s);
-        return exp(-alpha * dt * e);
-    }
-    const double n1 = P + 1;
-    const double a1 = n1 > 1 ? 1.0 / (eps1 * n1 * n1 * (n1 - 1) * (n1 - 1)) : 0.0;
-    const double a2 = N > 0 ? 1.0 / (eps2 * (double)N * N * (N + 1.0) * (N + 1.0)) : 0.0;
-    return 1.0 / (1.0 + a1 * m * m * (m + 1.0) * (m + 1.0) + a2 * (double)k * k * (k + 1.0) * (k + 1.0));
-}
-
-// theta of §4.2, Eq. 47 from the top-mode and total energies.
-__device__ inline bool detector_flags(double top, double total, double s0, double kappa) {
-    if (!(total > 0.0) || !(top > 0.0)) return false;
-    const double se = log10(top / total);
-    double theta;
-    if (se < s0 - kappa) theta = 1.0;
-    else if (se > s0 + kappa) theta = 0.0;
-    else theta = 0.5 * (1.0 - sin(M_PI * (se - s0) / (2.0 * kappa)));
-    return theta < 0.99;
 }
 
 template <typename T, int NP, int S, int EQ>
@@ -85,7 +60,7 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
     {
         T* p = reinterpret_cast<T*>(smem_raw);
         sm.U = p; p += (size_t)TE * elsz;
-        sm.G = p; p += (size_t)TE * NP * S * Q;
+        sm.G = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
         sm.Tr = p; p += (size_t)(TE + 2) * 2 * S * Q;
         sm.Vz = p; p += M * Q;
         sm.Pz = p; p += M * Q;
@@ -94,7 +69,10 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
         sm.lp = p; p += NP;
         sm.dhL = p; p += NP;
         sm.dhR = p; p += NP;
-        sm.F = p; p += M * NP * NP;
+        sm.Vf = p; p += NP * NP;
+        sm.Vfinv = p; p += NP * NP;
+        sm.Lam = p; p += NP * M;
+        sm.Top = p; p += NP;
         sm.Red = p; p += 2 * TE * Q;
         sm.flag = reinterpret_cast<int*>(p);
     }
@@ -112,18 +90,14 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
         sm.dhL[i] = (T)tab[A.off.dhL + i];
         sm.dhR[i] = (T)tab[A.off.dhR + i];
     }
+    const double dt = A.dtp ? *A.dtp : A.dt_filter;
     if (A.do_filter) {
-        // F_k = Vx diag(Lambda[., k]) Vx^{-1}: the nodal form of the filter, per gPC mode.
-        for (int i = tid; i < M * NP * NP; i += nthr) {
-            const int k = i / (NP * NP), j = (i / NP) % NP, jp = i % NP;
-            double acc = 0.0;
-            for (int m = 0; m < NP; ++m)
-                acc += tab[A.off.Vx + j * NP + m] *
-                       filter_strength(A.filter, m, k, NP - 1, M - 1, A.f_alpha, A.f_s, A.dt_filter, A.f_eps1,
-                                       A.f_eps2) *
-                       tab[A.off.Vxinv + m * NP + jp];
-            sm.F[i] = (T)acc;
+        for (int i = tid; i < NP * NP; i += nthr) {
+            sm.Vf[i] = (T)tab[A.off.Vf + i];
+            sm.Vfinv[i] = (T)tab[A.off.Vfinv + i];
         }
+        for (int i = tid; i < NP; i += nthr) sm.Top[i] = (T)tab[A.off.top + i];
+        load_filter_strengths<T>(A, NP, sm.Lam, tid, nthr, dt);
     }
     {
         const T* src = uin + (size_t)e0 * elsz;
@@ -239,7 +213,7 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
     __syncthreads();
 
     // ---- a4 + a8: projection of the residual onto the modes, SSP combination
-    const T ca = (T)A.a, cb = (T)A.b, cc = (T)A.c;
+    const T ca = (T)A.a, cb = (T)A.b, cc = (T)(A.dtp ? A.c * dt : A.c);
     const T* ubase = static_cast<const T*>(A.ubase);
     T* uout = static_cast<T*>(A.uout);
     const size_t gbase = (size_t)e0 * elsz;
@@ -263,54 +237,9 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
     }
     if (A.do_filter) {
         __syncthreads();
-        // ---- a9: detector on variable 0, partial energies per thread, fixed-order sum
-        if (active) {
-            double tot = 0.0, top = 0.0;
-            const T* ue = sm.U + te * elsz;
-            for (int i = tq; i < NP * M; i += Q) {
-                const int m = i / M, k = i % M;
-                double um = 0.0;
-#pragma unroll
-                for (int j = 0; j < NP; ++j) um += A.tab[A.off.Vxinv + m * NP + j] * (double)ue[(j * M + k) * S];
-                tot += um * um;
-                if (m == NP - 1 || k == M - 1) top += um * um;
-            }
-            sm.Red[(te * Q + tq) * 2 + 0] = (T)tot;
-            sm.Red[(te * Q + tq) * 2 + 1] = (T)top;
-        }
-        __syncthreads();
-        if (active && tq == 0) {
-            double tot = 0.0, top = 0.0;
-            for (int i = 0; i < Q; ++i) {
-                tot += (double)sm.Red[(te * Q + i) * 2 + 0];
-                top += (double)sm.Red[(te * Q + i) * 2 + 1];
-            }
-            const int e = e0 + te;
-            int fl;
-            if (A.replay) fl = A.replay[e] ? 1 : 0;
-            else if (!A.sensor) fl = 1;
-            else fl = detector_flags(top, tot, A.s0, A.kappa) ? 1 : 0;
-            sm.flag[te] = fl;
-            if (A.flags) A.flags[e] = (uint8_t)fl;
-        }
-        __syncthreads();
-        // ---- a10: filtered (or unchanged) coefficients, one coalesced store
-        for (int o = tid; o < nout; o += nthr) {
-            const int el = o / elsz, rr = o - el * elsz;
-            T val;
-            if (sm.flag[el]) {
-                const int j = rr / (M * S), k = (rr / S) % M, s = rr % S;
-                const T* Fk = sm.F + (k * NP + j) * NP;
-                const T* ue = sm.U + el * elsz + k * S + s;
-                val = T(0);
-#pragma unroll
-                for (int jp = 0; jp < NP; ++jp) val += Fk[jp] * ue[jp * M * S];
-            } else {
-                val = sm.U[o];
-            }
-            uout[gbase + o] = val;
-            bad |= !finite_val(val);
-        }
+        // ---- a9 + a10: detector and filter, one coalesced store
+        bad |= detector_filter_store<T, NP, S>(A, sm.U, sm.G, sm.Vf, sm.Vfinv, sm.Lam, sm.Top, sm.Red, sm.flag, tid,
+                                               nthr, te, tq, Q, active, ne, e0, uout, gbase);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }

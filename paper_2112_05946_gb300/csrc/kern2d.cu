@@ -17,6 +17,7 @@
 //       Psi_ma(r) Psi_mb(s) Phi_k(z) (§4.2); a10 filter of flagged elements (§4.1, Eq. 34)
 #include <cuda_runtime.h>
 
+#include "epilogue.cuh"
 #include "internal.h"
 #include "physics.cuh"
 
@@ -29,11 +30,11 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
     size_t n = 0;
     n += (size_t)TE * Np * M * S;           // U (coefficients, later the new state)
     n += (size_t)TE * Np * S * Q;           // Un (nodal values)
-    n += (size_t)TE * Np * S * Q;           // G (nodal residual)
+    n += (size_t)TE * Np * S * (Q > M ? Q : M);   // G (nodal residual, later the modal coefficients)
     n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][s][q]
     n += 2 * (size_t)M * Q;                 // Vz, Pz
     n += (size_t)n1 * n1 + 4 * n1;          // D, lm, lp, dhL, dhR
-    n += (size_t)M * Np * Np;               // F (filter per gPC mode)
+    n += 2 * (size_t)Np * Np + (size_t)Np * M + Np;   // Vf, Vfinv, Lam, Top
     n += (size_t)2 * TE * n1 * Q;           // Red
     return n;
 }
@@ -41,31 +42,6 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
 template <typename T>
 size_t smem2d_bytes_t(int TE, int n1, int M, int Q, int S) {
     return smem2d_elems<T>(TE, n1, M, Q, S) * sizeof(T) + (size_t)TE * sizeof(int) + 16;
-}
-
-__device__ inline double filter_strength_2d(int filter, int ma, int mb, int k, int P, int N, double alpha, double s,
-                                            double dt, double eps1, double eps2) {
-    if (filter == FRSG_FILTER_EXP) {
-        double e = 0.0;
-        if (P > 0) e += pow((double)ma / P, s) + pow((double)mb / P, s);
-        if (N > 0) e += pow((double)k / N, s);
-        return exp(-alpha * dt * e);
-    }
-    const double n1 = P + 1;
-    const double a1 = n1 > 1 ? 1.0 / (eps1 * n1 * n1 * (n1 - 1) * (n1 - 1)) : 0.0;
-    const double a2 = N > 0 ? 1.0 / (eps2 * (double)N * N * (N + 1.0) * (N + 1.0)) : 0.0;
-    return 1.0 / (1.0 + a1 * ((double)ma * ma * (ma + 1.0) * (ma + 1.0) + (double)mb * mb * (mb + 1.0) * (mb + 1.0)) +
-                  a2 * (double)k * k * (k + 1.0) * (k + 1.0));
-}
-
-__device__ inline bool detector_flags_2d(double top, double total, double s0, double kappa) {
-    if (!(total > 0.0) || !(top > 0.0)) return false;
-    const double se = log10(top / total);
-    double theta;
-    if (se < s0 - kappa) theta = 1.0;
-    else if (se > s0 + kappa) theta = 0.0;
-    else theta = 0.5 * (1.0 - sin(M_PI * (se - s0) / (2.0 * kappa)));
-    return theta < 0.99;
 }
 
 // Trace of element `e` at z-node q along a line: sum over the n1 points of the line of
@@ -107,7 +83,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     T* p = reinterpret_cast<T*>(smem_raw);
     T* sU = p; p += (size_t)TE * elsz;
     T* sUn = p; p += (size_t)TE * NP * S * Q;
-    T* sG = p; p += (size_t)TE * NP * S * Q;
+    T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
     T* sTx = p; p += (size_t)(TE + 2) * 2 * N1 * S * Q;
     T* sVz = p; p += M * Q;
     T* sPz = p; p += M * Q;
@@ -116,7 +92,10 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     T* slp = p; p += N1;
     T* sdhL = p; p += N1;
     T* sdhR = p; p += N1;
-    T* sF = p; p += (size_t)M * NP * NP;
+    T* sVf = p; p += NP * NP;
+    T* sVfinv = p; p += NP * NP;
+    T* sLam = p; p += NP * M;
+    T* sTop = p; p += NP;
     T* sRed = p; p += 2 * TE * N1 * Q;
     int* sFlag = reinterpret_cast<int*>(p);
 
@@ -132,20 +111,14 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
         sdhL[i] = (T)tab[A.off.dhL + i];
         sdhR[i] = (T)tab[A.off.dhR + i];
     }
+    const double dt = A.dtp ? *A.dtp : A.dt_filter;
     if (A.do_filter) {
-        // F_k[(b,a)][(b',a')] = sum_{ma,mb} Vx[a][ma] Vx[b][mb] Lambda[ma][mb][k] Vxinv[ma][a'] Vxinv[mb][b']
-        for (int i = tid; i < M * NP * NP; i += nthr) {
-            const int k = i / (NP * NP), jo = (i / NP) % NP, ji = i % NP;
-            const int a = jo % N1, b = jo / N1, ap = ji % N1, bp = ji / N1;
-            double acc = 0.0;
-            for (int mb = 0; mb < N1; ++mb)
-                for (int ma = 0; ma < N1; ++ma)
-                    acc += tab[A.off.Vx + a * N1 + ma] * tab[A.off.Vx + b * N1 + mb] *
-                           filter_strength_2d(A.filter, ma, mb, k, N1 - 1, M - 1, A.f_alpha, A.f_s, A.dt_filter,
-                                              A.f_eps1, A.f_eps2) *
-                           tab[A.off.Vxinv + ma * N1 + ap] * tab[A.off.Vxinv + mb * N1 + bp];
-            sF[i] = (T)acc;
+        for (int i = tid; i < NP * NP; i += nthr) {
+            sVf[i] = (T)tab[A.off.Vf + i];
+            sVfinv[i] = (T)tab[A.off.Vfinv + i];
         }
+        for (int i = tid; i < NP; i += nthr) sTop[i] = (T)tab[A.off.top + i];
+        load_filter_strengths<T>(A, NP, sLam, tid, nthr, dt);
     }
     {
         const T* src = uin + (size_t)e0 * elsz;
@@ -342,7 +315,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     __syncthreads();
 
     // ---- projection + SSP combination
-    const T ca = (T)A.a, cb = (T)A.b, cc = (T)A.c;
+    const T ca = (T)A.a, cb = (T)A.b, cc = (T)(A.dtp ? A.c * dt : A.c);
     const T* ubase = static_cast<const T*>(A.ubase);
     T* uout = static_cast<T*>(A.uout);
     const size_t gbase = (size_t)e0 * elsz;
@@ -366,57 +339,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     }
     if (A.do_filter) {
         __syncthreads();
-        const int lt = tl * Q + tq, nlt = N1 * Q;   // thread index inside the element
-        if (active) {
-            double tot = 0.0, top = 0.0;
-            const T* ue = sU + te * elsz;
-            for (int i = lt; i < NP * M; i += nlt) {
-                const int mm = i / M, k = i % M;
-                const int ma = mm % N1, mb = mm / N1;
-                double um = 0.0;
-#pragma unroll
-                for (int b = 0; b < N1; ++b)
-#pragma unroll
-                    for (int a = 0; a < N1; ++a)
-                        um += tab[A.off.Vxinv + mb * N1 + b] * tab[A.off.Vxinv + ma * N1 + a] *
-                              (double)ue[((b * N1 + a) * M + k) * S];
-                tot += um * um;
-                if (ma == N1 - 1 || mb == N1 - 1 || k == M - 1) top += um * um;
-            }
-            sRed[(te * nlt + lt) * 2 + 0] = (T)tot;
-            sRed[(te * nlt + lt) * 2 + 1] = (T)top;
-        }
-        __syncthreads();
-        if (active && lt == 0) {
-            double tot = 0.0, top = 0.0;
-            for (int i = 0; i < nlt; ++i) {
-                tot += (double)sRed[(te * nlt + i) * 2 + 0];
-                top += (double)sRed[(te * nlt + i) * 2 + 1];
-            }
-            int fl;
-            if (A.replay) fl = A.replay[e] ? 1 : 0;
-            else if (!A.sensor) fl = 1;
-            else fl = detector_flags_2d(top, tot, A.s0, A.kappa) ? 1 : 0;
-            sFlag[te] = fl;
-            if (A.flags) A.flags[e] = (uint8_t)fl;
-        }
-        __syncthreads();
-        for (int o = tid; o < nout; o += nthr) {
-            const int el = o / elsz, rr = o - el * elsz;
-            T val;
-            if (sFlag[el]) {
-                const int j = rr / (M * S), k = (rr / S) % M, s = rr % S;
-                const T* Fk = sF + ((size_t)k * NP + j) * NP;
-                const T* ue = sU + el * elsz + k * S + s;
-                val = T(0);
-#pragma unroll
-                for (int jp = 0; jp < NP; ++jp) val += Fk[jp] * ue[jp * M * S];
-            } else {
-                val = sU[o];
-            }
-            uout[gbase + o] = val;
-            bad |= !finite_val(val);
-        }
+        bad |= detector_filter_store<T, NP, S>(A, sU, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, tid, nthr, te,
+                                               tl * Q + tq, N1 * Q, active, ne, e0, uout, gbase);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }

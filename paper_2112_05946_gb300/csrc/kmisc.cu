@@ -63,7 +63,7 @@ __device__ inline double pressure_root(const double* ub, const double* us, doubl
 
 // Block (Q, TE): thread (q, te) owns z-node q of element te.
 template <typename T, int NPT, int S>
-__global__ void limit_kernel(const LimitArgs A) {
+__global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
     extern __shared__ double lsm[];
     const int Q = A.Q, M = A.M, TE = A.TE, NL = A.off.NL;
     const int tq = threadIdx.x, te = threadIdx.y;
