@@ -182,6 +182,38 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out);
  * each captured kernel).  Host counter; never synchronises. */
 uint64_t fr_sg_launch_count(const frsg_ctx* ctx);
 
+/* Allocation-free variant of fr_sg_rk_step for 1D problems in FRSG_FP64.  The paper has no
+ * counterpart: this entry point exists for callers, not for the method.
+ *
+ * Some callers may not allocate device memory.  Examples are code whose GPU memory is owned
+ * by another allocator (a framework's caching pool, or an arena reserved at start-up) and
+ * code on a latency-critical path: cudaMalloc and cudaFree can synchronise the device and
+ * fragment the owner's pool, so such callers must not trigger them.  This call takes the
+ * caller's input and output state and allocates nothing: no context, no cudaMalloc, no
+ * cudaFree, no allocating library routine, and only fixed-size host storage.  Its scratch
+ * (two stage buffers, the tables, the step size, the ghost modes and an error word) is one
+ * static __device__ array of 8 MiB, which every GPU that loads this library keeps until the
+ * process exits.  A problem whose stage buffers and tables do not fit (about 500,000 state
+ * values) is rejected with FRSG_E_INVAL and a message on stderr.
+ *
+ * cfg: as for fr_sg_init, with dim = 1 and precision = FRSG_FP64 (FRSG_E_UNSUPPORTED otherwise).
+ * ghost_modes: host [4][M][S] gPC modes of the Dirichlet sides' ghost states (the modes that
+ *   fr_sg_set_boundary_nodal computes), or NULL when no side is Dirichlet.
+ * u_in, u_out: device double [E][Np][M][S]; u_out receives the state after nsteps steps of
+ *   size dt of the same scheme as fr_sg_rk_step (limiter, residual, SSP combination, detector
+ *   and filter per stage); u_in == u_out is allowed.
+ * stream: a cudaStream_t.  The work is enqueued there and the call synchronises that stream
+ *   before it returns, so that it can report the errors kernels latch (FRSG_E_NONFINITE,
+ *   FRSG_E_POSITIVITY).
+ * The first call on a device looks up the device address of the static array, with that
+ * device current; make that first call before any stream capture.  Every call shares the
+ * array and leaves its contents behind: each call clears what must start at zero (the
+ * error word) and overwrites the rest before reading it.  Calls that overlapped on the GPU
+ * would race on the shared array, so the library runs them one at a time: a call holds a
+ * process-wide lock until its stream work has finished. */
+frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const double* ghost_modes, const double* u_in,
+                                  double* u_out, double dt, int nsteps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -337,14 +337,6 @@ int choose_tile_2d(const frsg_ctx* c) {
 namespace frsg {
 std::string noalloc_validate(const frsg_config& c) { return validate(c); }
 
-void noalloc_tables(const frsg_config& c, std::vector<double>* tab, TabOff* off) {
-    HostTables ht;
-    build_tables(c.P, c.N, c.Q, &ht);
-    const int n1 = c.P + 1;
-    TableCtx tc{c, c.dim == 1 ? n1 : n1 * n1, c.N + 1, {}};
-    build_table_block(&tc, ht, tab);
-    *off = tc.off;
-}
 }  // namespace frsg
 
 extern "C" {

@@ -77,6 +77,8 @@ _SIGNATURES = [
     ("fr_sg_check", ctypes.c_int, [ctypes.c_void_p]),
     ("fr_sg_launch_count", ctypes.c_uint64, [ctypes.c_void_p]),
     ("fr_sg_set_tile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("fr_sg_rk_step_noalloc", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
 ]
 
 
@@ -128,6 +130,20 @@ def _ptr(a):
             raise ValueError("host arrays must be C-contiguous")
         return a.ctypes.data
     return a.data_ptr()   # torch tensor
+
+
+def rk_step_noalloc(u_in, u_out, dt, nsteps=1, ghost_modes=None, stream=None, **cfg):
+    """fr_sg_rk_step_noalloc: nsteps SSP-RK3 steps of a 1D FP64 problem for callers that may
+    not allocate device memory; u_in, u_out are device float64 tensors [E, Np, M, S]."""
+    lib = load_library()
+    c = make_config(**cfg)
+    g = None
+    if ghost_modes is not None:
+        g = np.ascontiguousarray(ghost_modes, dtype=np.float64)
+    st = lib.fr_sg_rk_step_noalloc(ctypes.byref(c), _ptr(g), _ptr(u_in), _ptr(u_out), float(dt), int(nsteps),
+                                   ctypes.c_void_p(stream or 0))
+    if st != OK:
+        raise FrsgError(st, "fr_sg_rk_step_noalloc failed (details on stderr)")
 
 
 class Solver:
