@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--workload", default="burgers", choices=sorted(workloads.ALL))
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Sod and 2D shock-vortex lines")
     return ap.parse_args()
 
 
@@ -205,6 +206,134 @@ def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracl
     )
 
 
+def measure_extra(torch, frsg, wl, precision, steps, warmup, stream, flush):
+    """Throughput of another workload (FP64 or FP32 form): per-step events with the L2
+    flush between steps, dt fixed from the initial CFL condition, plus the stage-kernel
+    duration (limiter launches, if any, timed with their stage)."""
+    E, Np, M, S = workload_sizes(wl)
+    dof = E * Np * M * S
+    esz = 8 if precision == "fp64" else 4
+    s = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
+    nodes = s.nodes()
+    if "boundary" in wl:
+        for side, fn in wl["boundary"].items():
+            s.set_boundary_nodal(side, workloads.boundary_values(fn, nodes[-1]))
+    if len(nodes) == 2:
+        s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[1]))
+    else:
+        s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[2], nodes[1]))
+    # half the CFL number of the correctness runs, refreshed every 20 steps outside the timed
+    # events: the Euler wave speeds grow after t = 0
+    cfl = 0.5 * wl["cfl"]
+    dt = s.cfl_dt(cfl)
+    with torch.cuda.stream(stream):
+        s.rk_step(dt, warmup, graph=True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            if i % 20 == 0:
+                dt = s.cfl_dt(cfl)
+            flush.zero_()
+            starts[i].record(stream)
+            s.rk_step(dt, 1, graph=True)
+            ends[i].record(stream)
+        stream.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        kst = min(steps, 50)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kst)]
+        for i in range(kst):
+            flush.zero_()
+            evs[i][0].record(stream)
+            for st in range(3):
+                s.stage(st, dt)
+                evs[i][st + 1].record(stream)
+        stream.synchronize()
+    s.check()
+    s.close()
+    stage = np.mean(np.array([[evs[i][k].elapsed_time(evs[i][k + 1]) for k in range(3)] for i in range(kst)]), axis=0)
+    ms = float(np.mean(step_ms))
+    alg = (2 + 3 + 3) * esz * dof
+    return dict(value=dof * 3 / (ms * 1e-3), ms_per_step=ms, dof=dof, stage_us=[float(v * 1e3) for v in stage],
+                achieved_gbs=alg / (float(np.sum(stage)) * 1e-3) / 1e9, limiter=bool(wl["solver"].get("limiter")))
+
+
+def measure_batch(torch, frsg, precision, steps, warmup, stream, flush):
+    """The batched workload: 256 seeded Burgers problems of uneven size and order, advanced
+    together by one persistent launch per stage (graph-replayed), L2 flushed between steps."""
+    wls = workloads.burgers_batch()
+    solvers = []
+    dof = 0
+    for wl in wls:
+        sv = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
+        x, z = sv.nodes()
+        sv.set_initial_nodal(workloads.nodal_values(wl["ic"], x, z))
+        solvers.append(sv)
+        E, Np, M, S = workload_sizes(wl)
+        dof += E * Np * M * S
+    dts = np.array([wl["cfl"] * (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"] / wl["lam0"]
+                    for wl in wls])
+    b = frsg.Batch(solvers, stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        b.rk_step(dts, warmup)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        l0 = b.launch_count()
+        for i in range(steps):
+            flush.zero_()
+            starts[i].record(stream)
+            b.rk_step(dts, 1)
+            ends[i].record(stream)
+        stream.synchronize()
+    launches = b.launch_count() - l0
+    for sv in solvers:
+        sv.check()
+    ms = float(np.mean([a.elapsed_time(c) for a, c in zip(starts, ends)]))
+    info = b.info()
+    b.close()
+    for sv in solvers:
+        sv.close()
+    esz = 8 if precision == "fp64" else 4
+    alg = (2 + 3 + 3) * esz * dof
+    return dict(value=dof * 3 / (ms * 1e-3), ms_per_step=ms, dof=dof, members=len(wls), launches_per_step=launches / steps,
+                step_gbs=alg / (ms * 1e-3) / 1e9, **info)
+
+
+def measure_adjoint(torch, frsg, stream, nsteps=64, k=16):
+    """Time of fr_sg_adjoint over the time of fr_sg_forward_record for the same run
+    (Burgers, 1024 elements, FP64, checkpoints every k steps)."""
+    wl = workloads.burgers_1d()
+    sv = frsg.Solver(stream=stream.cuda_stream, **wl["solver"])
+    x, z = sv.nodes()
+    sv.set_initial_nodal(workloads.nodal_values(wl["ic"], x, z))
+    u0 = torch.empty(sv.state_shape, dtype=torch.float64, device="cuda")
+    sv.get_state(u0)
+    dt = wl["cfl"] * (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"] / wl["lam0"]
+    lam = torch.zeros_like(u0)
+    g = torch.empty_like(u0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fw, bw = [], []
+    with torch.cuda.stream(stream):
+        for rep in range(4):
+            sv.set_state(u0)
+            sv.forward_record(dt, nsteps, k)
+            lam.zero_()
+            lam[:, :, 0, 0] = 1.0
+            stream.synchronize()
+            ev[0].record(stream)
+            sv.forward_record(dt, nsteps, k)
+            ev[1].record(stream)
+            sv.adjoint(lam, g)
+            ev[2].record(stream)
+            stream.synchronize()
+            if rep > 0:
+                fw.append(ev[0].elapsed_time(ev[1]))
+                bw.append(ev[1].elapsed_time(ev[2]))
+    sv.check()
+    sv.close()
+    f, a = float(np.median(fw)), float(np.median(bw))
+    return dict(workload=wl["name"], steps=nsteps, checkpoint_every=k, forward_ms=f, adjoint_ms=a, ratio=a / f)
+
+
 def cpu_baseline(wl, seconds):
     import oracle
     from oracle import integrate, tables
@@ -262,6 +391,18 @@ def run_ours(args):
     forms = {}
     for prec in ("fp64", "fp32"):
         forms[prec] = measure_form(torch, frsg, wl, prec, args.steps, args.warmup, stream, flush, ref)
+    extra = {}
+    batch = {}
+    adj = None
+    if not args.no_extra:
+        bsteps = max(3, min(args.steps, 50))
+        batch = {prec: measure_batch(torch, frsg, prec, bsteps, 3, stream, flush) for prec in ("fp64", "fp32")}
+        adj = measure_adjoint(torch, frsg, stream)
+        xsteps = max(3, min(args.steps, 100))
+        for name in ("sod", "shock_vortex"):
+            ewl = workloads.ALL[name]()
+            extra[ewl["name"]] = {prec: measure_extra(torch, frsg, ewl, prec, xsteps, 3, stream, flush)
+                                  for prec in ("fp64", "fp32")}
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -310,6 +451,15 @@ def run_ours(args):
                 "d2h_bytes_per_step": chosen["d2h"], "ms_per_step": chosen["e2e_ms"]},
         "gpu_launches": chosen["launches"],
         "clocks": clocks,
+        "batched": {"workload": "burgers_batch0: 256 problems, E 64-2048, P 1-4, N 2-10, Q 2N",
+                    **{p: {k2: (float(v2) if isinstance(v2, (int, float)) else v2) for k2, v2 in f.items()}
+                       for p, f in batch.items()}},
+        "adjoint": adj,
+        "other_workloads": {
+            k: {p: {"value": f["value"], "ms_per_step": f["ms_per_step"], "dof": f["dof"], "stage_us": f["stage_us"],
+                    "stage_gbs": f["achieved_gbs"], "stage_hbm_frac": f["achieved_gbs"] / hbm_peak,
+                    "limiter": f["limiter"]} for p, f in v.items()}
+            for k, v in extra.items()},
     }
     if rank == 0:
         print(json.dumps(line))

@@ -106,6 +106,11 @@ frsg_status fr_sg_set_stream(frsg_ctx* ctx, void* stream);
  * evaluates initial or boundary data at these nodes for the two projection calls below. */
 frsg_status fr_sg_get_nodes(const frsg_ctx* ctx, double* x, double* y, double* z);
 
+/* Host copies of the quadrature weights the library uses: wx[Np] Gauss-Legendre weights of
+ * the solution points on the reference element (tensor products in 2D; they sum to 2^dim),
+ * wz[Q] probability weights of the z-nodes (they sum to 1).  Either pointer may be NULL. */
+frsg_status fr_sg_get_quadrature(const frsg_ctx* ctx, double* wx, double* wz);
+
 /* Dirichlet ghost state of one boundary side (0..3 as in cfg->bc), given as host values
  * g[Q][S] at the z-nodes; projected onto the gPC modes like the initial data (§2.1, Eq. 6,
  * third line).  The ghost state is constant along the side. */
@@ -172,6 +177,41 @@ frsg_status fr_sg_set_replay(frsg_ctx* ctx, const uint8_t* flags, int nstages);
 
 /* Synchronise the context's stream and report (and clear) errors latched by kernels. */
 frsg_status fr_sg_check(frsg_ctx* ctx);
+
+/* Batch of independent 1D problems advanced together (uneven sizes, degrees and gPC orders).
+ * The paper treats one problem at a time; a batch exists so that many small uncertain
+ * instances fill the GPU.  fr_sg_batch_create takes n existing contexts (borrowed; they must
+ * outlive the batch), all 1D, scalar (advection or Burgers), without limiter, with the same
+ * equation and precision (FRSG_E_INVAL otherwise), and builds per-problem stage arguments and
+ * a tile list (at most 256/Q elements per tile, largest tiles first).
+ * fr_sg_batch_rk_step advances every member by nsteps SSP-RK3 steps, member i with step size
+ * dt[i] (host array of n): each stage is ONE persistent launch over all tiles of all members
+ * (grid = SMs x resident CTAs), the three stages replayed from a captured CUDA graph when
+ * use_graph = 1.  Each member's state, decisions and error word stay in its context. */
+typedef struct frsg_batch frsg_batch;
+frsg_status fr_sg_batch_create(frsg_ctx* const* ctxs, int n, void* stream, frsg_batch** out);
+void fr_sg_batch_destroy(frsg_batch* b);
+frsg_status fr_sg_batch_rk_step(frsg_batch* b, const double* dt, int nsteps, int use_graph);
+uint64_t fr_sg_batch_launch_count(const frsg_batch* b);
+/* Tile count, persistent grid size and dynamic shared memory per CTA of the batched launch. */
+frsg_status fr_sg_batch_info(const frsg_batch* b, int* ntiles, int* grid, size_t* smem);
+
+/* Discrete adjoint of fr_sg_rk_step for 1D periodic advection / Burgers contexts in
+ * FRSG_FP64 without limiter (FRSG_E_UNSUPPORTED otherwise).  The paper has no adjoint; it
+ * is the exact transpose of the linearised scheme of §2.1-§4.2 with the filter decisions of
+ * the forward run frozen and the Lax-Friedrichs dissipation max(lambda_L, lambda_R)
+ * differentiated along the branch the forward values take.
+ *
+ * fr_sg_forward_record advances the state by nsteps steps of size dt (as fr_sg_rk_step) and
+ * keeps, on the device, a checkpoint of the state every checkpoint_every steps and the
+ * filter decision of every stage.  Allocates its buffers on first use (and when a longer
+ * run needs more).
+ * fr_sg_adjoint then maps lambda_T = dQ/du(T) (DEVICE double [E][Np][M][S]) to
+ * grad_u0 = dQ/du(0) (DEVICE double, same layout) for the recorded run: each segment between
+ * checkpoints is recomputed with the recorded decisions replayed, then walked backwards
+ * stage by stage.  The context's state is the recorded final state again when it returns. */
+frsg_status fr_sg_forward_record(frsg_ctx* ctx, double dt, int nsteps, int checkpoint_every);
+frsg_status fr_sg_adjoint(frsg_ctx* ctx, const double* lambda_T, double* grad_u0);
 
 /* Elements per CTA of the stage kernel (the tile): te >= 1 sets it, te = 0 restores the
  * automatic choice.  Returns FRSG_E_INVAL when the tile does not fit in shared memory or

@@ -27,6 +27,7 @@ struct frsg_ctx {
     frsg::TabOff off{};
     std::vector<double> htab;
     double* d_tab = nullptr;
+    float* d_tabf = nullptr;      // float copy of the table block (FP32 contexts)
     double* d_ghost = nullptr;
     void* d_u = nullptr;
     void* d_u1 = nullptr;
@@ -44,6 +45,13 @@ struct frsg_ctx {
     uint64_t launches = 0;
     int TE = 1, TE_lim = 1;
     cudaGraphExec_t graph_exec = nullptr;
+    // recorded run for the adjoint: checkpoints every rec_k steps, filter decisions per stage
+    int rec_nsteps = 0, rec_k = 0, rec_cap_ckpt = 0, rec_cap_steps = 0, rec_cap_seg = 0;
+    double rec_dt = 0.0;
+    double* d_ckpt = nullptr;     // [n_ckpt][state]
+    uint8_t* d_log = nullptr;     // [3 * nsteps][E]
+    double* d_seg = nullptr;      // [3 * k][state]: stage inputs of one segment
+    double* d_work = nullptr;     // [4][state]: final state, lambda, stage cotangents
     int graph_kernels = 0;
 };
 
@@ -225,6 +233,7 @@ StageArgs base_args(frsg_ctx* c) {
     A.invJx = 2.0 * c->cfg.nx / (c->cfg.x1 - c->cfg.x0);
     A.invJy = c->cfg.dim == 2 ? 2.0 * c->cfg.ny / (c->cfg.y1 - c->cfg.y0) : 0.0;
     A.tab = c->d_tab;
+    A.tabf = c->d_tabf;
     A.off = c->off;
     A.ghost = c->d_ghost;
     for (int i = 0; i < 4; ++i) A.bc[i] = c->cfg.bc[i];
@@ -238,6 +247,7 @@ StageArgs base_args(frsg_ctx* c) {
     A.f_eps2 = c->cfg.f_eps2;
     A.s0 = c->cfg.s0;
     A.kappa = c->cfg.kappa;
+    A.det_ratio = frsg::detector_ratio(c->cfg.s0, c->cfg.kappa);
     A.err = c->d_err;
     A.TE = c->TE;
     return A;
@@ -271,6 +281,31 @@ cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
 // Stage s of an SSP-RK3 step (Shu-Osher form): limit the stage input, then
 // uout = a_s u^n + b_s (uin + dt L(uin)) followed by detector + filter.
 //   s = 0: u -> u1,  s = 1: u1 -> u2,  s = 2: u2 -> u (in place on u^n, element-local).
+cudaError_t issue_stage_ex(frsg_ctx* c, int s, double dt, uint8_t* flags_out, const uint8_t* replay_in) {
+    const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
+    void* bufs_in[3] = {c->d_u, c->d_u1, c->d_u2};
+    void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    if (c->cfg.limiter) {
+        cudaError_t e = launch_limiter(c, bufs_in[s], c->d_beta + (size_t)s * c->E);
+        if (e != cudaSuccess) return e;
+    }
+    StageArgs A = base_args(c);
+    A.uin = bufs_in[s];
+    A.ubase = c->d_u;
+    A.uout = bufs_out[s];
+    A.a = ca[s];
+    A.b = cb[s];
+    A.c = cb[s];
+    A.dtp = c->d_dt;
+    A.dt_filter = dt;
+    A.do_filter = filt ? 1 : 0;
+    A.flags = flags_out;
+    A.replay = replay_in;
+    return launch_stage(c, A);
+}
+
 cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
     const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
     void* bufs_in[3] = {c->d_u, c->d_u1, c->d_u2};
@@ -337,6 +372,10 @@ int choose_tile_2d(const frsg_ctx* c) {
 namespace frsg {
 std::string noalloc_validate(const frsg_config& c) { return validate(c); }
 
+double detector_ratio(double s0, double kappa) {
+    return std::pow(10.0, s0 - (2.0 * kappa / M_PI) * std::asin(0.98));
+}
+
 }  // namespace frsg
 
 extern "C" {
@@ -372,6 +411,13 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     };
     cudaError_t e;
     if ((e = cudaMalloc(&ctx->d_tab, sizeof(double) * ctx->off.total)) != cudaSuccess) return cleanup_fail(e, "tables");
+    if (!ctx->fp64) {
+        if ((e = cudaMalloc(&ctx->d_tabf, sizeof(float) * ctx->off.total)) != cudaSuccess)
+            return cleanup_fail(e, "float tables");
+        std::vector<float> tf(ctx->htab.begin(), ctx->htab.end());
+        e = cudaMemcpy(ctx->d_tabf, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cleanup_fail(e, "float tables upload");
+    }
     if ((e = cudaMalloc(&ctx->d_ghost, sizeof(double) * 4 * ctx->M * ctx->S)) != cudaSuccess) return cleanup_fail(e, "ghost");
     if ((e = cudaMalloc(&ctx->d_u, ctx->esz * nstate)) != cudaSuccess) return cleanup_fail(e, "state");
     if ((e = cudaMalloc(&ctx->d_u1, ctx->esz * nstate)) != cudaSuccess) return cleanup_fail(e, "stage 1");
@@ -413,6 +459,7 @@ void fr_sg_destroy(frsg_ctx* ctx) {
     if (!ctx) return;
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     cudaFree(ctx->d_tab);
+    cudaFree(ctx->d_tabf);
     cudaFree(ctx->d_ghost);
     cudaFree(ctx->d_u);
     cudaFree(ctx->d_u1);
@@ -424,6 +471,10 @@ void fr_sg_destroy(frsg_ctx* ctx) {
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_speed);
     cudaFree(ctx->d_replay);
+    cudaFree(ctx->d_ckpt);
+    cudaFree(ctx->d_log);
+    cudaFree(ctx->d_seg);
+    cudaFree(ctx->d_work);
     delete ctx;
 }
 
@@ -467,6 +518,17 @@ frsg_status fr_sg_get_nodes(const frsg_ctx* ctx, double* x, double* y, double* z
     }
     if (z)
         for (int q = 0; q < ctx->Q; ++q) z[q] = ctx->ht.z[q];
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_get_quadrature(const frsg_ctx* ctx, double* wx, double* wz) {
+    if (!ctx) return FRSG_E_INVAL;
+    const int n1 = ctx->n1;
+    if (wx)
+        for (int j = 0; j < ctx->Np; ++j)
+            wx[j] = ctx->cfg.dim == 1 ? ctx->ht.w[j] : ctx->ht.w[j % n1] * ctx->ht.w[j / n1];
+    if (wz)
+        for (int q = 0; q < ctx->Q; ++q) wz[q] = ctx->ht.wz[q];
     return FRSG_OK;
 }
 
@@ -731,6 +793,298 @@ frsg_status fr_sg_check(frsg_ctx* ctx) {
 }
 
 uint64_t fr_sg_launch_count(const frsg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+static frsg_status adjoint_supported(frsg_ctx* ctx) {
+    const frsg_config& c = ctx->cfg;
+    if (c.dim != 1 || !ctx->fp64 || c.equation == FRSG_EQ_EULER || c.limiter || c.bc[0] != FRSG_BC_PERIODIC)
+        return fail(ctx, FRSG_E_UNSUPPORTED,
+                    "the adjoint covers 1D periodic advection/Burgers contexts in FRSG_FP64 without limiter");
+    return FRSG_OK;
+}
+
+static cudaError_t grow(void** p, int* cap, int want, size_t unit) {
+    if (want <= *cap) return cudaSuccess;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, unit * (size_t)want);
+    if (e == cudaSuccess) *cap = want;
+    return e;
+}
+
+struct frsg_batch {
+    std::vector<frsg_ctx*> ctx;
+    cudaStream_t stream = nullptr;
+    bool fp64 = true;
+    int equation = FRSG_EQ_BURGERS;
+    frsg::StageArgs* d_args = nullptr;   // [3][n]
+    int4* d_tiles = nullptr;
+    double* d_dt = nullptr;               // [n]
+    int ntiles = 0, grid = 1;
+    size_t smem = 0;
+    uint64_t launches = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<double> dt_set;
+};
+
+frsg_status fr_sg_batch_create(frsg_ctx* const* ctxs, int n, void* stream, frsg_batch** out) {
+    if (!out) return FRSG_E_INVAL;
+    *out = nullptr;
+    if (!ctxs || n < 1) return FRSG_E_INVAL;
+    const frsg_ctx* c0 = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        const frsg_ctx* c = ctxs[i];
+        if (!c || c->cfg.dim != 1 || c->cfg.limiter || c->S != 1 || c->fp64 != c0->fp64 ||
+            c->cfg.equation != c0->cfg.equation || c->cfg.equation == FRSG_EQ_EULER) {
+            std::fprintf(stderr, "fr_sg_batch_create: member %d must be a 1D scalar problem without limiter, "
+                                 "with the equation and precision of member 0\n", i);
+            return FRSG_E_INVAL;
+        }
+    }
+    frsg_batch* b = new (std::nothrow) frsg_batch();
+    if (!b) return FRSG_E_NOMEM;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->fp64 = c0->fp64;
+    b->equation = c0->cfg.equation;
+    b->dt_set.assign(n, -1.0);
+    auto bail = [&](cudaError_t e) {
+        std::fprintf(stderr, "fr_sg_batch_create: %s\n", cudaGetErrorString(e));
+        fr_sg_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? FRSG_E_NOMEM : FRSG_E_CUDA;
+    };
+    cudaError_t e = cudaMalloc(&b->d_dt, sizeof(double) * n);
+    if (e != cudaSuccess) return bail(e);
+    // per-problem stage arguments; tiles of at most 256 threads (rows = 256 / Q elements)
+    std::vector<frsg::StageArgs> args(3 * (size_t)n);
+    struct T4 { int inst, e0, ne, np; double cost; };
+    std::vector<T4> tiles;
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int i = 0; i < n; ++i) {
+        frsg_ctx* c = b->ctx[i];
+        const int rows = std::max(1, 256 / c->Q);
+        void* bin[3] = {c->d_u, c->d_u1, c->d_u2};
+        void* bout[3] = {c->d_u1, c->d_u2, c->d_u};
+        for (int s = 0; s < 3; ++s) {
+            frsg::StageArgs A = base_args(c);
+            A.uin = bin[s];
+            A.ubase = c->d_u;
+            A.uout = bout[s];
+            A.a = ca[s];
+            A.b = cb[s];
+            A.c = cb[s];
+            A.dtp = b->d_dt + i;
+            A.do_filter = c->cfg.filter != FRSG_FILTER_NONE ? 1 : 0;
+            A.flags = c->d_flags + (size_t)s * c->E;
+            A.replay = nullptr;
+            A.TE = rows;
+            args[(size_t)s * n + i] = A;
+        }
+        b->smem = std::max(b->smem, frsg::stage1d_smem_bytes(b->fp64, rows, c->Np, c->M, c->Q, 1));
+        for (int e0 = 0; e0 < c->E; e0 += rows) {
+            const int ne = std::min(rows, c->E - e0);
+            tiles.push_back({i, e0, ne, c->Np, (double)ne * c->Np * c->M * c->Q});
+        }
+    }
+    // largest tiles first: CTA b takes tiles b, b + grid, ... so the big ones spread first
+    std::stable_sort(tiles.begin(), tiles.end(), [](const T4& a, const T4& c) { return a.cost > c.cost; });
+    std::vector<int4> t4(tiles.size());
+    for (size_t t = 0; t < tiles.size(); ++t) t4[t] = make_int4(tiles[t].inst, tiles[t].e0, tiles[t].ne, tiles[t].np);
+    b->ntiles = (int)t4.size();
+    if (b->smem > 220 * 1024) {
+        fr_sg_batch_destroy(b);
+        return FRSG_E_INVAL;
+    }
+    e = cudaMalloc(&b->d_args, sizeof(frsg::StageArgs) * args.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(int4) * t4.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_args, args.data(), sizeof(frsg::StageArgs) * args.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, t4.data(), sizeof(int4) * t4.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(e);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = frsg::stage1d_batched_blocks_per_sm(b->fp64, b->equation, b->smem);
+    b->grid = std::max(1, std::min(b->ntiles, per_sm * sms));
+    *out = b;
+    return FRSG_OK;
+}
+
+void fr_sg_batch_destroy(frsg_batch* b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_args);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_dt);
+    delete b;
+}
+
+static cudaError_t batch_issue_step(frsg_batch* b) {
+    const int n = (int)b->ctx.size();
+    for (int s = 0; s < 3; ++s) {
+        cudaError_t e = frsg::launch_stage1d_batched(b->fp64, b->equation, b->d_args + (size_t)s * n, b->d_tiles,
+                                                     b->ntiles, b->smem, b->grid, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+frsg_status fr_sg_batch_rk_step(frsg_batch* b, const double* dt, int nsteps, int use_graph) {
+    if (!b || !dt || nsteps < 0) return FRSG_E_INVAL;
+    const int n = (int)b->ctx.size();
+    bool changed = false;
+    for (int i = 0; i < n; ++i) {
+        if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return FRSG_E_INVAL;
+        changed |= dt[i] != b->dt_set[i];
+    }
+    if (changed) {
+        if (cudaMemcpyAsync(b->d_dt, dt, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+            return FRSG_E_CUDA;
+        b->dt_set.assign(dt, dt + n);
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        if (use_graph) {
+            if (!b->graph) {
+                cudaStream_t cap = b->stream;
+                bool own = false;
+                if (cap == nullptr) {
+                    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return FRSG_E_CUDA;
+                    own = true;
+                }
+                cudaStream_t saved = b->stream;
+                b->stream = cap;
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e1 = batch_issue_step(b);
+                    e = cudaStreamEndCapture(cap, &g);
+                    if (e1 != cudaSuccess) e = e1;
+                }
+                b->stream = saved;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (own) {
+                    cudaStreamSynchronize(cap);
+                    cudaStreamDestroy(cap);
+                }
+                if (e != cudaSuccess) return FRSG_E_CUDA;
+            }
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return FRSG_E_CUDA;
+        } else if (batch_issue_step(b) != cudaSuccess) {
+            return FRSG_E_CUDA;
+        }
+        b->launches += 3;
+    }
+    return FRSG_OK;
+}
+
+uint64_t fr_sg_batch_launch_count(const frsg_batch* b) { return b ? b->launches : 0; }
+
+frsg_status fr_sg_batch_info(const frsg_batch* b, int* ntiles, int* grid, size_t* smem) {
+    if (!b) return FRSG_E_INVAL;
+    if (ntiles) *ntiles = b->ntiles;
+    if (grid) *grid = b->grid;
+    if (smem) *smem = b->smem;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_forward_record(frsg_ctx* ctx, double dt, int nsteps, int checkpoint_every) {
+    if (!ctx) return FRSG_E_INVAL;
+    frsg_status st = adjoint_supported(ctx);
+    if (st != FRSG_OK) return st;
+    if (nsteps < 1 || checkpoint_every < 1 || !(dt > 0.0) || !std::isfinite(dt))
+        return fail(ctx, FRSG_E_INVAL, "need nsteps >= 1, checkpoint_every >= 1, dt > 0");
+    const size_t nstate = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    const int nck = (nsteps + checkpoint_every - 1) / checkpoint_every;
+    int cap_work = ctx->d_work ? 1 : 0;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(grow((void**)&ctx->d_ckpt, &ctx->rec_cap_ckpt, nck, sizeof(double) * nstate));
+    CK(grow((void**)&ctx->d_log, &ctx->rec_cap_steps, nsteps, 3 * (size_t)ctx->E));
+    CK(grow((void**)&ctx->d_seg, &ctx->rec_cap_seg, 3 * checkpoint_every, sizeof(double) * nstate));
+    CK(grow((void**)&ctx->d_work, &cap_work, 1, 5 * sizeof(double) * nstate));
+    CK(set_dt(ctx, dt));
+    double* u = static_cast<double*>(ctx->d_u);
+    for (int n = 0; n < nsteps; ++n) {
+        if (n % checkpoint_every == 0)
+            CK(cudaMemcpyAsync(ctx->d_ckpt + (size_t)(n / checkpoint_every) * nstate, u, sizeof(double) * nstate,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int s = 0; s < 3; ++s) CK(issue_stage_ex(ctx, s, dt, ctx->d_log + (size_t)(3 * n + s) * ctx->E, nullptr));
+    }
+    CK(cudaMemcpyAsync(ctx->d_work, u, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->rec_nsteps = nsteps;
+    ctx->rec_k = checkpoint_every;
+    ctx->rec_dt = dt;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_adjoint(frsg_ctx* ctx, const double* lambda_T, double* grad_u0) {
+    if (!ctx) return FRSG_E_INVAL;
+    frsg_status st = adjoint_supported(ctx);
+    if (st != FRSG_OK) return st;
+    if (!lambda_T || !grad_u0) return fail(ctx, FRSG_E_INVAL, "null cotangent or gradient");
+    if (ctx->rec_nsteps < 1) return fail(ctx, FRSG_E_INVAL, "no recorded run: call fr_sg_forward_record first");
+    const size_t nstate = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    const int nsteps = ctx->rec_nsteps, k = ctx->rec_k;
+    const double dt = ctx->rec_dt;
+    const frsg_config& c = ctx->cfg;
+    const bool filt = c.filter != FRSG_FILTER_NONE;
+    const double alpha_dt = c.f_alpha * dt;
+    const double invJx = 2.0 * c.nx / (c.x1 - c.x0);
+    double* fin = ctx->d_work;
+    double* lam = fin + nstate;        // cotangent of the current step's output
+    double* lb = lam + nstate;         // cotangent of the step's input (accumulated)
+    double* t1 = lb + nstate;          // filter-transposed stage cotangent
+    double* t2 = t1 + nstate;          // cotangent of a stage input
+    double* u = static_cast<double*>(ctx->d_u);
+    CK(set_dt(ctx, dt));
+    CK(cudaMemcpyAsync(lam, lambda_T, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+    const int nseg = (nsteps + k - 1) / k;
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int n0 = sg * k, n1 = std::min(nsteps, n0 + k);
+        CK(cudaMemcpyAsync(u, ctx->d_ckpt + (size_t)sg * nstate, sizeof(double) * nstate, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        for (int n = n0; n < n1; ++n) {
+            double* seg = ctx->d_seg + (size_t)3 * (n - n0) * nstate;
+            CK(cudaMemcpyAsync(seg, u, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+            for (int s = 0; s < 3; ++s) {
+                CK(issue_stage_ex(ctx, s, dt, nullptr, ctx->d_log + (size_t)(3 * n + s) * ctx->E));
+                if (s < 2)
+                    CK(cudaMemcpyAsync(seg + (size_t)(s + 1) * nstate, s == 0 ? ctx->d_u1 : ctx->d_u2,
+                                       sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+            }
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+            const double* seg = ctx->d_seg + (size_t)3 * (n - n0) * nstate;
+            const double* mu = lam;
+            for (int s = 2; s >= 0; --s) {
+                const uint8_t* fl = ctx->d_log + (size_t)(3 * n + s) * ctx->E;
+                const double* y = mu;
+                if (filt) {
+                    ctx->launches += 1;
+                    CK(frsg::launch_filter_transpose(c.P, mu, t1, fl, ctx->d_tab, ctx->off, c.filter, alpha_dt,
+                                                     ctx->E, ctx->M, ctx->S, ctx->stream));
+                    y = t1;
+                }
+                ctx->launches += 1;
+                CK(frsg::launch_adjoint_stage1d(c.P, c.equation, seg + (size_t)s * nstate, y, t2, lb, ca[s], cb[s],
+                                                cb[s] * dt, s == 2 ? 1 : 0, s == 0 ? 1 : 0, ctx->d_tab, ctx->off,
+                                                ctx->E, ctx->M, ctx->Q, ctx->TE, invJx, c.adv_speed, ctx->stream));
+                if (s > 0) {
+                    // the next stage down receives the cotangent of this stage's input
+                    CK(cudaMemcpyAsync(lam, t2, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+                    mu = lam;
+                }
+            }
+            CK(cudaMemcpyAsync(lam, lb, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+    }
+    CK(cudaMemcpyAsync(grad_u0, lam, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(u, fin, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+    return FRSG_OK;
+}
 
 frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out) {
     if (!ctx) return FRSG_E_INVAL;

@@ -1,12 +1,18 @@
-// Detector + modal filter epilogue shared by the 1D and 2D stage kernels (§4.1-4.2).
+// Projection / combination and detector + modal filter epilogue shared by the 1D and 2D
+// stage kernels (§2.1 Eq. 6; §4.1-4.2).
 //
-// Input: the tile's new coefficients in shared memory (nodal in x, modal in z).
-// Pass A transforms every element to the modal basis Psi_m Phi_k with the element
-// Vandermonde inverse (§4, Eqs. 27-28, nodal = V modal); the detector sums the squared
-// coefficients of the first variable (orthonormal basis: inner products are plain sums),
-// flags elements with theta < 0.99 (§4.2, Eq. 47); pass B writes Vf (Lambda o modal)
-// for flagged elements (§4.1, Eq. 34) and the unchanged coefficients otherwise.
-// All of it runs in the state's precision T; only theta's log10/sin run in double.
+// Thread layout inside an element: "k-lane" kl in [0, nk) owns the gPC modes k = kl,
+// kl + nk, ...; "m-lane" ml in [0, nm) owns the point / physical-mode rows ml, ml + nm, ...
+// Loops over points, physical modes and variables have compile-time bounds, so no index
+// is decoded by integer division.
+//
+// The detector transforms every element to the modal basis Psi_m Phi_k with the element
+// Vandermonde inverse (§4, Eqs. 27-28, nodal = V modal), sums the squared coefficients of the
+// first variable (orthonormal bases: inner products are plain sums) and flags elements with
+// theta < 0.99 (§4.2, Eq. 47).  theta falls monotonically with S_e = top/total energy, so
+// the test is S_e > 10^(s0 - (2 kappa/pi) asin 0.98), with no logarithm or sine per element.
+// Flagged elements get Vf (Lambda o modal) (§4.1, Eq. 34).  Everything runs in the state's
+// precision T.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,97 +22,134 @@
 
 namespace frsg {
 
+// The table block in the kernel's precision.
+template <typename T>
+__device__ inline const T* table_block(const StageArgs& A);
+template <>
+__device__ inline const double* table_block<double>(const StageArgs& A) { return A.tab; }
+template <>
+__device__ inline const float* table_block<float>(const StageArgs& A) { return A.tabf; }
+
 // Lambda[m][k] for this launch: exp(-alpha dt E[m][k]) (exponential, E = sum eta^s) or the
 // stored L2 factor.
 template <typename T>
 __device__ inline void load_filter_strengths(const StageArgs& A, int NP, T* sLam, int tid, int nthr, double dt) {
     const int n = NP * A.M;
+    const T* tab = table_block<T>(A);
+    const T adt = (T)(A.f_alpha * dt);
     for (int i = tid; i < n; i += nthr) {
-        const double v = A.tab[A.off.lam + i];
-        if (A.filter == FRSG_FILTER_EXP) sLam[i] = (T)exp(-(T)(A.f_alpha * dt) * (T)v);
-        else sLam[i] = (T)v;
+        const T v = tab[A.off.lam + i];
+        sLam[i] = A.filter == FRSG_FILTER_EXP ? exp(-adt * v) : v;
     }
 }
 
-__device__ inline int detector_flag(double top, double total, double s0, double kappa) {
-    if (!(total > 0.0) || !(top > 0.0)) return 0;
-    const double se = log10(top / total);
-    double theta;
-    if (se < s0 - kappa) theta = 1.0;
-    else if (se > s0 + kappa) theta = 0.0;
-    else theta = 0.5 * (1.0 - sin(M_PI * (se - s0) / (2.0 * kappa)));
-    return theta < 0.99 ? 1 : 0;
+// a4 + a8 for one element: uhat_new[j][k][s] = cb*U + cc*sum_q Pz[k][q] G[j][s][q] + ca*B.
+// G is the element's nodal residual [NP][S][Q]; U, B its stage input and SSP base [NP][M][S].
+// Writes the result to dst (shared memory or global).
+template <typename T, int NP, int S>
+__device__ inline bool project_combine(const T* G, const T* U, const T* B, const T* sPz, T* dst, int M, int Q, int kl,
+                                       int nk, int ml, int nm, T ca, T cb, T cc, bool use_base) {
+    bool bad = false;
+    for (int k = kl; k < M; k += nk) {
+        for (int j = ml; j < NP; j += nm) {
+            T acc[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) acc[s] = T(0);
+            const T* g = G + j * S * Q;
+            for (int q = 0; q < Q; ++q) {
+                const T pz = sPz[k * Q + q];
+#pragma unroll
+                for (int s = 0; s < S; ++s) acc[s] += pz * g[s * Q + q];
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const int o = (j * M + k) * S + s;
+                T val = cb * U[o] + cc * acc[s];
+                if (use_base) val += ca * B[o];
+                dst[o] = val;
+                bad |= !finite_val(val);
+            }
+        }
+    }
+    return bad;
 }
 
-// tid/nthr: flat thread index / count of the CTA; te: this thread's element in the tile;
-// lt/nlt: this thread's index / count within its element; sMod: scratch >= TE*NP*M*S.
+// a9 + a10 for the tile.  Us: the tile's new coefficients [ne][NP][M][S] in shared memory;
+// Mod: scratch of the same size; te: this thread's element; active: te < ne.
 template <typename T, int NP, int S>
-__device__ inline bool detector_filter_store(const StageArgs& A, const T* sU, T* sMod, const T* sVf,
-                                             const T* sVfinv, const T* sLam, const T* sTop, T* sRed, int* sFlag,
-                                             int tid, int nthr, int te, int lt, int nlt, bool active, int ne,
-                                             int e0, T* uout, size_t gbase) {
+__device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T* Mod, const T* sVf, const T* sVfinv,
+                                             const T* sLam, const T* sTop, T* sRed, int* sFlag, int te, int kl,
+                                             int nk, int ml, int nm, bool active, bool member, int e0, T* uout,
+                                             size_t gbase) {
     const int M = A.M;
     const int elsz = NP * M * S;
-    const int nout = ne * elsz;
-    // pass A: modal coefficients
-    for (int o = tid; o < nout; o += nthr) {
-        const int el = o / elsz, rr = o - el * elsz;
-        const int m = rr / (M * S), ks = rr - m * M * S;
-        const T* ue = sU + el * elsz + ks;
-        const T* vi = sVfinv + m * NP;
-        T acc = T(0);
-#pragma unroll
-        for (int jp = 0; jp < NP; ++jp) acc += vi[jp] * ue[jp * M * S];
-        sMod[o] = acc;
-    }
-    __syncthreads();
-    // detector energies of variable 0, fixed-order partial sums per element
+    const T* ue = Us + te * elsz;
+    T* me = Mod + te * elsz;
+    T tot = T(0), top = T(0);
+    // pass A: modal coefficients of the own element; energies of variable 0
     if (active) {
-        T tot = T(0), top = T(0);
-        const T* um = sMod + te * elsz;
-        for (int i = lt; i < NP * M; i += nlt) {
-            const int m = i / M, k = i - m * M;
-            const T v = um[i * S];
-            const T v2 = v * v;
-            tot += v2;
-            if (sTop[m] != T(0) || k == M - 1) top += v2;
+        for (int k = kl; k < M; k += nk) {
+            for (int m = ml; m < NP; m += nm) {
+                T acc[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) acc[s] = T(0);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const T vi = sVfinv[m * NP + j];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) acc[s] += vi * ue[(j * M + k) * S + s];
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s) me[(m * M + k) * S + s] = acc[s];
+                const T v2 = acc[0] * acc[0];
+                tot += v2;
+                if (sTop[m] != T(0) || k == M - 1) top += v2;
+            }
         }
+    }
+    const int lt = ml * nk + kl, nlt = nk * nm;
+    if (member) {
         sRed[(te * nlt + lt) * 2 + 0] = tot;
         sRed[(te * nlt + lt) * 2 + 1] = top;
     }
     __syncthreads();
     if (active && lt == 0) {
-        double tot = 0.0, top = 0.0;
+        T t0 = T(0), t1 = T(0);
         for (int i = 0; i < nlt; ++i) {
-            tot += (double)sRed[(te * nlt + i) * 2 + 0];
-            top += (double)sRed[(te * nlt + i) * 2 + 1];
+            t0 += sRed[(te * nlt + i) * 2 + 0];
+            t1 += sRed[(te * nlt + i) * 2 + 1];
         }
         const int e = e0 + te;
         int fl;
         if (A.replay) fl = A.replay[e] ? 1 : 0;
         else if (!A.sensor) fl = 1;
-        else fl = detector_flag(top, tot, A.s0, A.kappa);
+        else fl = (t1 > T(0) && t1 > (T)A.det_ratio * t0) ? 1 : 0;
         sFlag[te] = fl;
         if (A.flags) A.flags[e] = (uint8_t)fl;
     }
     __syncthreads();
-    // pass B: filtered or unchanged coefficients, one coalesced store
+    // pass B: filtered or unchanged coefficients
     bool bad = false;
-    for (int o = tid; o < nout; o += nthr) {
-        const int el = o / elsz, rr = o - el * elsz;
-        T val;
-        if (sFlag[el]) {
-            const int j = rr / (M * S), ks = rr - j * M * S, k = ks / S;
-            const T* um = sMod + el * elsz + ks;
-            const T* vf = sVf + j * NP;
-            val = T(0);
+    if (active) {
+        const bool flag = sFlag[te] != 0;
+        T* dst = uout + gbase + (size_t)te * elsz;
+        for (int k = kl; k < M; k += nk) {
+            for (int j = ml; j < NP; j += nm) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) val += vf[m] * sLam[m * M + k] * um[m * M * S];
-        } else {
-            val = sU[o];
+                for (int s = 0; s < S; ++s) {
+                    T val;
+                    if (flag) {
+                        val = T(0);
+#pragma unroll
+                        for (int m = 0; m < NP; ++m) val += sVf[j * NP + m] * sLam[m * M + k] * me[(m * M + k) * S + s];
+                    } else {
+                        val = ue[(j * M + k) * S + s];
+                    }
+                    dst[(j * M + k) * S + s] = val;
+                    bad |= !finite_val(val);
+                }
+            }
         }
-        uout[gbase + o] = val;
-        bad |= !finite_val(val);
     }
     return bad;
 }

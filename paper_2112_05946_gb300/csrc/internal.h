@@ -52,12 +52,14 @@ struct StageArgs {
     int E, nx, ny, M, Q;
     double invJx, invJy;   // 2 / element width, 2 / element height
     const double* tab;     // device table block
+    const float* tabf;     // the same block in float (FP32 contexts), or null
     TabOff off;
     const double* ghost;   // [4][M][S] ghost gPC states of Dirichlet sides
     int bc[4];
     double adv, gamma;
     int do_filter, filter, sensor;
     double f_alpha, f_s, f_eps1, f_eps2, s0, kappa;
+    double det_ratio;      // theta < 0.99  <=>  S_e > det_ratio (theta decreases with S_e)
     const uint8_t* replay; // [E] filter decisions to use instead of the detector, or null
     uint8_t* flags;        // [E] filter decisions taken, or null
     unsigned* err;
@@ -79,6 +81,11 @@ struct LimitArgs {
 // Launch wrappers (kern1d.cu / kern2d.cu / kmisc.cu).  Return cudaGetLastError().
 cudaError_t launch_stage1d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st);
 cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st);
+// Persistent launch over tiles (problem, first element, element count, points per element)
+// of many 1D problems; args: device array of one StageArgs per problem.
+cudaError_t launch_stage1d_batched(bool fp64, int equation, const StageArgs* args, const int4* tiles, int ntiles,
+                                   size_t smem, int grid, cudaStream_t st);
+int stage1d_batched_blocks_per_sm(bool fp64, int equation, size_t smem);
 cudaError_t launch_limit(bool fp64, const LimitArgs& A, cudaStream_t st);
 cudaError_t launch_project(bool fp64, const double* u0, void* uhat, int E, int Np, int M, int Q, int S,
                            const double* tab, TabOff off, cudaStream_t st);
@@ -87,6 +94,17 @@ cudaError_t launch_moments(bool fp64, const void* uhat, double* mean, double* va
 cudaError_t launch_max_speed(bool fp64, const void* uhat, int E, int Np, int M, int Q, int S, int dim,
                              int equation, double adv, double gamma, const double* tab, TabOff off,
                              unsigned long long* out_bits, cudaStream_t st);
+// Discrete adjoint kernels (kadjoint.cu), 1D scalar FP64.
+cudaError_t launch_filter_transpose(int P, const double* mu, double* out, const uint8_t* flags, const double* tab,
+                                    TabOff off, int filter, double alpha_dt, int E, int M, int S, cudaStream_t st);
+cudaError_t launch_adjoint_stage1d(int P, int equation, const double* v, const double* y, double* lam_v,
+                                   double* lam_base, double a, double b, double cdt, int base_init, int accumulate,
+                                   const double* tab, TabOff off, int E, int M, int Q, int TE, double invJx,
+                                   double adv, cudaStream_t st);
+
+// 10^(s0 - (2 kappa / pi) asin(0.98)): the S_e at which theta of §4.2, Eq. 47 equals 0.99.
+double detector_ratio(double s0, double kappa);
+
 cudaError_t launch_convert(const void* src, void* dst, size_t n, bool to_float, cudaStream_t st);
 
 }  // namespace frsg

@@ -1,21 +1,20 @@
 // Fused FR-SG stage kernel on a 1D mesh.
 //
 // One CTA owns TE consecutive elements; thread (q, te) owns z-node q of element te.
-// Per stage, entirely on chip after one coalesced load of the elements' coefficients:
+// One coalesced sweep loads the tile, its two neighbour elements (the halo) and the
+// SSP base state into shared memory; then, on chip:
 //   a2  u(r_j, z_q) = sum_k Phi_k(z_q) uhat_jk            (§2.1, Eq. 2)
-//   a5  face traces u(+-1, z_q) by ell_j(+-1)             (§3.3)
-//   a6  LLF flux at both faces from the neighbours' traces (§3.3), halo traces of the
-//       two elements next to the tile are recomputed from global memory
+//   a5  face traces u(+-1, z_q) by ell_j(+-1)             (§3.3), halo traces included
+//   a6  LLF flux at both faces of every element           (§3.3)
 //   a3  f(u) at the solution points                       (§3.2, Eq. 15)
 //   a7  d f/dr (r_j) = sum_m D_jm f_m + (fI_L - fD_L) h_L'(r_j) + (fI_R - fD_R) h_R'(r_j)
 //       (§3.4, Eq. 21), residual -d f/dr / J, still nodal in z
 //   a4  Galerkin projection onto Phi_k of that nodal residual (§2.1, Eq. 6).  The
 //       projection is linear, so projecting the residual once equals projecting the
 //       flux and the interface flux separately as §3 orders it (up to rounding).
-//   a8  SSP combination uout = a*ubase + b*uin + c*L(uin)
+//   a8  SSP combination uout = a*ubase + b*uin + c*dt*L(uin)
 //   a9  detector on the first variable (§4.2, Eqs. 46-47)
-//   a10 filter of flagged elements, uhat <- Vx (Lambda o Vx^{-1} uhat) (§4.1, Eq. 34)
-//       and one coalesced store.
+//   a10 filter of flagged elements (§4.1, Eq. 34) and one coalesced store.
 #include <cuda_runtime.h>
 
 #include "epilogue.cuh"
@@ -26,98 +25,106 @@ namespace frsg {
 namespace {
 
 template <typename T>
-struct Smem1d {
-    T *U, *G, *Tr, *Vz, *Pz, *D, *lm, *lp, *dhL, *dhR, *Vf, *Vfinv, *Lam, *Top, *Red;
-    int* flag;
-};
-
-template <typename T>
 __host__ __device__ inline size_t smem1d_bytes(int TE, int NP, int M, int Q, int S) {
     size_t n = 0;
-    n += (size_t)TE * NP * M * S;          // U
-    n += (size_t)TE * NP * S * (Q > M ? Q : M);   // G (nodal residual, later the modal coefficients)
-    n += (size_t)(TE + 2) * 2 * S * Q;     // Tr
-    n += 2 * (size_t)M * Q;                // Vz, Pz
-    n += (size_t)NP * NP + 4 * NP;         // D, lm, lp, dhL, dhR
-    n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;   // Vf, Vfinv, Lam, Top
-    n += (size_t)2 * TE * Q;               // Red
+    n += (size_t)(TE + 2) * NP * M * S;              // U: halo + tile coefficients (tile later the new state)
+    n += (size_t)TE * NP * M * S;                    // B: SSP base state of the tile
+    n += (size_t)TE * NP * S * (Q > M ? Q : M);      // G: nodal residual, later the modal coefficients
+    n += (size_t)(TE + 2) * 2 * S * Q;               // Tr: face traces [slot][side][s][q]
+    n += 2 * (size_t)M * Q;                          // Vz, Pz
+    n += (size_t)NP * NP + 4 * NP;                   // D, lm, lp, dhL, dhR
+    n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;  // Vf, Vfinv, Lam, Top
+    n += (size_t)2 * TE * Q;                         // Red
     return n * sizeof(T) + (size_t)TE * sizeof(int) + 16;
 }
 
+// One tile: elements e0 .. e0+ne-1 (ne <= A.TE) of one problem.  (tq, te): this thread's
+// z-node and element row (rows >= A.TE or lanes >= Q idle but take part in the barriers);
+// tid / nthr: flat thread index / count of the CTA, used for cooperative loads.
 template <typename T, int NP, int S, int EQ>
-__global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Q = A.Q, M = A.M, TE = A.TE;
-    const int tq = threadIdx.x, te = threadIdx.y;
-    const int tid = te * Q + tq, nthr = Q * TE;
-    const int e0 = blockIdx.x * TE;
-    const int ne = min(TE, A.E - e0);
+__device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne, int tq, int te, int tid, int nthr,
+                                             unsigned char* smem_raw) {
+    const int Q = A.Q, M = A.M, TE = A.TE, E = A.E;
     const int elsz = NP * M * S;
     const T adv = (T)A.adv, gamma = (T)A.gamma;
     const T* uin = static_cast<const T*>(A.uin);
+    const T* ubase = static_cast<const T*>(A.ubase);
+    const bool periodic = A.bc[0] == FRSG_BC_PERIODIC;
 
-    Smem1d<T> sm;
-    {
-        T* p = reinterpret_cast<T*>(smem_raw);
-        sm.U = p; p += (size_t)TE * elsz;
-        sm.G = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
-        sm.Tr = p; p += (size_t)(TE + 2) * 2 * S * Q;
-        sm.Vz = p; p += M * Q;
-        sm.Pz = p; p += M * Q;
-        sm.D = p; p += NP * NP;
-        sm.lm = p; p += NP;
-        sm.lp = p; p += NP;
-        sm.dhL = p; p += NP;
-        sm.dhR = p; p += NP;
-        sm.Vf = p; p += NP * NP;
-        sm.Vfinv = p; p += NP * NP;
-        sm.Lam = p; p += NP * M;
-        sm.Top = p; p += NP;
-        sm.Red = p; p += 2 * TE * Q;
-        sm.flag = reinterpret_cast<int*>(p);
-    }
+    T* p = reinterpret_cast<T*>(smem_raw);
+    T* sU = p; p += (size_t)(TE + 2) * elsz;
+    T* sB = p; p += (size_t)TE * elsz;
+    T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
+    T* sTr = p; p += (size_t)(TE + 2) * 2 * S * Q;
+    T* sVz = p; p += M * Q;
+    T* sPz = p; p += M * Q;
+    T* sD = p; p += NP * NP;
+    T* slm = p; p += NP;
+    T* slp = p; p += NP;
+    T* sdhL = p; p += NP;
+    T* sdhR = p; p += NP;
+    T* sVf = p; p += NP * NP;
+    T* sVfinv = p; p += NP * NP;
+    T* sLam = p; p += NP * M;
+    T* sTop = p; p += NP;
+    T* sRed = p; p += 2 * TE * Q;
+    int* sFlag = reinterpret_cast<int*>(p);
 
-    // ---- tables and the tile's coefficients
-    const double* tab = A.tab;
+    // ---- one sweep of independent loads: tables, halo + tile, SSP base
+    const T* tab = table_block<T>(A);
     for (int i = tid; i < M * Q; i += nthr) {
-        sm.Vz[i] = (T)tab[A.off.VzT + i];
-        sm.Pz[i] = (T)tab[A.off.Pz + i];
+        sVz[i] = tab[A.off.VzT + i];
+        sPz[i] = tab[A.off.Pz + i];
     }
-    for (int i = tid; i < NP * NP; i += nthr) sm.D[i] = (T)tab[A.off.D + i];
+    for (int i = tid; i < NP * NP; i += nthr) sD[i] = tab[A.off.D + i];
     for (int i = tid; i < NP; i += nthr) {
-        sm.lm[i] = (T)tab[A.off.lm + i];
-        sm.lp[i] = (T)tab[A.off.lp + i];
-        sm.dhL[i] = (T)tab[A.off.dhL + i];
-        sm.dhR[i] = (T)tab[A.off.dhR + i];
+        slm[i] = tab[A.off.lm + i];
+        slp[i] = tab[A.off.lp + i];
+        sdhL[i] = tab[A.off.dhL + i];
+        sdhR[i] = tab[A.off.dhR + i];
     }
     const double dt = A.dtp ? *A.dtp : A.dt_filter;
     if (A.do_filter) {
         for (int i = tid; i < NP * NP; i += nthr) {
-            sm.Vf[i] = (T)tab[A.off.Vf + i];
-            sm.Vfinv[i] = (T)tab[A.off.Vfinv + i];
+            sVf[i] = tab[A.off.Vf + i];
+            sVfinv[i] = tab[A.off.Vfinv + i];
         }
-        for (int i = tid; i < NP; i += nthr) sm.Top[i] = (T)tab[A.off.top + i];
-        load_filter_strengths<T>(A, NP, sm.Lam, tid, nthr, dt);
+        for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
+        load_filter_strengths<T>(A, NP, sLam, tid, nthr, dt);
     }
     {
-        const T* src = uin + (size_t)e0 * elsz;
-        const int n = ne * elsz;
-        for (int i = tid; i < n; i += nthr) sm.U[i] = src[i];
+        // slot 0: left neighbour, slots 1..ne: the tile, slot ne+1: right neighbour
+        // (neighbours wrap when periodic and are absent at a physical boundary)
+        const int nl = e0 - 1, nr = e0 + ne;
+        const bool hasL = nl >= 0 || periodic, hasR = nr < E || periodic;
+        const T* srcL = uin + (size_t)(nl < 0 ? E - 1 : nl) * elsz;
+        const T* srcR = uin + (size_t)(nr >= E ? 0 : nr) * elsz;
+        for (int i = tid; i < elsz; i += nthr) {
+            if (hasL) sU[i] = srcL[i];
+            if (hasR) sU[(ne + 1) * elsz + i] = srcR[i];
+        }
+        const T* srcT = uin + (size_t)e0 * elsz;
+        for (int i = tid; i < ne * elsz; i += nthr) sU[elsz + i] = srcT[i];
+        if (A.a != 0.0) {
+            const T* srcB = ubase + (size_t)e0 * elsz;
+            for (int i = tid; i < ne * elsz; i += nthr) sB[i] = srcB[i];
+        }
     }
     __syncthreads();
 
     // ---- a2 + a5: nodal values in z, own traces, halo traces
     T u[NP][S];
     T uLf[S], uRf[S];
-    const bool active = te < ne;
+    const bool active = te < ne && tq < Q;
+    const bool member = te < TE && tq < Q;   // owns a slot of the per-element scratch
     if (active) {
-        const T* ue = sm.U + te * elsz;
+        const T* ue = sU + (te + 1) * elsz;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
 #pragma unroll
             for (int s = 0; s < S; ++s) u[j][s] = T(0);
         for (int k = 0; k < M; ++k) {
-            const T v = sm.Vz[k * Q + tq];
+            const T v = sVz[k * Q + tq];
 #pragma unroll
             for (int j = 0; j < NP; ++j)
 #pragma unroll
@@ -128,33 +135,31 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
             T a = T(0), b = T(0);
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                a += sm.lm[j] * u[j][s];
-                b += sm.lp[j] * u[j][s];
+                a += slm[j] * u[j][s];
+                b += slp[j] * u[j][s];
             }
             uLf[s] = a;
             uRf[s] = b;
-            sm.Tr[((te + 1) * 2 + 0) * S * Q + s * Q + tq] = a;
-            sm.Tr[((te + 1) * 2 + 1) * S * Q + s * Q + tq] = b;
+            sTr[((te + 1) * 2 + 0) * S * Q + s * Q + tq] = a;
+            sTr[((te + 1) * 2 + 1) * S * Q + s * Q + tq] = b;
         }
-        // halo: right trace of the left neighbour, left trace of the right neighbour
+        // halo: right trace of the left neighbour (slot 0), left trace of the right one (slot ne+1)
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const bool edge = side == 0 ? (te == 0) : (te == ne - 1);
             if (!edge) continue;
-            const int e = e0 + te;
-            int nb = side == 0 ? e - 1 : e + 1;
-            const int row = side == 0 ? 0 : ne + 1;
+            const int nb = side == 0 ? e0 - 1 : e0 + ne;
+            const int slot = side == 0 ? 0 : ne + 1;
             const int nside = side == 0 ? 1 : 0;   // which trace of the neighbour faces us
             const int bc = side == 0 ? A.bc[0] : A.bc[1];
-            if ((nb < 0 || nb >= A.E) && bc == FRSG_BC_PERIODIC) nb = side == 0 ? A.E - 1 : 0;
             T g[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) g[s] = T(0);
-            if (nb >= 0 && nb < A.E) {
-                const T* un = uin + (size_t)nb * elsz;
-                const T* lw = side == 0 ? sm.lp : sm.lm;
+            if ((nb >= 0 && nb < E) || periodic) {
+                const T* un = sU + slot * elsz;
+                const T* lw = side == 0 ? slp : slm;
                 for (int k = 0; k < M; ++k) {
-                    const T v = sm.Vz[k * Q + tq];
+                    const T v = sVz[k * Q + tq];
 #pragma unroll
                     for (int j = 0; j < NP; ++j)
 #pragma unroll
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
             } else if (bc == FRSG_BC_DIRICHLET) {
                 const double* gh = A.ghost + (size_t)side * M * S;
                 for (int k = 0; k < M; ++k) {
-                    const T v = sm.Vz[k * Q + tq];
+                    const T v = sVz[k * Q + tq];
 #pragma unroll
                     for (int s = 0; s < S; ++s) g[s] += v * (T)gh[k * S + s];
                 }
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
                 ghost_from_interior<T, EQ, S, 0>(bc, uRf, g);
             }
 #pragma unroll
-            for (int s = 0; s < S; ++s) sm.Tr[(row * 2 + nside) * S * Q + s * Q + tq] = g[s];
+            for (int s = 0; s < S; ++s) sTr[(slot * 2 + nside) * S * Q + s * Q + tq] = g[s];
         }
     }
     __syncthreads();
@@ -189,13 +194,13 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
             T a = T(0), b = T(0);
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                a += sm.lm[j] * f[j][s];
-                b += sm.lp[j] * f[j][s];
+                a += slm[j] * f[j][s];
+                b += slp[j] * f[j][s];
             }
             fDL[s] = a;
             fDR[s] = b;
-            nL[s] = sm.Tr[(te * 2 + 1) * S * Q + s * Q + tq];
-            nR[s] = sm.Tr[((te + 2) * 2 + 0) * S * Q + s * Q + tq];
+            nL[s] = sTr[(te * 2 + 1) * S * Q + s * Q + tq];
+            nR[s] = sTr[((te + 2) * 2 + 0) * S * Q + s * Q + tq];
         }
         llf<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma);
         llf<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma);
@@ -204,57 +209,72 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
         for (int j = 0; j < NP; ++j)
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                T d = (fIL[s] - fDL[s]) * sm.dhL[j] + (fIR[s] - fDR[s]) * sm.dhR[j];
+                T d = (fIL[s] - fDL[s]) * sdhL[j] + (fIR[s] - fDR[s]) * sdhR[j];
 #pragma unroll
-                for (int m = 0; m < NP; ++m) d += sm.D[j * NP + m] * f[m][s];
-                sm.G[((te * NP + j) * S + s) * Q + tq] = -invJ * d;
+                for (int m = 0; m < NP; ++m) d += sD[j * NP + m] * f[m][s];
+                sG[((te * NP + j) * S + s) * Q + tq] = -invJ * d;
             }
     }
     __syncthreads();
 
     // ---- a4 + a8: projection of the residual onto the modes, SSP combination
     const T ca = (T)A.a, cb = (T)A.b, cc = (T)(A.dtp ? A.c * dt : A.c);
-    const T* ubase = static_cast<const T*>(A.ubase);
     T* uout = static_cast<T*>(A.uout);
+    T* sTile = sU + elsz;
     const size_t gbase = (size_t)e0 * elsz;
-    const int nout = ne * elsz;
     bool bad = false;
-    for (int o = tid; o < nout; o += nthr) {
-        const int el = o / elsz, rr = o - el * elsz;
-        const int j = rr / (M * S), k = (rr / S) % M, s = rr % S;
-        const T* g = sm.G + ((el * NP + j) * S + s) * Q;
-        const T* pz = sm.Pz + k * Q;
-        T acc = T(0);
-        for (int q = 0; q < Q; ++q) acc += pz[q] * g[q];
-        T val = cb * sm.U[o] + cc * acc;
-        if (ca != T(0)) val += ca * ubase[gbase + o];
-        if (A.do_filter) {
-            sm.U[o] = val;
-        } else {
-            uout[gbase + o] = val;
-            bad |= !finite_val(val);
-        }
+    if (active) {
+        T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
+        bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
+                                         Q, 0, 1, ca, cb, cc, A.a != 0.0);
     }
     if (A.do_filter) {
         __syncthreads();
-        // ---- a9 + a10: detector and filter, one coalesced store
-        bad |= detector_filter_store<T, NP, S>(A, sm.U, sm.G, sm.Vf, sm.Vfinv, sm.Lam, sm.Top, sm.Red, sm.flag, tid,
-                                               nthr, te, tq, Q, active, ne, e0, uout, gbase);
+        // ---- a9 + a10: detector and filter, one store per coefficient
+        bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, 0, 1,
+                                              active, member, e0, uout, gbase);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }
 
 template <typename T, int NP, int S, int EQ>
+__global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int e0 = blockIdx.x * A.TE;
+    const int tq = threadIdx.x, te = threadIdx.y;
+    stage1d_tile<T, NP, S, EQ>(A, e0, min(A.TE, A.E - e0), tq, te, te * A.Q + tq, A.Q * A.TE, smem_raw);
+}
+
+// Persistent kernel over the tiles of many 1D problems (one StageArgs per problem): CTA b
+// takes tiles b, b + gridDim.x, ...; the shared-memory carve-up follows each tile's sizes.
+template <typename T, int S, int EQ>
+__global__ void __launch_bounds__(256) stage1d_batched_kernel(const StageArgs* __restrict__ args,
+                                                              const int4* __restrict__ tiles, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tr = tiles[t];   // (problem, first element, element count, points per element)
+        const StageArgs& A = args[tr.x];
+        const int tq = threadIdx.x % A.Q, te = threadIdx.x / A.Q;
+        switch (tr.w) {
+            case 2: stage1d_tile<T, 2, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+            case 3: stage1d_tile<T, 3, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+            case 4: stage1d_tile<T, 4, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+            case 5: stage1d_tile<T, 5, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int NP, int S, int EQ>
 cudaError_t launch_typed(const StageArgs& A, cudaStream_t st) {
     const int TE = A.TE;
-    const int M = A.M, Q = A.Q;
-    const size_t smem = smem1d_bytes<T>(TE, NP, M, Q, S);
+    const size_t smem = smem1d_bytes<T>(TE, NP, A.M, A.Q, S);
     auto kern = stage1d_kernel<T, NP, S, EQ>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 block(Q, TE);
+    dim3 block(A.Q, TE);
     dim3 grid((A.E + TE - 1) / TE);
     kern<<<grid, block, smem, st>>>(A);
     return cudaGetLastError();
@@ -289,6 +309,45 @@ size_t stage1d_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S) {
 
 cudaError_t launch_stage1d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st) {
     return fp64 ? launch_np<double>(cfg, A, st) : launch_np<float>(cfg, A, st);
+}
+
+namespace {
+template <typename T, int EQ>
+cudaError_t batched_typed(const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,
+                          cudaStream_t st) {
+    auto kern = stage1d_batched_kernel<T, 1, EQ>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, 256, smem, st>>>(args, tiles, ntiles);
+    return cudaGetLastError();
+}
+
+template <typename T, int EQ>
+int batched_occ(size_t smem) {
+    auto kern = stage1d_batched_kernel<T, 1, EQ>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+}  // namespace
+
+cudaError_t launch_stage1d_batched(bool fp64, int equation, const StageArgs* args, const int4* tiles, int ntiles,
+                                   size_t smem, int grid, cudaStream_t st) {
+    if (equation == FRSG_EQ_ADVECTION)
+        return fp64 ? batched_typed<double, FRSG_EQ_ADVECTION>(args, tiles, ntiles, smem, grid, st)
+                    : batched_typed<float, FRSG_EQ_ADVECTION>(args, tiles, ntiles, smem, grid, st);
+    if (equation == FRSG_EQ_BURGERS)
+        return fp64 ? batched_typed<double, FRSG_EQ_BURGERS>(args, tiles, ntiles, smem, grid, st)
+                    : batched_typed<float, FRSG_EQ_BURGERS>(args, tiles, ntiles, smem, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+int stage1d_batched_blocks_per_sm(bool fp64, int equation, size_t smem) {
+    if (equation == FRSG_EQ_ADVECTION) return fp64 ? batched_occ<double, FRSG_EQ_ADVECTION>(smem) : batched_occ<float, FRSG_EQ_ADVECTION>(smem);
+    return fp64 ? batched_occ<double, FRSG_EQ_BURGERS>(smem) : batched_occ<float, FRSG_EQ_BURGERS>(smem);
 }
 
 }  // namespace frsg

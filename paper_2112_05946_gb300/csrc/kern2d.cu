@@ -7,9 +7,9 @@
 // and stage:
 //   a2  u(r_a, s_b, z_q) = sum_k Phi_k(z_q) uhat_(b,a),k          (§2.1, Eq. 2)
 //   a5  traces on the four faces by ell(+-1) along rows / columns (§3.3)
-//   a6  LLF fluxes on x-faces (f, |v_x| + c) and y-faces (g, |v_y| + c); the right/left
-//       neighbours' x-traces come from the tile or from halo threads, the y-neighbours'
-//       traces are recomputed by each column thread from global memory
+//   a6  LLF fluxes on x-faces (f, |v_x| + c) and y-faces (g, |v_y| + c); one coalesced
+//       sweep loads the tile, its two x-neighbours and the rows of elements below and
+//       above it, so every neighbour trace is computed from shared memory
 //   a3/a7 total-flux derivative per direction with the 1D Radau correction along each
 //       line (§3.5, Eq. 24, minus sign of Eq. 12): -(1/Jx) df/dr - (1/Jy) dg/ds
 //   a4  projection of the nodal residual onto the modes (§2.1, Eq. 6)
@@ -28,7 +28,8 @@ template <typename T>
 __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int S) {
     const int Np = n1 * n1;
     size_t n = 0;
-    n += (size_t)TE * Np * M * S;           // U (coefficients, later the new state)
+    n += (size_t)(3 * TE + 2) * Np * M * S; // U: x-halo + tile, row below, row above (tile later the new state)
+    n += (size_t)TE * Np * M * S;           // B: SSP base state of the tile
     n += (size_t)TE * Np * S * Q;           // Un (nodal values)
     n += (size_t)TE * Np * S * (Q > M ? Q : M);   // G (nodal residual, later the modal coefficients)
     n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][s][q]
@@ -81,7 +82,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     const T* uin = static_cast<const T*>(A.uin);
 
     T* p = reinterpret_cast<T*>(smem_raw);
-    T* sU = p; p += (size_t)TE * elsz;
+    T* sU = p; p += (size_t)(3 * TE + 2) * elsz;
+    T* sB = p; p += (size_t)TE * elsz;
     T* sUn = p; p += (size_t)TE * NP * S * Q;
     T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
     T* sTx = p; p += (size_t)(TE + 2) * 2 * N1 * S * Q;
@@ -99,41 +101,65 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     T* sRed = p; p += 2 * TE * N1 * Q;
     int* sFlag = reinterpret_cast<int*>(p);
 
-    const double* tab = A.tab;
+    const T* tab = table_block<T>(A);
     for (int i = tid; i < M * Q; i += nthr) {
-        sVz[i] = (T)tab[A.off.VzT + i];
-        sPz[i] = (T)tab[A.off.Pz + i];
+        sVz[i] = tab[A.off.VzT + i];
+        sPz[i] = tab[A.off.Pz + i];
     }
-    for (int i = tid; i < N1 * N1; i += nthr) sD[i] = (T)tab[A.off.D + i];
+    for (int i = tid; i < N1 * N1; i += nthr) sD[i] = tab[A.off.D + i];
     for (int i = tid; i < N1; i += nthr) {
-        slm[i] = (T)tab[A.off.lm + i];
-        slp[i] = (T)tab[A.off.lp + i];
-        sdhL[i] = (T)tab[A.off.dhL + i];
-        sdhR[i] = (T)tab[A.off.dhR + i];
+        slm[i] = tab[A.off.lm + i];
+        slp[i] = tab[A.off.lp + i];
+        sdhL[i] = tab[A.off.dhL + i];
+        sdhR[i] = tab[A.off.dhR + i];
     }
     const double dt = A.dtp ? *A.dtp : A.dt_filter;
     if (A.do_filter) {
         for (int i = tid; i < NP * NP; i += nthr) {
-            sVf[i] = (T)tab[A.off.Vf + i];
-            sVfinv[i] = (T)tab[A.off.Vfinv + i];
+            sVf[i] = tab[A.off.Vf + i];
+            sVfinv[i] = tab[A.off.Vfinv + i];
         }
-        for (int i = tid; i < NP; i += nthr) sTop[i] = (T)tab[A.off.top + i];
+        for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
         load_filter_strengths<T>(A, NP, sLam, tid, nthr, dt);
     }
+    const T* ubase = static_cast<const T*>(A.ubase);
+    const bool xper = A.bc[0] == FRSG_BC_PERIODIC, yper = A.bc[2] == FRSG_BC_PERIODIC;
     {
-        const T* src = uin + (size_t)e0 * elsz;
-        const int n = ne * elsz;
-        for (int i = tid; i < n; i += nthr) sU[i] = src[i];
+        // slots 0..ne+1: left neighbour, tile, right neighbour (row ey);
+        // slots TE+2..TE+1+ne: row below; slots 2TE+2..2TE+1+ne: row above
+        const int nl = ex0 - 1, nr = ex0 + ne;
+        const bool hasL = nl >= 0 || xper, hasR = nr < nx || xper;
+        const T* srcL = uin + ((size_t)ey * nx + (nl < 0 ? nx - 1 : nl)) * elsz;
+        const T* srcR = uin + ((size_t)ey * nx + (nr >= nx ? 0 : nr)) * elsz;
+        for (int i = tid; i < elsz; i += nthr) {
+            if (hasL) sU[i] = srcL[i];
+            if (hasR) sU[(ne + 1) * elsz + i] = srcR[i];
+        }
+        const T* srcT = uin + (size_t)e0 * elsz;
+        for (int i = tid; i < ne * elsz; i += nthr) sU[elsz + i] = srcT[i];
+        for (int side = 0; side < 2; ++side) {
+            int eyn = side == 0 ? ey - 1 : ey + 1;
+            if (eyn < 0 || eyn >= ny) {
+                if (!yper) continue;
+                eyn = eyn < 0 ? ny - 1 : 0;
+            }
+            T* dst = sU + (size_t)(TE + 2 + side * TE) * elsz;
+            const T* src = uin + ((size_t)eyn * nx + ex0) * elsz;
+            for (int i = tid; i < ne * elsz; i += nthr) dst[i] = src[i];
+        }
+        if (A.a != 0.0) {
+            const T* src = ubase + (size_t)e0 * elsz;
+            for (int i = tid; i < ne * elsz; i += nthr) sB[i] = src[i];
+        }
     }
     __syncthreads();
 
     const bool active = te < ne;
     const int ex = ex0 + te;
-    const int e = e0 + te;
     T u[N1][S];                     // row b = tl: values at (a, b), a = 0..N1-1
     T ybot[S], ytop[S];             // column a = tl: neighbours' facing traces (y)
     if (active) {
-        const T* ue = sU + te * elsz;
+        const T* ue = sU + (te + 1) * elsz;
         const int b = tl;
 #pragma unroll
         for (int a = 0; a < N1; ++a)
@@ -170,12 +196,11 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
         for (int side = 0; side < 2; ++side) {
             const bool edge = side == 0 ? (te == 0) : (te == ne - 1);
             if (!edge) continue;
-            int nbx = side == 0 ? ex - 1 : ex + 1;
+            const int nbx = side == 0 ? ex - 1 : ex + 1;
             const int bc = side == 0 ? A.bc[0] : A.bc[1];
-            if ((nbx < 0 || nbx >= nx) && bc == FRSG_BC_PERIODIC) nbx = side == 0 ? nx - 1 : 0;
             T g[S];
-            if (nbx >= 0 && nbx < nx) {
-                const T* un = uin + ((size_t)ey * nx + nbx) * elsz;
+            if ((nbx >= 0 && nbx < nx) || xper) {
+                const T* un = sU + (size_t)(side == 0 ? 0 : ne + 1) * elsz;
                 line_trace<T, N1, S>(un, M, sVz + tq, Q, side == 0 ? slp : slm, false, b, g);
             } else if (bc == FRSG_BC_DIRICHLET) {
                 const double* gh = A.ghost + (size_t)side * M * S;
@@ -200,12 +225,11 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
         const int a = tl;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            int nby = side == 0 ? ey - 1 : ey + 1;
+            const int nby = side == 0 ? ey - 1 : ey + 1;
             const int bc = side == 0 ? A.bc[2] : A.bc[3];
-            if ((nby < 0 || nby >= ny) && bc == FRSG_BC_PERIODIC) nby = side == 0 ? ny - 1 : 0;
             T g[S];
-            if (nby >= 0 && nby < ny) {
-                const T* un = uin + ((size_t)nby * nx + ex) * elsz;
+            if ((nby >= 0 && nby < ny) || yper) {
+                const T* un = sU + (size_t)(TE + 2 + side * TE + te) * elsz;
                 line_trace<T, N1, S>(un, M, sVz + tq, Q, side == 0 ? slp : slm, true, a, g);
             } else if (bc == FRSG_BC_DIRICHLET) {
                 const double* gh = A.ghost + (size_t)(2 + side) * M * S;
@@ -316,31 +340,19 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
 
     // ---- projection + SSP combination
     const T ca = (T)A.a, cb = (T)A.b, cc = (T)(A.dtp ? A.c * dt : A.c);
-    const T* ubase = static_cast<const T*>(A.ubase);
     T* uout = static_cast<T*>(A.uout);
+    T* sTile = sU + elsz;
     const size_t gbase = (size_t)e0 * elsz;
-    const int nout = ne * elsz;
     bool bad = false;
-    for (int o = tid; o < nout; o += nthr) {
-        const int el = o / elsz, rr = o - el * elsz;
-        const int j = rr / (M * S), k = (rr / S) % M, s = rr % S;
-        const T* gq = sG + ((el * NP + j) * S + s) * Q;
-        const T* pz = sPz + k * Q;
-        T acc = T(0);
-        for (int q = 0; q < Q; ++q) acc += pz[q] * gq[q];
-        T val = cb * sU[o] + cc * acc;
-        if (ca != T(0)) val += ca * ubase[gbase + o];
-        if (A.do_filter) {
-            sU[o] = val;
-        } else {
-            uout[gbase + o] = val;
-            bad |= !finite_val(val);
-        }
+    if (active) {
+        T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
+        bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
+                                         Q, tl, N1, ca, cb, cc, A.a != 0.0);
     }
     if (A.do_filter) {
         __syncthreads();
-        bad |= detector_filter_store<T, NP, S>(A, sU, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, tid, nthr, te,
-                                               tl * Q + tq, N1 * Q, active, ne, e0, uout, gbase);
+        bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tl, N1,
+                                              active, true, e0, uout, gbase);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }

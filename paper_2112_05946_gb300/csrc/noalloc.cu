@@ -274,6 +274,7 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
     A.f_eps2 = cfg->f_eps2;
     A.s0 = cfg->s0;
     A.kappa = cfg->kappa;
+    A.det_ratio = detector_ratio(cfg->s0, cfg->kappa);
     A.err = d_err;
     A.TE = te;
     A.dtp = d_dt;

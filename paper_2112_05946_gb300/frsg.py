@@ -61,6 +61,7 @@ _SIGNATURES = [
     ("fr_sg_sizes", ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 5),
     ("fr_sg_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_get_nodes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fr_sg_get_quadrature", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_set_boundary_nodal", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("fr_sg_set_initial_nodal", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -77,6 +78,15 @@ _SIGNATURES = [
     ("fr_sg_check", ctypes.c_int, [ctypes.c_void_p]),
     ("fr_sg_launch_count", ctypes.c_uint64, [ctypes.c_void_p]),
     ("fr_sg_set_tile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("fr_sg_forward_record", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_adjoint", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fr_sg_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    ("fr_sg_batch_destroy", None, [ctypes.c_void_p]),
+    ("fr_sg_batch_rk_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_batch_launch_count", ctypes.c_uint64, [ctypes.c_void_p]),
+    ("fr_sg_batch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_size_t)]),
     ("fr_sg_rk_step_noalloc", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
 ]
@@ -129,7 +139,9 @@ def _ptr(a):
         if not a.flags["C_CONTIGUOUS"]:
             raise ValueError("host arrays must be C-contiguous")
         return a.ctypes.data
-    return a.data_ptr()   # torch tensor
+    if not a.is_contiguous():   # torch tensor: the C ABI reads the row-major layout
+        raise ValueError("device tensors must be contiguous")
+    return a.data_ptr()
 
 
 def rk_step_noalloc(u_in, u_out, dt, nsteps=1, ghost_modes=None, stream=None, **cfg):
@@ -195,6 +207,13 @@ class Solver:
         z = np.zeros(self.Q)
         self._ck(self.lib.fr_sg_get_nodes(self.h, _ptr(x), _ptr(y), _ptr(z)), "get_nodes")
         return (x, z) if self.cfg.dim == 1 else (x, y, z)
+
+    def quadrature(self):
+        """(wx[Np], wz[Q]): reference-element Gauss weights and z probability weights."""
+        wx = np.zeros(self.Np)
+        wz = np.zeros(self.Q)
+        self._ck(self.lib.fr_sg_get_quadrature(self.h, _ptr(wx), _ptr(wz)), "get_quadrature")
+        return wx, wz
 
     def set_boundary_nodal(self, side, g):
         g = np.ascontiguousarray(g, dtype=np.float64).reshape(self.Q, self.S)
@@ -273,6 +292,14 @@ class Solver:
     def check(self):
         self._ck(self.lib.fr_sg_check(self.h), "check")
 
+    def forward_record(self, dt, nsteps, checkpoint_every=16):
+        self._ck(self.lib.fr_sg_forward_record(self.h, float(dt), int(nsteps), int(checkpoint_every)),
+                 "forward_record")
+
+    def adjoint(self, lambda_T, grad_u0):
+        """lambda_T, grad_u0: device float64 tensors [E, Np, M, S]."""
+        self._ck(self.lib.fr_sg_adjoint(self.h, _ptr(lambda_T), _ptr(grad_u0)), "adjoint")
+
     def set_tile(self, te):
         """Elements per CTA of the stage kernel (0 = automatic); returns the tile in use."""
         out = ctypes.c_int()
@@ -281,3 +308,42 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.fr_sg_launch_count(self.h))
+
+
+class Batch:
+    """fr_sg_batch_*: many 1D Solver objects advanced by one persistent launch per stage."""
+
+    def __init__(self, solvers, stream=None):
+        self.lib = load_library()
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        st = self.lib.fr_sg_batch_create(arr, len(self.solvers), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != OK:
+            raise FrsgError(st, "fr_sg_batch_create rejected the members (details on stderr)")
+        self.h = h
+
+    def rk_step(self, dts, nsteps=1, graph=True):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        st = self.lib.fr_sg_batch_rk_step(self.h, _ptr(d), int(nsteps), int(bool(graph)))
+        if st != OK:
+            raise FrsgError(st, "fr_sg_batch_rk_step failed")
+
+    def info(self):
+        nt, gr, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        self.lib.fr_sg_batch_info(self.h, ctypes.byref(nt), ctypes.byref(gr), ctypes.byref(sm))
+        return dict(tiles=nt.value, grid=gr.value, smem=sm.value)
+
+    def launch_count(self):
+        return int(self.lib.fr_sg_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fr_sg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

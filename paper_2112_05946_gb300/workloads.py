@@ -132,6 +132,61 @@ def shock_vortex_2d(nx=256, ny=128, P=3, N=4, Q=8, mach=1.1):
     )
 
 
+def splitmix64(state):
+    """One step of the SplitMix64 generator: returns (next_state, 64-bit output)."""
+    mask = (1 << 64) - 1
+    state = (state + 0x9E3779B97F4A7C15) & mask
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+    return state, z ^ (z >> 31)
+
+
+class _Stream:
+    def __init__(self, seed):
+        self.state = seed & ((1 << 64) - 1)
+
+    def uniform(self):
+        self.state, z = splitmix64(self.state)
+        return (z >> 11) * (1.0 / (1 << 53))
+
+    def integer(self, lo, hi):
+        return lo + min(int(self.uniform() * (hi - lo + 1)), hi - lo)
+
+
+def burgers_batch(n=256, seed=0, e_range=(64, 2048), cfl=0.05):
+    """Uneven batch of stochastic Burgers problems on periodic [0, 2] (§5.2 family).
+
+    Instance i draws from SplitMix64 seeded with seed * 1000003 + i: E ~ U{64..2048},
+    P ~ U{1..4}, N ~ U{2..10}, Q = 2N; half of the instances start from
+    A sin(2 pi m x / L + phi) + 0.1 z (A in [0.5, 1], m in {1, 2, 3}, phi in [0, 2 pi)),
+    the other half from A exp(-(x - x0)^2 / (2 w^2)) (1 + 0.1 z) (w in [0.05, 0.2]).
+    Detector + exponential filter as the single Burgers workload; dt = cfl * dx / (A + 0.1)."""
+    out = []
+    L = 2.0
+    for i in range(n):
+        r = _Stream(seed * 1000003 + i)
+        E = r.integer(*e_range)
+        P = r.integer(1, 4)
+        N = r.integer(2, 10)
+        A = 0.5 + 0.5 * r.uniform()
+        if i % 2 == 0:
+            m = r.integer(1, 3)
+            phi = 2.0 * math.pi * r.uniform()
+            ic = (lambda A, m, phi: (lambda x, z: (A * np.sin(2.0 * math.pi * m * x / L + phi) + 0.1 * z)[..., None]))(
+                A, m, phi)
+        else:
+            x0 = L * r.uniform()
+            w = 0.05 + 0.15 * r.uniform()
+            ic = (lambda A, x0, w: (lambda x, z: (A * np.exp(-((x - x0) ** 2) / (2.0 * w * w)) * (1.0 + 0.1 * z))[..., None]))(
+                A, x0, w)
+        solver = dict(dim=1, nx=E, x0=0.0, x1=L, bc=("periodic",) * 4, P=P, N=N, Q=2 * N, equation="burgers",
+                      filter="exp", sensor=True, f_alpha=36.0, f_s=4.0, s0=-2.0 * math.log10(P), kappa=4.0)
+        out.append(dict(name=f"burgers_batch{seed}_{i}_E{E}_P{P}_N{N}", solver=solver, ic=ic, cfl=cfl, lam0=A + 0.1,
+                        t_end=0.5))
+    return out
+
+
 ALL = {"advection": advection_1d, "burgers": burgers_1d, "sod": sod_1d, "shock_vortex": shock_vortex_2d}
 
 

@@ -1,0 +1,136 @@
+"""Hand-written discrete adjoint on the GPU (fr_sg_forward_record / fr_sg_adjoint and the
+torch.autograd.Function around them) against the oracle adjoint, central finite
+differences and closed forms."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adjoint, integrate
+from paper_2112_05946_gb300 import workloads
+from tests.helpers import oracle_problem, rel_l2, solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _burgers(nx=24, P=2, N=3, Q=7, filt="exp"):
+    wl = workloads.burgers_1d(nx=nx, P=P, N=N, Q=Q)
+    wl["solver"]["filter"] = filt
+    return wl
+
+
+def _state(prob, wl):
+    return integrate.project_initial(prob, lambda x, z: (np.sin(np.pi * x) + 0.1 * z + 0.3)[..., None])
+
+
+@pytest.mark.parametrize("nsteps,k", [(40, 16), (17, 5), (9, 1)])
+@pytest.mark.parametrize("filt", ["exp", "none"])
+def test_adjoint_matches_oracle_adjoint(nsteps, k, filt):
+    import torch
+    wl = _burgers(filt=filt)
+    prob = oracle_problem(wl)
+    u0 = _state(prob, wl)
+    dt = 0.1 * prob.dx / 1.3
+    rec = []
+    integrate.run(prob, u0, dt, nsteps, record=rec)
+    ref = adjoint.gradients(prob, u0, dt, nsteps, rec)
+    s = solver(wl)
+    s.set_state(u0)
+    s.forward_record(dt, nsteps, k)
+    s.check()
+    assert rel_l2(s.get_state(), ref["state"]) < 1e-12
+    flags = s.decisions()[0]
+    gm_seed, gv_seed = adjoint.qoi_seeds(prob, ref["state"])
+    for seed, key in [(gm_seed, "grad_mean"), (gv_seed, "grad_var")]:
+        lam = torch.tensor(seed, device="cuda")
+        g = torch.empty_like(lam)
+        s.adjoint(lam, g)
+        s.check()
+        assert rel_l2(g.cpu().numpy(), ref[key]) < 1e-11, key
+    # the context's state is the final state again
+    assert rel_l2(s.get_state(), ref["state"]) < 1e-12
+    del flags
+
+
+def test_adjoint_finite_differences_through_the_abi():
+    """<grad, v> against (Q(u0 + h v) - Q(u0 - h v)) / 2h with both runs on the GPU and the
+    forward run's filter decisions replayed."""
+    import torch
+    wl = _burgers(nx=32, P=3, N=4, Q=9)
+    prob = oracle_problem(wl)
+    u0 = _state(prob, wl)
+    dt = 0.1 * prob.dx / 1.3
+    nsteps = 60
+    s = solver(wl)
+    s.set_state(u0)
+    s.forward_record(dt, nsteps, 16)
+    uT = s.get_state()
+    # decisions of the recorded run, replayed in the perturbed runs
+    rec = []
+    integrate.run(prob, u0, dt, nsteps, record=rec)
+    _, gv_seed = adjoint.qoi_seeds(prob, uT)
+    lam = torch.tensor(gv_seed, device="cuda")
+    g = torch.empty_like(lam)
+    s.adjoint(lam, g)
+    g = g.cpu().numpy()
+
+    def qvar(u):
+        w = s.quadrature()[0]
+        I = 0.5 * prob.dx * np.einsum("j,ejk->k", w, u[..., 0])
+        return np.sum(I[1:] ** 2)
+
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for _ in range(2):
+        v = rng.standard_normal(u0.shape)
+        vals = []
+        for sign in (1, -1):
+            s2 = solver(wl)
+            s2.set_state(u0 + sign * h * v)
+            s2.set_replay(np.array(rec, dtype=np.uint8))
+            s2.rk_step(dt, nsteps, graph=False)
+            vals.append(qvar(s2.get_state()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(np.sum(g * v) - fd) < 1e-6 * max(abs(fd), 1e-4)
+
+
+def test_mean_gradient_closed_form():
+    """Periodic conservative FR with a mode-0-preserving filter conserves E[int u]: its
+    gradient w.r.t. uhat(0) is J w_j on mode 0 and zero elsewhere."""
+    import torch
+    wl = _burgers(nx=48, P=3, N=8, Q=16)
+    prob = oracle_problem(wl)
+    u0 = _state(prob, wl)
+    s = solver(wl)
+    s.set_state(u0)
+    s.forward_record(0.1 * prob.dx / 1.3, 100, 16)
+    gm_seed, _ = adjoint.qoi_seeds(prob, u0)
+    lam = torch.tensor(gm_seed, device="cuda")
+    g = torch.empty_like(lam)
+    s.adjoint(lam, g)
+    np.testing.assert_allclose(g.cpu().numpy(), gm_seed, atol=1e-13)
+
+
+def test_autograd_function_gives_the_adjoint_gradient():
+    import torch
+    from paper_2112_05946_gb300.autograd import FRSGRun, qoi_mean_var, quadrature_weights
+    wl = _burgers(nx=24)
+    prob = oracle_problem(wl)
+    u0n = _state(prob, wl)
+    dt = 0.1 * prob.dx / 1.3
+    s = solver(wl)
+    u0 = torch.tensor(u0n, device="cuda", requires_grad=True)
+    uT = FRSGRun.apply(u0, s, dt, 40, 16)
+    mean, var = qoi_mean_var(quadrature_weights(s), uT)
+    (var + 0.5 * mean).backward()
+    rec = []
+    integrate.run(prob, u0n, dt, 40, record=rec)
+    ref = adjoint.gradients(prob, u0n, dt, 40, rec)
+    assert rel_l2(u0.grad.cpu().numpy(), ref["grad_var"] + 0.5 * ref["grad_mean"]) < 1e-11
+
+
+def test_adjoint_rejects_unsupported_contexts():
+    from paper_2112_05946_gb300 import frsg
+    s = solver(workloads.sod_1d(nx=8))
+    with pytest.raises(frsg.FrsgError) as ei:
+        s.forward_record(1e-4, 2, 1)
+    assert ei.value.status == frsg.E_UNSUPPORTED
