@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--workload", default="burgers", choices=sorted(workloads.ALL))
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the Sod and 2D shock-vortex lines")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Sod, 2D, batched and adjoint lines")
+    ap.add_argument("--only", default=None, choices=["burgers", "sod", "shock_vortex", "batch", "adjoint"],
+                    help="measure one extra workload alone and print its line (for profiling runs)")
     return ap.parse_args()
 
 
@@ -126,6 +128,7 @@ def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracl
     E, Np, M, S = workload_sizes(wl)
     dof = E * Np * M * S
     s = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
+    variant, tile = s.autotune()
     x, z = s.nodes()
     u0 = workloads.nodal_values(wl["ic"], x, z)
     dx = (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"]
@@ -202,7 +205,7 @@ def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracl
         err_bound=ERR_BOUND[precision], dof=dof, launches=launches, steady_ms=steady_ms,
         stage_us=[float(v * 1e3) for v in mean_stage], achieved_gbs=achieved,
         alg_bytes_per_step=sum(alg_bytes), e2e_value=dof * 3 / e2e_s, e2e_ms=e2e_s * 1e3,
-        h2d=dof * 8, d2h=dof * 8,
+        h2d=dof * 8, d2h=dof * 8, variant=variant, tile=tile,
     )
 
 
@@ -214,6 +217,7 @@ def measure_extra(torch, frsg, wl, precision, steps, warmup, stream, flush):
     dof = E * Np * M * S
     esz = 8 if precision == "fp64" else 4
     s = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
+    s.autotune()
     nodes = s.nodes()
     if "boundary" in wl:
         for side, fn in wl["boundary"].items():
@@ -365,8 +369,33 @@ def oracle_reference(wl, nsteps):
     return integrate.run(prob, u, dt, nsteps)
 
 
+def run_only(args):
+    """One extra measurement alone, both forms where they apply (profiling aid)."""
+    import torch
+    from paper_2112_05946_gb300 import build as _b
+    from paper_2112_05946_gb300 import frsg
+    _b.build()
+    frsg.load_library()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if args.only == "burgers":
+        wl = workloads.burgers_1d()
+        ref = oracle_reference(wl, ACC_STEPS)
+        out = measure_form(torch, frsg, wl, "fp32", args.steps, args.warmup, stream, flush, ref)
+    elif args.only == "batch":
+        out = {p: measure_batch(torch, frsg, p, args.steps, args.warmup, stream, flush) for p in ("fp64", "fp32")}
+    elif args.only == "adjoint":
+        out = measure_adjoint(torch, frsg, stream)
+    else:
+        wl = workloads.ALL[args.only]()
+        out = {p: measure_extra(torch, frsg, wl, p, args.steps, args.warmup, stream, flush) for p in ("fp64", "fp32")}
+    print(json.dumps({"only": args.only, "result": out}))
+
+
 def run_ours(args):
     import torch
+    if args.only:
+        return run_only(args)
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -444,7 +473,8 @@ def run_ours(args):
         "chosen": chosen["precision"],
         "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "rel_l2_vs_oracle": v["err_vs_oracle"],
                       "err_bound": v["err_bound"], "steady_ms_per_step": v["steady_ms"],
-                      "stage_us": v["stage_us"]} for k, v in forms.items()},
+                      "stage_us": v["stage_us"], "variant": v["variant"], "tile": v["tile"]}
+                  for k, v in forms.items()},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": chosen["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": chosen["h2d"],

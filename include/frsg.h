@@ -218,6 +218,19 @@ frsg_status fr_sg_adjoint(frsg_ctx* ctx, const double* lambda_T, double* grad_u0
  * exceeds 512 threads.  *te_out (may be NULL) receives the tile in use. */
 frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out);
 
+/* Layout of the 1D stage kernel: 0 = one thread per (z-node, element), looping over the
+ * element's solution points; 1 (the default for 1D) = one thread per (z-node, point,
+ * element).  Both compute the same stage; the tile is re-chosen automatically.
+ * 2D contexts accept only 0 (FRSG_E_UNSUPPORTED for 1). */
+frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant);
+
+/* Autotuner: times the stage kernel (stage 0 of a step, reps launches each, CUDA events on
+ * the context's stream) for every layout (1D) and tile that fits, keeps the fastest and
+ * caches the choice per (dim, P, N, Q, S, precision, elements, filter, equation) for the
+ * process.  Overwrites the first stage buffer and the decision rows; the state is kept.
+ * Synchronises.  variant_out / te_out (may be NULL) receive the choice. */
+frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_out);
+
 /* Number of kernel launches issued on this context since creation (graph replays count
  * each captured kernel).  Host counter; never synchronises. */
 uint64_t fr_sg_launch_count(const frsg_ctx* ctx);

@@ -3,6 +3,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -14,6 +17,7 @@
 
 namespace frsg {
 size_t stage1d_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S);
+size_t stage1d_wide_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S);
 size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S);
 }  // namespace frsg
 
@@ -44,6 +48,7 @@ struct frsg_ctx {
     std::string last_error;
     uint64_t launches = 0;
     int TE = 1, TE_lim = 1;
+    int wide = 0;                 // 1D stage kernel layout: 1 = thread per (z-node, point)
     cudaGraphExec_t graph_exec = nullptr;
     // recorded run for the adjoint: checkpoints every rec_k steps, filter decisions per stage
     int rec_nsteps = 0, rec_k = 0, rec_cap_ckpt = 0, rec_cap_steps = 0, rec_cap_seg = 0;
@@ -250,6 +255,7 @@ StageArgs base_args(frsg_ctx* c) {
     A.det_ratio = frsg::detector_ratio(c->cfg.s0, c->cfg.kappa);
     A.err = c->d_err;
     A.TE = c->TE;
+    A.wide = c->wide;
     return A;
 }
 
@@ -351,11 +357,18 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
     return cudaSuccess;
 }
 
+bool tile_fits_1d(const frsg_ctx* c, int te, int wide) {
+    const int thr = te * c->Q * (wide ? c->Np : 1);
+    const size_t sm = wide ? frsg::stage1d_wide_smem_bytes(c->fp64, te, c->Np, c->M, c->Q, c->S)
+                           : frsg::stage1d_smem_bytes(c->fp64, te, c->Np, c->M, c->Q, c->S);
+    return thr <= (wide ? 256 : 512) && sm <= 200 * 1024;
+}
+
 int choose_tile_1d(const frsg_ctx* c) {
-    const int Q = c->Q;
     int te = std::max(1, c->E / (2 * 152));
-    te = std::min(te, std::max(1, 512 / Q));
-    while (te > 1 && frsg::stage1d_smem_bytes(c->fp64, te, c->Np, c->M, Q, c->S) > 200 * 1024) --te;
+    const int cap = c->wide ? 256 : 512;
+    te = std::min(te, std::max(1, cap / (c->Q * (c->wide ? c->Np : 1))));
+    while (te > 1 && !tile_fits_1d(c, te, c->wide)) --te;
     return te;
 }
 
@@ -440,6 +453,7 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     }
     if (e != cudaSuccess) return cleanup_fail(e, "upload");
+    ctx->wide = cfg->dim == 1 ? 1 : 0;
     ctx->TE = cfg->dim == 1 ? choose_tile_1d(ctx) : 1;
     ctx->TE_lim = std::max(1, 256 / ctx->Q);   // limit_kernel is built for at most 256 threads
     if (cfg->dim == 2) {
@@ -794,6 +808,98 @@ frsg_status fr_sg_check(frsg_ctx* ctx) {
 
 uint64_t fr_sg_launch_count(const frsg_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::mutex g_tune_mu;
+}  // namespace
+
+frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_out) {
+    if (!ctx) return FRSG_E_INVAL;
+    const frsg_config& c = ctx->cfg;
+    const TuneKey key{c.dim, c.P, c.N, c.Q, ctx->S, c.precision, ctx->E, c.filter != FRSG_FILTER_NONE, c.equation};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            ctx->wide = it->second.first;
+            ctx->TE = it->second.second;
+            if (ctx->graph_exec) {
+                cudaGraphExecDestroy(ctx->graph_exec);
+                ctx->graph_exec = nullptr;
+            }
+            if (variant_out) *variant_out = ctx->wide;
+            if (te_out) *te_out = ctx->TE;
+            return FRSG_OK;
+        }
+    }
+    if (reps < 1) reps = 5;
+    if (ctx->dt_set <= 0.0) CK(set_dt(ctx, 1e-3));
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    const int saved_wide = ctx->wide, saved_te = ctx->TE;
+    float best = 1e30f;
+    int best_w = saved_wide, best_te = saved_te;
+    const int variants = c.dim == 1 ? 2 : 1;
+    for (int w = 0; w < variants; ++w) {
+        for (int te : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+            bool fits;
+            if (c.dim == 1) {
+                fits = tile_fits_1d(ctx, te, w);
+            } else {
+                fits = te * ctx->Q * ctx->n1 <= 512 &&
+                       frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) <= 200 * 1024;
+            }
+            if (!fits || te > ctx->E) continue;
+            ctx->wide = c.dim == 1 ? w : 0;
+            ctx->TE = te;
+            CK(issue_stage(ctx, 0, ctx->dt_set, false));   // warm-up (and attribute setup)
+            CK(cudaEventRecord(ev0, ctx->stream));
+            for (int r = 0; r < reps; ++r) CK(issue_stage(ctx, 0, ctx->dt_set, false));
+            CK(cudaEventRecord(ev1, ctx->stream));
+            CK(cudaEventSynchronize(ev1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev0, ev1));
+            if (ms < best) {
+                best = ms;
+                best_w = ctx->wide;
+                best_te = te;
+            }
+        }
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    ctx->launches = 0;
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+    ctx->wide = best_w;
+    ctx->TE = best_te;
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = {best_w, best_te};
+    }
+    if (variant_out) *variant_out = best_w;
+    if (te_out) *te_out = best_te;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (variant < 0 || variant > 1) return fail(ctx, FRSG_E_INVAL, "variant must be 0 or 1");
+    if (ctx->cfg.dim != 1) return variant == 0 ? FRSG_OK : fail(ctx, FRSG_E_UNSUPPORTED, "2D has one layout");
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    ctx->wide = variant;
+    ctx->TE = choose_tile_1d(ctx);
+    return FRSG_OK;
+}
+
 static frsg_status adjoint_supported(frsg_ctx* ctx) {
     const frsg_config& c = ctx->cfg;
     if (c.dim != 1 || !ctx->fp64 || c.equation == FRSG_EQ_EULER || c.limiter || c.bc[0] != FRSG_BC_PERIODIC)
@@ -1093,8 +1199,7 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out) {
     if (te == 0) {
         want = ctx->cfg.dim == 1 ? choose_tile_1d(ctx) : choose_tile_2d(ctx);
     } else if (ctx->cfg.dim == 1) {
-        if (te * ctx->Q > 512 || frsg::stage1d_smem_bytes(ctx->fp64, te, ctx->Np, ctx->M, ctx->Q, ctx->S) > 220 * 1024)
-            return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
+        if (!tile_fits_1d(ctx, te, ctx->wide)) return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
     } else {
         if (te * ctx->Q * ctx->n1 > 512 ||
             frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) > 220 * 1024)

@@ -86,22 +86,15 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
     const T* ue = Us + te * elsz;
     T* me = Mod + te * elsz;
     T tot = T(0), top = T(0);
-    // pass A: modal coefficients of the own element; energies of variable 0
+    // pass A0: modal coefficients of variable 0 for every element; its energies
     if (active) {
         for (int k = kl; k < M; k += nk) {
             for (int m = ml; m < NP; m += nm) {
-                T acc[S];
+                T acc = T(0);
 #pragma unroll
-                for (int s = 0; s < S; ++s) acc[s] = T(0);
-#pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    const T vi = sVfinv[m * NP + j];
-#pragma unroll
-                    for (int s = 0; s < S; ++s) acc[s] += vi * ue[(j * M + k) * S + s];
-                }
-#pragma unroll
-                for (int s = 0; s < S; ++s) me[(m * M + k) * S + s] = acc[s];
-                const T v2 = acc[0] * acc[0];
+                for (int j = 0; j < NP; ++j) acc += sVfinv[m * NP + j] * ue[(j * M + k) * S];
+                me[(m * M + k) * S] = acc;
+                const T v2 = acc * acc;
                 tot += v2;
                 if (sTop[m] != T(0) || k == M - 1) top += v2;
             }
@@ -128,6 +121,27 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
         if (A.flags) A.flags[e] = (uint8_t)fl;
     }
     __syncthreads();
+    // pass A1: the other variables' modal coefficients, flagged elements only
+    if constexpr (S > 1) {
+        if (active && sFlag[te]) {
+            for (int k = kl; k < M; k += nk) {
+                for (int m = ml; m < NP; m += nm) {
+                    T acc[S];
+#pragma unroll
+                    for (int s = 1; s < S; ++s) acc[s] = T(0);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const T vi = sVfinv[m * NP + j];
+#pragma unroll
+                        for (int s = 1; s < S; ++s) acc[s] += vi * ue[(j * M + k) * S + s];
+                    }
+#pragma unroll
+                    for (int s = 1; s < S; ++s) me[(m * M + k) * S + s] = acc[s];
+                }
+            }
+        }
+        __syncthreads();
+    }
     // pass B: filtered or unchanged coefficients
     bool bad = false;
     if (active) {

@@ -64,6 +64,7 @@ struct StageArgs {
     uint8_t* flags;        // [E] filter decisions taken, or null
     unsigned* err;
     int TE;                // elements per block
+    int wide;              // 1D: one thread per (z-node, point) instead of per z-node
 };
 
 struct LimitArgs {

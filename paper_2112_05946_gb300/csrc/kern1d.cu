@@ -237,6 +237,202 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     if (bad) atomicOr(A.err, kErrNonFinite);
 }
 
+// Wide variant: thread (q, j, te) owns z-node q of solution point j of element te, so an
+// element has Q*NP threads and each carries one point's share of every step.
+template <typename T>
+__host__ __device__ inline size_t smem1d_wide_bytes(int TE, int NP, int M, int Q, int S) {
+    size_t n = 0;
+    n += (size_t)(TE + 2) * NP * M * S;              // U: halo + tile coefficients
+    n += (size_t)TE * NP * M * S;                    // B: SSP base
+    n += (size_t)(TE + 2) * NP * S * Q;              // Un: nodal values (halo + tile)
+    n += (size_t)TE * NP * S * Q;                    // F: nodal fluxes (tile)
+    n += (size_t)TE * NP * S * (Q > M ? Q : M);      // G: nodal residual, later modal coefficients
+    n += 2 * (size_t)M * Q;                          // Vz, Pz
+    n += (size_t)NP * NP + 4 * NP;                   // D, lm, lp, dhL, dhR
+    n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;  // Vf, Vfinv, Lam, Top
+    n += (size_t)2 * TE * Q * NP;                    // Red
+    return n * sizeof(T) + (size_t)TE * sizeof(int) + 16;
+}
+
+template <typename T, int NP, int S, int EQ>
+__global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Q = A.Q, M = A.M, TE = A.TE, E = A.E;
+    const int tq = threadIdx.x, tj = threadIdx.y, te = threadIdx.z;
+    const int tid = (te * NP + tj) * Q + tq, nthr = Q * NP * TE;
+    const int e0 = blockIdx.x * TE;
+    const int ne = min(TE, E - e0);
+    const int elsz = NP * M * S;
+    const int nsz = NP * S * Q;   // nodal values of one element
+    const T adv = (T)A.adv, gamma = (T)A.gamma;
+    const T* uin = static_cast<const T*>(A.uin);
+    const T* ubase = static_cast<const T*>(A.ubase);
+    const bool periodic = A.bc[0] == FRSG_BC_PERIODIC;
+
+    T* p = reinterpret_cast<T*>(smem_raw);
+    T* sU = p; p += (size_t)(TE + 2) * elsz;
+    T* sB = p; p += (size_t)TE * elsz;
+    T* sUn = p; p += (size_t)(TE + 2) * nsz;
+    T* sF = p; p += (size_t)TE * nsz;
+    T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
+    T* sVz = p; p += M * Q;
+    T* sPz = p; p += M * Q;
+    T* sD = p; p += NP * NP;
+    T* slm = p; p += NP;
+    T* slp = p; p += NP;
+    T* sdhL = p; p += NP;
+    T* sdhR = p; p += NP;
+    T* sVf = p; p += NP * NP;
+    T* sVfinv = p; p += NP * NP;
+    T* sLam = p; p += NP * M;
+    T* sTop = p; p += NP;
+    T* sRed = p; p += 2 * TE * Q * NP;
+    int* sFlag = reinterpret_cast<int*>(p);
+
+    const T* tab = table_block<T>(A);
+    for (int i = tid; i < M * Q; i += nthr) {
+        sVz[i] = tab[A.off.VzT + i];
+        sPz[i] = tab[A.off.Pz + i];
+    }
+    for (int i = tid; i < NP * NP; i += nthr) sD[i] = tab[A.off.D + i];
+    for (int i = tid; i < NP; i += nthr) {
+        slm[i] = tab[A.off.lm + i];
+        slp[i] = tab[A.off.lp + i];
+        sdhL[i] = tab[A.off.dhL + i];
+        sdhR[i] = tab[A.off.dhR + i];
+    }
+    const double dt = A.dtp ? *A.dtp : A.dt_filter;
+    if (A.do_filter) {
+        for (int i = tid; i < NP * NP; i += nthr) {
+            sVf[i] = tab[A.off.Vf + i];
+            sVfinv[i] = tab[A.off.Vfinv + i];
+        }
+        for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
+        load_filter_strengths<T>(A, NP, sLam, tid, nthr, dt);
+    }
+    const int nl = e0 - 1, nr = e0 + ne;
+    const bool hasL = nl >= 0 || periodic, hasR = nr < E || periodic;
+    {
+        const T* srcL = uin + (size_t)(nl < 0 ? E - 1 : nl) * elsz;
+        const T* srcR = uin + (size_t)(nr >= E ? 0 : nr) * elsz;
+        for (int i = tid; i < elsz; i += nthr) {
+            if (hasL) sU[i] = srcL[i];
+            if (hasR) sU[(ne + 1) * elsz + i] = srcR[i];
+        }
+        const T* srcT = uin + (size_t)e0 * elsz;
+        for (int i = tid; i < ne * elsz; i += nthr) sU[elsz + i] = srcT[i];
+        if (A.a != 0.0) {
+            const T* srcB = ubase + (size_t)e0 * elsz;
+            for (int i = tid; i < ne * elsz; i += nthr) sB[i] = srcB[i];
+        }
+    }
+    __syncthreads();
+
+    // ---- a2 + a3: nodal value and flux of point j at node q (halo slots: values only)
+    const bool active = te < ne;
+    auto zeval = [&](int slot, T (&out)[S]) {
+        const T* ue = sU + slot * elsz + tj * M * S;
+#pragma unroll
+        for (int s = 0; s < S; ++s) out[s] = T(0);
+        for (int k = 0; k < M; ++k) {
+            const T v = sVz[k * Q + tq];
+#pragma unroll
+            for (int s = 0; s < S; ++s) out[s] += v * ue[k * S + s];
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) sUn[((slot * NP + tj) * S + s) * Q + tq] = out[s];
+    };
+    T u[S], f[S];
+    if (active) {
+        zeval(te + 1, u);
+        phys_flux<T, EQ, S, 1, 0>(u, f, adv, gamma);
+#pragma unroll
+        for (int s = 0; s < S; ++s) sF[((te * NP + tj) * S + s) * Q + tq] = f[s];
+        T h[S];
+        if (te == 0 && hasL) zeval(0, h);
+        if (te == ne - 1 && hasR) zeval(ne + 1, h);
+    }
+    __syncthreads();
+
+    // ---- a5 + a6 + a7: traces, interface fluxes, derivative row j (nodal in z)
+    if (active) {
+        auto trace = [&](const T* src, const T* w, int s) {
+            T acc = T(0);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) acc += w[m] * src[(m * S + s) * Q + tq];
+            return acc;
+        };
+        const T* own = sUn + (size_t)(te + 1) * nsz;
+        const T* fown = sF + (size_t)te * nsz;
+        T uLf[S], uRf[S], nL[S], nR[S], fDL[S], fDR[S], fIL[S], fIR[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            uLf[s] = trace(own, slm, s);
+            uRf[s] = trace(own, slp, s);
+            fDL[s] = trace(fown, slm, s);
+            fDR[s] = trace(fown, slp, s);
+        }
+        // neighbours: the tile's own slots or the halo slots; ghosts at physical boundaries
+        if (te > 0 || hasL) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) nL[s] = trace(sUn + (size_t)te * nsz, slp, s);
+        } else if (A.bc[0] == FRSG_BC_DIRICHLET) {
+            const double* gh = A.ghost;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                T acc = T(0);
+                for (int k = 0; k < M; ++k) acc += sVz[k * Q + tq] * (T)gh[k * S + s];
+                nL[s] = acc;
+            }
+        } else {
+            ghost_from_interior<T, EQ, S, 0>(A.bc[0], uLf, nL);
+        }
+        if (te < ne - 1 || hasR) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) nR[s] = trace(sUn + (size_t)(te + 2) * nsz, slm, s);
+        } else if (A.bc[1] == FRSG_BC_DIRICHLET) {
+            const double* gh = A.ghost + (size_t)M * S;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                T acc = T(0);
+                for (int k = 0; k < M; ++k) acc += sVz[k * Q + tq] * (T)gh[k * S + s];
+                nR[s] = acc;
+            }
+        } else {
+            ghost_from_interior<T, EQ, S, 0>(A.bc[1], uRf, nR);
+        }
+        llf<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma);
+        llf<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma);
+        const T invJ = (T)A.invJx;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            T d = (fIL[s] - fDL[s]) * sdhL[tj] + (fIR[s] - fDR[s]) * sdhR[tj];
+#pragma unroll
+            for (int m = 0; m < NP; ++m) d += sD[tj * NP + m] * fown[(m * S + s) * Q + tq];
+            sG[((te * NP + tj) * S + s) * Q + tq] = -invJ * d;
+        }
+    }
+    __syncthreads();
+
+    // ---- a4 + a8: projection (k-lane q, row j), SSP combination
+    const T ca = (T)A.a, cb = (T)A.b, cc = (T)(A.dtp ? A.c * dt : A.c);
+    T* uout = static_cast<T*>(A.uout);
+    T* sTile = sU + elsz;
+    const size_t gbase = (size_t)e0 * elsz;
+    bool bad = false;
+    if (active) {
+        T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
+        bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
+                                         Q, tj, NP, ca, cb, cc, A.a != 0.0);
+    }
+    if (A.do_filter) {
+        __syncthreads();
+        bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tj, NP,
+                                              active, true, e0, uout, gbase);
+    }
+    if (bad) atomicOr(A.err, kErrNonFinite);
+}
+
 template <typename T, int NP, int S, int EQ>
 __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -268,6 +464,18 @@ __global__ void __launch_bounds__(256) stage1d_batched_kernel(const StageArgs* _
 template <typename T, int NP, int S, int EQ>
 cudaError_t launch_typed(const StageArgs& A, cudaStream_t st) {
     const int TE = A.TE;
+    if (A.wide) {
+        const size_t smem = smem1d_wide_bytes<T>(TE, NP, A.M, A.Q, S);
+        auto kern = stage1d_wide_kernel<T, NP, S, EQ>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        dim3 block(A.Q, NP, TE);
+        dim3 grid((A.E + TE - 1) / TE);
+        kern<<<grid, block, smem, st>>>(A);
+        return cudaGetLastError();
+    }
     const size_t smem = smem1d_bytes<T>(TE, NP, A.M, A.Q, S);
     auto kern = stage1d_kernel<T, NP, S, EQ>;
     if (smem > 48 * 1024) {
@@ -305,6 +513,10 @@ cudaError_t launch_np(const frsg_config& cfg, const StageArgs& A, cudaStream_t s
 
 size_t stage1d_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S) {
     return fp64 ? smem1d_bytes<double>(TE, NP, M, Q, S) : smem1d_bytes<float>(TE, NP, M, Q, S);
+}
+
+size_t stage1d_wide_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S) {
+    return fp64 ? smem1d_wide_bytes<double>(TE, NP, M, Q, S) : smem1d_wide_bytes<float>(TE, NP, M, Q, S);
 }
 
 cudaError_t launch_stage1d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st) {

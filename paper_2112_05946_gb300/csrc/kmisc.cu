@@ -61,62 +61,171 @@ __device__ inline double pressure_root(const double* ub, const double* us, doubl
     return fmin(fmax(beta, 0.0), 1.0);
 }
 
-// Block (Q, TE): thread (q, te) owns z-node q of element te.
-template <typename T, int NPT, int S>
+// Visit the state at each of the limiter's points, given the solution-point values v[s][j]:
+// the solution points themselves, then the flux points on the faces, each interpolated along
+// its line of points (1D: r = -1, +1; 2D: r = -1 and r = +1 for every s_b, s = -1 and s = +1
+// for every r_a) with n1 multiply-adds per face point and variable.
+template <typename T, int N1, int DIM, int S, typename F>
+__device__ inline void for_each_limiter_point(const T (&v)[S][DIM == 1 ? N1 : N1 * N1], const T* lm, const T* lp,
+                                              F&& visit) {
+    constexpr int NPT = DIM == 1 ? N1 : N1 * N1;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        T val[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) val[s] = v[s][j];
+        visit(val);
+    }
+    constexpr int NLINE = DIM == 1 ? 1 : N1;
+#pragma unroll
+    for (int face = 0; face < 2 * DIM; ++face) {
+        const T* w = (face & 1) ? lp : lm;
+#pragma unroll
+        for (int i = 0; i < NLINE; ++i) {
+            T val[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                T acc = T(0);
+#pragma unroll
+                for (int l = 0; l < N1; ++l) {
+                    const int j = DIM == 1 ? l : (face < 2 ? i * N1 + l : l * N1 + i);
+                    acc += w[l] * v[s][j];
+                }
+                val[s] = acc;
+            }
+            visit(val);
+        }
+    }
+}
+
+// Block (Q, TE): thread (q, te) owns z-node q of element te.  Screening pass in the state's
+// precision T over all elements; the exact FP64 test and the limiting (§4.3, Eqs. 48-52) for
+// elements the screen cannot clear.  For T = double the screen is the exact test.
+template <typename T, int N1, int DIM, int S>
 __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
+    constexpr int NPT = DIM == 1 ? N1 : N1 * N1;
     extern __shared__ double lsm[];
-    const int Q = A.Q, M = A.M, TE = A.TE, NL = A.off.NL;
+    const int Q = A.Q, M = A.M, TE = A.TE;
     const int tq = threadIdx.x, te = threadIdx.y;
     const int e = blockIdx.x * TE + te;
     const bool active = e < A.E;
-    double* un = lsm + (size_t)te * NPT * S * Q;          // nodal values [j][s][q]
-    double* red = lsm + (size_t)TE * NPT * S * Q;         // [TE][Q][2]
+    double* red = lsm;                                    // [TE][Q][2]
     double* el = red + (size_t)TE * Q * 2;                // [TE][4]: rho_min, p_min, beta1, beta2
+    int* cand = reinterpret_cast<int*>(el + (size_t)TE * 4);   // [TE]
     T* u = static_cast<T*>(A.u);
     const size_t elsz = (size_t)NPT * M * S;
     const double* tab = A.tab;
     const double gamma = A.gamma;
+    T lmT[N1], lpT[N1];
+    double lmD[N1], lpD[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        lmD[j] = tab[A.off.lm + j];
+        lpD[j] = tab[A.off.lp + j];
+        lmT[j] = (T)lmD[j];
+        lpT[j] = (T)lpD[j];
+    }
 
-    double ubar[S];
-    double rho_bar = 1.0, p_bar = 1.0, eps = 0.0;
-    bool admissible = true;
-    double rmin = 1e300, pmin = 1e300;
+    const bool exact = sizeof(T) == sizeof(double);
     if (active) {
+        const T* ue = u + (size_t)e * elsz;
+        // screen in T: element mean, nodal values at the solution points, every limiter point
+        T ub[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) ub[s] = T(0);
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const T wj = (T)tab[A.off.w + j];
+#pragma unroll
+            for (int s = 0; s < S; ++s) ub[s] += wj * ue[(size_t)j * M * S + s];
+        }
+        T v[S][NPT];
+#pragma unroll
+        for (int j = 0; j < NPT; ++j)
+#pragma unroll
+            for (int s = 0; s < S; ++s) v[s][j] = T(0);
+        for (int k = 0; k < M; ++k) {
+            const T vz = (T)tab[A.off.VzT + k * Q + tq];
+#pragma unroll
+            for (int j = 0; j < NPT; ++j)
+#pragma unroll
+                for (int s = 0; s < S; ++s) v[s][j] += vz * ue[((size_t)j * M + k) * S + s];
+        }
+        T rmin = T(1e30), pmin = T(1e30);
+        const T g1 = (T)(gamma - 1.0);
+        for_each_limiter_point<T, N1, DIM, S>(v, lmT, lpT, [&](const T (&w)[S]) {
+            T m2 = T(0);
+#pragma unroll
+            for (int d = 1; d < S - 1; ++d) m2 += w[d] * w[d];
+            rmin = fmin(rmin, w[0]);
+            pmin = fmin(pmin, g1 * (w[S - 1] - T(0.5) * m2 / w[0]));
+        });
+        // thresholds: exact for double states; for float states eps <= 1e-8 plus a margin far
+        // above float rounding (1e-4 of the mean density / energy), so that a cleared element
+        // is certainly admissible and untriggered in exact arithmetic
+        T m2 = T(0);
+#pragma unroll
+        for (int d = 1; d < S - 1; ++d) m2 += ub[d] * ub[d];
+        const T pb = g1 * (ub[S - 1] - T(0.5) * m2 / ub[0]);
+        bool c;
+        if (exact) {
+            const T eps_e = fmin(T(1e-8), fmin(ub[0], pb));
+            c = !(ub[0] > T(0) && pb > T(0)) || rmin < eps_e || pmin < eps_e;
+        } else {
+            const T mr = T(1e-4) * fabs(ub[0]), me = T(1e-4) * fabs(ub[S - 1]);
+            c = !(ub[0] > mr && pb > me) || rmin < T(1e-8) + mr || pmin < T(1e-8) + me;
+        }
+        c = c || !(rmin == rmin) || !(pmin == pmin);
+        red[(te * Q + tq) * 2 + 0] = c ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (active && tq == 0) {
+        int any = 0;
+        for (int i = 0; i < Q; ++i) any |= red[(te * Q + i) * 2 + 0] != 0.0;
+        cand[te] = any;
+    }
+    __syncthreads();
+    const bool is_cand = active && cand[te];
+    // exact pass in double for candidate elements: mean, admissibility, minima, beta
+    double vd[S][NPT];
+    double ubar[S];
+    double rho_bar = 1.0, eps = 0.0;
+    bool admissible = true;
+    if (is_cand) {
         const T* ue = u + (size_t)e * elsz;
 #pragma unroll
         for (int s = 0; s < S; ++s) ubar[s] = 0.0;
+#pragma unroll
         for (int j = 0; j < NPT; ++j) {
             const double wj = tab[A.off.w + j];
 #pragma unroll
             for (int s = 0; s < S; ++s) ubar[s] += wj * ld(ue, (size_t)j * M * S + s);
         }
         rho_bar = ubar[0];
-        p_bar = pressure_d<S>(ubar, gamma);
+        const double p_bar = pressure_d<S>(ubar, gamma);
         admissible = rho_bar > 0.0 && p_bar > 0.0;
         eps = fmin(1e-8, fmin(rho_bar, p_bar));
+#pragma unroll
         for (int j = 0; j < NPT; ++j)
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                double acc = 0.0;
-                for (int k = 0; k < M; ++k) acc += tab[A.off.VzT + k * Q + tq] * ld(ue, ((size_t)j * M + k) * S + s);
-                un[(j * S + s) * Q + tq] = acc;
-            }
-        for (int l = 0; l < NL; ++l) {
-            double ul[S];
+            for (int s = 0; s < S; ++s) vd[s][j] = 0.0;
+        for (int k = 0; k < M; ++k) {
+            const double vz = tab[A.off.VzT + k * Q + tq];
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                double acc = 0.0;
-                for (int j = 0; j < NPT; ++j) acc += tab[A.off.Lpts + l * NPT + j] * un[(j * S + s) * Q + tq];
-                ul[s] = acc;
-            }
-            rmin = fmin(rmin, ul[0]);
-            pmin = fmin(pmin, pressure_d<S>(ul, gamma));
+            for (int j = 0; j < NPT; ++j)
+#pragma unroll
+                for (int s = 0; s < S; ++s) vd[s][j] += vz * ld(ue, ((size_t)j * M + k) * S + s);
         }
+        double rmin = 1e300, pmin = 1e300;
+        for_each_limiter_point<double, N1, DIM, S>(vd, lmD, lpD, [&](const double (&w)[S]) {
+            rmin = fmin(rmin, w[0]);
+            pmin = fmin(pmin, pressure_d<S>(w, gamma));
+        });
         red[(te * Q + tq) * 2 + 0] = rmin;
         red[(te * Q + tq) * 2 + 1] = pmin;
     }
     __syncthreads();
-    if (active && tq == 0) {
+    if (is_cand && tq == 0) {
         double a = 1e300, b = 1e300;
         for (int i = 0; i < Q; ++i) {
             a = fmin(a, red[(te * Q + i) * 2 + 0]);
@@ -131,21 +240,17 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
         if (!(a == a) || !(b == b)) atomicOr(A.err, kErrNonFinite);
     }
     __syncthreads();
-    const bool trig = active && admissible && fmin(el[te * 4 + 0], el[te * 4 + 1]) < eps;
+    const bool trig = is_cand && admissible && fmin(el[te * 4 + 0], el[te * 4 + 1]) < eps;
     if (trig) {
         const double beta1 = el[te * 4 + 2];
         double bmin = 1.0;
-        for (int l = 0; l < NL; ++l) {
-            double ul[S];
+        for_each_limiter_point<double, N1, DIM, S>(vd, lmD, lpD, [&](const double (&w)[S]) {
+            double us[S];
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                double acc = 0.0;
-                for (int j = 0; j < NPT; ++j) acc += tab[A.off.Lpts + l * NPT + j] * un[(j * S + s) * Q + tq];
-                ul[s] = acc;
-            }
-            ul[0] = beta1 * (ul[0] - rho_bar) + rho_bar;
-            if (pressure_d<S>(ul, gamma) < eps) bmin = fmin(bmin, pressure_root<S>(ubar, ul, eps, gamma));
-        }
+            for (int d = 0; d < S; ++d) us[d] = w[d];
+            us[0] = beta1 * (us[0] - rho_bar) + rho_bar;
+            if (pressure_d<S>(us, gamma) < eps) bmin = fmin(bmin, pressure_root<S>(ubar, us, eps, gamma));
+        });
         red[(te * Q + tq) * 2 + 0] = bmin;
     }
     __syncthreads();
@@ -251,14 +356,10 @@ int grid_for(size_t n, int threads) {
     return (int)g;
 }
 
-template <typename T, int NPT, int S>
+template <typename T, int N1, int DIM, int S>
 cudaError_t limit_typed(const LimitArgs& A, cudaStream_t st) {
-    const size_t smem = sizeof(double) * ((size_t)A.TE * NPT * S * A.Q + (size_t)A.TE * A.Q * 2 + (size_t)A.TE * 4);
-    auto kern = limit_kernel<T, NPT, S>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const size_t smem = sizeof(double) * ((size_t)A.TE * A.Q * 2 + (size_t)A.TE * 4) + sizeof(int) * A.TE + 16;
+    auto kern = limit_kernel<T, N1, DIM, S>;
     dim3 block(A.Q, A.TE);
     dim3 grid((A.E + A.TE - 1) / A.TE);
     kern<<<grid, block, smem, st>>>(A);
@@ -269,16 +370,16 @@ template <typename T>
 cudaError_t limit_np(const LimitArgs& A, cudaStream_t st) {
     if (A.dim == 1) {
         switch (A.Np) {
-            case 2: return limit_typed<T, 2, 3>(A, st);
-            case 3: return limit_typed<T, 3, 3>(A, st);
-            case 4: return limit_typed<T, 4, 3>(A, st);
-            case 5: return limit_typed<T, 5, 3>(A, st);
+            case 2: return limit_typed<T, 2, 1, 3>(A, st);
+            case 3: return limit_typed<T, 3, 1, 3>(A, st);
+            case 4: return limit_typed<T, 4, 1, 3>(A, st);
+            case 5: return limit_typed<T, 5, 1, 3>(A, st);
         }
     } else {
         switch (A.Np) {
-            case 4: return limit_typed<T, 4, 4>(A, st);
-            case 9: return limit_typed<T, 9, 4>(A, st);
-            case 16: return limit_typed<T, 16, 4>(A, st);
+            case 4: return limit_typed<T, 2, 2, 4>(A, st);
+            case 9: return limit_typed<T, 3, 2, 4>(A, st);
+            case 16: return limit_typed<T, 4, 2, 4>(A, st);
         }
     }
     return cudaErrorInvalidValue;

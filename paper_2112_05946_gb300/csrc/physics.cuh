@@ -54,9 +54,33 @@ __device__ __forceinline__ T wave_speed(const T (&u)[S], T adv, T gamma) {
     }
 }
 
+// Euler flux along DIR and the spectral radius |v_n| + c from one reciprocal of rho.
+template <typename T, int S, int DIM, int DIR>
+__device__ __forceinline__ T euler_flux_speed(const T (&u)[S], T (&f)[S], T gamma) {
+    const T ir = T(1) / u[0];
+    T m2 = T(0);
+#pragma unroll
+    for (int d = 1; d < S - 1; ++d) m2 += u[d] * u[d];
+    const T p = (gamma - T(1)) * (u[S - 1] - T(0.5) * m2 * ir);
+    const T vn = u[1 + DIR] * ir;
+#pragma unroll
+    for (int s = 0; s < S; ++s) f[s] = u[s] * vn;
+    f[1 + DIR] += p;
+    f[S - 1] += p * vn;
+    return fabs(vn) + sqrt(gamma * p * ir);
+}
+
 // f^I = (f(uL) + f(uR))/2 - alpha (uR - uL)/2, alpha = max(lambda(uL), lambda(uR)).
 template <typename T, int EQ, int S, int DIM, int DIR>
 __device__ __forceinline__ void llf(const T (&uL)[S], const T (&uR)[S], T (&fI)[S], T adv, T gamma) {
+    if constexpr (EQ == FRSG_EQ_EULER) {
+        T fL[S], fR[S];
+        const T a = fmax(euler_flux_speed<T, S, DIM, DIR>(uL, fL, gamma),
+                         euler_flux_speed<T, S, DIM, DIR>(uR, fR, gamma));
+#pragma unroll
+        for (int s = 0; s < S; ++s) fI[s] = T(0.5) * (fL[s] + fR[s]) - T(0.5) * a * (uR[s] - uL[s]);
+        return;
+    }
     T fL[S], fR[S];
     phys_flux<T, EQ, S, DIM, DIR>(uL, fL, adv, gamma);
     phys_flux<T, EQ, S, DIM, DIR>(uR, fR, adv, gamma);

@@ -78,6 +78,9 @@ _SIGNATURES = [
     ("fr_sg_check", ctypes.c_int, [ctypes.c_void_p]),
     ("fr_sg_launch_count", ctypes.c_uint64, [ctypes.c_void_p]),
     ("fr_sg_set_tile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("fr_sg_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
     ("fr_sg_forward_record", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_adjoint", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
@@ -308,6 +311,16 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.fr_sg_launch_count(self.h))
+
+    def autotune(self, reps=5):
+        """Pick the fastest stage-kernel layout and tile (cached per problem shape)."""
+        v, t = ctypes.c_int(), ctypes.c_int()
+        self._ck(self.lib.fr_sg_autotune(self.h, int(reps), ctypes.byref(v), ctypes.byref(t)), "autotune")
+        return v.value, t.value
+
+    def set_variant(self, variant):
+        """1D stage layout: 0 thread per (z-node, element), 1 thread per (z-node, point, element)."""
+        self._ck(self.lib.fr_sg_set_variant(self.h, int(variant)), "set_variant")
 
 
 class Batch:

@@ -45,11 +45,15 @@ CASES = [
 
 @pytest.mark.parametrize("name,orders,base,amp", CASES)
 @pytest.mark.parametrize("tile", [1, 3, 8])
-def test_rhs_parity(name, orders, base, amp, tile):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_rhs_parity(name, orders, base, amp, tile, variant):
     wl = workloads.ALL[name]()
     over = dict(orders, nx=37)
     prob = oracle_problem(wl, **over)
     s = solver(wl, **over)
+    s.set_variant(variant)
+    if variant == 1 and tile * s.Q * s.Np > 256:
+        tile = max(1, 256 // (s.Q * s.Np))
     assert s.set_tile(tile) == tile
     u = workloads.random_state(s.state_shape, seed=11 + tile, base=base, amp=amp)
     ref = scheme.rhs(prob, prob.tabs(), u)
@@ -58,11 +62,14 @@ def test_rhs_parity(name, orders, base, amp, tile):
 
 
 @pytest.mark.parametrize("bc", [("outflow", "outflow"), ("reflect", "reflect"), ("dirichlet", "outflow")])
-def test_rhs_boundaries(bc):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_rhs_boundaries(bc, variant):
     wl = workloads.sod_1d(nx=9, P=2, N=3, Q=6)
     over = dict(bc=bc + ("periodic", "periodic"), nx=9)
     prob = oracle_problem(wl, **over)
     s = solver(wl, **over)
+    s.set_variant(variant)
+    s.set_tile(3)
     u = workloads.random_state(s.state_shape, seed=3, base=[1.0, 0.4, 2.5], amp=[0.05, 0.05, 0.1])
     got = _rhs_gpu(s, u)
     ref = scheme.rhs(prob, prob.tabs(), u)
@@ -92,13 +99,15 @@ def test_cfl_dt(name):
     assert abs(s.cfl_dt(0.1) / integrate.cfl_dt(prob, prob.tabs(), u, 0.1) - 1) < 1e-13
 
 
-@pytest.mark.parametrize("tile", [1, 5])
-def test_one_step_burgers_with_filter(tile):
+@pytest.mark.parametrize("tile", [1, 3])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_one_step_burgers_with_filter(tile, variant):
     """One SSP-RK3 step with the detector-switched exponential filter, from a state with
     a steep front so that some elements are flagged and others are not."""
     wl = workloads.burgers_1d(nx=40)
     prob = oracle_problem(wl)
     s = solver(wl)
+    s.set_variant(variant)
     s.set_tile(tile)
     x = s.nodes()[0]
     rng = np.random.default_rng(4)
@@ -269,3 +278,23 @@ def test_inadmissible_mean_is_reported():
     with pytest.raises(frsg.FrsgError) as ei:
         s.check()
     assert ei.value.status == frsg.E_POSITIVITY
+
+
+@pytest.mark.parametrize("name", ["burgers", "sod"])
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", 1e-5)])
+def test_autotuned_choice_keeps_parity(name, precision, tol):
+    wl = workloads.ALL[name](nx=64)
+    prob = oracle_problem(wl)
+    s = solver(wl, precision=precision)
+    variant, tile = s.autotune(reps=2)
+    assert variant in (0, 1) and tile >= 1
+    base = [0.2] if name == "burgers" else [1.0, 0.2, 2.5]
+    amp = [0.5] if name == "burgers" else [0.05, 0.05, 0.1]
+    u = workloads.random_state(s.state_shape, seed=8, base=base, amp=amp)
+    if precision == "fp32":
+        u = u.astype(np.float32).astype(np.float64)
+    ref = scheme.rhs(prob, prob.tabs(), u)
+    assert rel_l2(_rhs_gpu(s, u), ref) < tol
+    # a second context of the same shape takes the cached choice
+    s2 = solver(wl, precision=precision)
+    assert s2.autotune() == (variant, tile)
