@@ -199,7 +199,11 @@ def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracl
     mean_stage = np.mean(np.array(stage_ms), axis=0)           # ms per stage launch
     arrays = [2, 3, 3]                                         # state arrays read+written per stage
     alg_bytes = [a * esz * dof for a in arrays]
-    achieved = sum(alg_bytes) / (sum(mean_stage) * 1e-3) / 1e9  # GB/s over the stage kernels
+    if variant == 2:
+        # one launch per step: the timed step is the kernel
+        achieved = sum(alg_bytes) / (ms * 1e-3) / 1e9
+    else:
+        achieved = sum(alg_bytes) / (sum(mean_stage) * 1e-3) / 1e9  # GB/s over the stage kernels
     return dict(
         precision=precision, value=dof * 3 / (ms * 1e-3), ms_per_step=ms, err_vs_oracle=err,
         err_bound=ERR_BOUND[precision], dof=dof, launches=launches, steady_ms=steady_ms,
@@ -452,9 +456,10 @@ def run_ours(args):
         with open(pk) as f:
             peaks = json.load(f)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    kname = {0: "stage1d_kernel", 1: "stage1d_wide_kernel", 2: "stage1d_step_kernel"}[chosen["variant"]]
     roofline = {"bound": "hbm", "achieved": round(chosen["achieved_gbs"], 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(chosen["achieved_gbs"] / hbm_peak, 5), "traffic": None,
-                "kernel": "stage1d_kernel", "peak_source": "measured" if peaks else "fallback",
+                "kernel": kname, "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_step": chosen["alg_bytes_per_step"], "stage_us": chosen["stage_us"]}
 
     cpu = None

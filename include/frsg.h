@@ -220,15 +220,17 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out);
 
 /* Layout of the 1D stage kernel: 0 = one thread per (z-node, element), looping over the
  * element's solution points; 1 (the default for 1D) = one thread per (z-node, point,
- * element).  Both compute the same stage; the tile is re-chosen automatically.
- * 2D contexts accept only 0 (FRSG_E_UNSUPPORTED for 1). */
+ * element); 2 = layout 0, with the three stages of an SSP-RK3 step in ONE cooperative launch
+ * separated by grid-wide barriers (1D without limiter; a barrier that waits longer than
+ * about 2 s latches FRSG_E_TIMEOUT and the kernel returns).  All compute the same stage; the
+ * tile is re-chosen automatically.  2D contexts accept only 0 (FRSG_E_UNSUPPORTED otherwise). */
 frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant);
 
-/* Autotuner: times the stage kernel (stage 0 of a step, reps launches each, CUDA events on
- * the context's stream) for every layout (1D) and tile that fits, keeps the fastest and
- * caches the choice per (dim, P, N, Q, S, precision, elements, filter, equation) for the
- * process.  Overwrites the first stage buffer and the decision rows; the state is kept.
- * Synchronises.  variant_out / te_out (may be NULL) receive the choice. */
+/* Autotuner: times whole SSP-RK3 steps (reps per candidate, CUDA events on the context's
+ * stream) for every layout (1D) and tile that fits, keeps the fastest and caches the choice
+ * per (dim, P, N, Q, S, precision, elements, filter, equation) for the process.  Saves and
+ * restores the state (one temporary device allocation); overwrites the stage buffers and
+ * the decision rows.  Synchronises.  variant_out / te_out (may be NULL) receive the choice. */
 frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_out);
 
 /* Number of kernel launches issued on this context since creation (graph replays count

@@ -38,6 +38,7 @@ struct frsg_ctx {
     void* d_u2 = nullptr;
     double* d_conv = nullptr;     // FP32 contexts: double staging buffer for set/get_state
     double* d_dt = nullptr;       // step size read by the stage kernels (graphs do not depend on dt)
+    unsigned* d_bar = nullptr;    // grid-barrier words of the one-launch step (count, generation)
     double dt_set = -1.0;         // value last written to d_dt
     uint8_t* d_flags = nullptr;   // [3][E]
     double* d_beta = nullptr;     // [3][E]
@@ -255,7 +256,7 @@ StageArgs base_args(frsg_ctx* c) {
     A.det_ratio = frsg::detector_ratio(c->cfg.s0, c->cfg.kappa);
     A.err = c->d_err;
     A.TE = c->TE;
-    A.wide = c->wide;
+    A.wide = c->wide == 1 ? 1 : 0;
     return A;
 }
 
@@ -349,7 +350,40 @@ cudaError_t set_dt(frsg_ctx* c, double dt) {
     return e;
 }
 
+bool one_launch_step(const frsg_ctx* c) { return c->cfg.dim == 1 && c->wide == 2 && !c->cfg.limiter; }
+
 cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
+    if (one_launch_step(c)) {
+        // one cooperative launch for the three stages (variant 2)
+        const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
+        void* bin[3] = {c->d_u, c->d_u1, c->d_u2};
+        void* bout[3] = {c->d_u1, c->d_u2, c->d_u};
+        const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+        const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+        StageArgs A3[3];
+        for (int s = 0; s < 3; ++s) {
+            StageArgs A = base_args(c);
+            A.wide = 0;
+            A.uin = bin[s];
+            A.ubase = c->d_u;
+            A.uout = bout[s];
+            A.a = ca[s];
+            A.b = cb[s];
+            A.c = cb[s];
+            A.dtp = c->d_dt;
+            A.dt_filter = dt;
+            A.do_filter = filt ? 1 : 0;
+            A.flags = c->d_flags + (size_t)s * c->E;
+            A.replay = nullptr;
+            if (use_replay && c->replay_pos < c->replay_rows) {
+                A.replay = c->d_replay + (size_t)c->replay_pos * c->E;
+                c->replay_pos += 1;
+            }
+            A3[s] = A;
+        }
+        c->launches += 1;
+        return frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
+    }
     for (int s = 0; s < 3; ++s) {
         cudaError_t e = issue_stage(c, s, dt, use_replay);
         if (e != cudaSuccess) return e;
@@ -365,10 +399,11 @@ bool tile_fits_1d(const frsg_ctx* c, int te, int wide) {
 }
 
 int choose_tile_1d(const frsg_ctx* c) {
+    const int w = c->wide == 1 ? 1 : 0;
     int te = std::max(1, c->E / (2 * 152));
-    const int cap = c->wide ? 256 : 512;
-    te = std::min(te, std::max(1, cap / (c->Q * (c->wide ? c->Np : 1))));
-    while (te > 1 && !tile_fits_1d(c, te, c->wide)) --te;
+    const int cap = w ? 256 : 512;
+    te = std::min(te, std::max(1, cap / (c->Q * (w ? c->Np : 1))));
+    while (te > 1 && !tile_fits_1d(c, te, w)) --te;
     return te;
 }
 
@@ -438,6 +473,8 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     if (!ctx->fp64 && (e = cudaMalloc(&ctx->d_conv, sizeof(double) * nstate)) != cudaSuccess)
         return cleanup_fail(e, "conversion buffer");
     if ((e = cudaMalloc(&ctx->d_dt, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "dt");
+    if ((e = cudaMalloc(&ctx->d_bar, 2 * sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "barrier");
+    if ((e = cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "barrier");
     if ((e = cudaMalloc(&ctx->d_flags, 3 * (size_t)ctx->E)) != cudaSuccess) return cleanup_fail(e, "flags");
     if ((e = cudaMalloc(&ctx->d_beta, 3 * sizeof(double) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "beta");
     if ((e = cudaMalloc(&ctx->d_err, sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "err");
@@ -480,6 +517,7 @@ void fr_sg_destroy(frsg_ctx* ctx) {
     cudaFree(ctx->d_u2);
     cudaFree(ctx->d_conv);
     cudaFree(ctx->d_dt);
+    cudaFree(ctx->d_bar);
     cudaFree(ctx->d_flags);
     cudaFree(ctx->d_beta);
     cudaFree(ctx->d_err);
@@ -641,12 +679,12 @@ frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt) {
 frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     if (!ctx) return FRSG_E_INVAL;
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
-    const int kernels_per_step = 3 * (ctx->cfg.limiter ? 2 : 1);
+    const int kernels_per_step = one_launch_step(ctx) ? 1 : 3 * (ctx->cfg.limiter ? 2 : 1);
     if (nsteps == 0) return FRSG_OK;
     CK(set_dt(ctx, dt));
     for (int n = 0; n < nsteps; ++n) {
         const bool replaying = ctx->replay_pos < ctx->replay_rows;
-        if (use_graph && !replaying) {
+        if (use_graph && !replaying && !one_launch_step(ctx)) {
             if (!ctx->graph_exec) {
                 cudaStream_t cap = ctx->stream;
                 bool own = false;
@@ -801,7 +839,10 @@ frsg_status fr_sg_check(frsg_ctx* ctx) {
         CK(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
         if (err & frsg::kErrPositivity) return fail(ctx, FRSG_E_POSITIVITY, "an element mean has rho <= 0 or p <= 0");
         if (err & frsg::kErrNonFinite) return fail(ctx, FRSG_E_NONFINITE, "a kernel produced a non-finite value");
-        if (err & frsg::kErrTimeout) return fail(ctx, FRSG_E_TIMEOUT, "a bounded device wait gave up");
+        if (err & frsg::kErrTimeout) {
+            CK(cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned)));
+            return fail(ctx, FRSG_E_TIMEOUT, "a bounded device wait gave up");
+        }
     }
     return FRSG_OK;
 }
@@ -835,18 +876,23 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
     }
     if (reps < 1) reps = 5;
     if (ctx->dt_set <= 0.0) CK(set_dt(ctx, 1e-3));
+    const double dt = ctx->dt_set;
+    const size_t nbytes = ctx->esz * (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    void* saved = nullptr;
+    CK(cudaMalloc(&saved, nbytes));
+    CK(cudaMemcpyAsync(saved, ctx->d_u, nbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     cudaEvent_t ev0, ev1;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
     const int saved_wide = ctx->wide, saved_te = ctx->TE;
     float best = 1e30f;
     int best_w = saved_wide, best_te = saved_te;
-    const int variants = c.dim == 1 ? 2 : 1;
+    const int variants = c.dim == 1 ? (c.limiter ? 2 : 3) : 1;
     for (int w = 0; w < variants; ++w) {
         for (int te : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
             bool fits;
             if (c.dim == 1) {
-                fits = tile_fits_1d(ctx, te, w);
+                fits = tile_fits_1d(ctx, te, w == 1 ? 1 : 0);
             } else {
                 fits = te * ctx->Q * ctx->n1 <= 512 &&
                        frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) <= 200 * 1024;
@@ -854,9 +900,9 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
             if (!fits || te > ctx->E) continue;
             ctx->wide = c.dim == 1 ? w : 0;
             ctx->TE = te;
-            CK(issue_stage(ctx, 0, ctx->dt_set, false));   // warm-up (and attribute setup)
+            CK(issue_step(ctx, dt, false));   // warm-up (and attribute setup)
             CK(cudaEventRecord(ev0, ctx->stream));
-            for (int r = 0; r < reps; ++r) CK(issue_stage(ctx, 0, ctx->dt_set, false));
+            for (int r = 0; r < reps; ++r) CK(issue_step(ctx, dt, false));
             CK(cudaEventRecord(ev1, ctx->stream));
             CK(cudaEventSynchronize(ev1));
             float ms = 0.f;
@@ -866,8 +912,11 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
                 best_w = ctx->wide;
                 best_te = te;
             }
+            CK(cudaMemcpyAsync(ctx->d_u, saved, nbytes, cudaMemcpyDeviceToDevice, ctx->stream));
         }
     }
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(saved);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     ctx->launches = 0;
@@ -889,8 +938,10 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
 
 frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
     if (!ctx) return FRSG_E_INVAL;
-    if (variant < 0 || variant > 1) return fail(ctx, FRSG_E_INVAL, "variant must be 0 or 1");
+    if (variant < 0 || variant > 2) return fail(ctx, FRSG_E_INVAL, "variant must be 0, 1 or 2");
     if (ctx->cfg.dim != 1) return variant == 0 ? FRSG_OK : fail(ctx, FRSG_E_UNSUPPORTED, "2D has one layout");
+    if (variant == 2 && ctx->cfg.limiter)
+        return fail(ctx, FRSG_E_UNSUPPORTED, "the one-launch step does not run the limiter");
     if (ctx->graph_exec) {
         cudaGraphExecDestroy(ctx->graph_exec);
         ctx->graph_exec = nullptr;
@@ -1199,7 +1250,7 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out) {
     if (te == 0) {
         want = ctx->cfg.dim == 1 ? choose_tile_1d(ctx) : choose_tile_2d(ctx);
     } else if (ctx->cfg.dim == 1) {
-        if (!tile_fits_1d(ctx, te, ctx->wide)) return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
+        if (!tile_fits_1d(ctx, te, ctx->wide == 1 ? 1 : 0)) return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
     } else {
         if (te * ctx->Q * ctx->n1 > 512 ||
             frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) > 220 * 1024)

@@ -87,6 +87,10 @@ cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A
 cudaError_t launch_stage1d_batched(bool fp64, int equation, const StageArgs* args, const int4* tiles, int ntiles,
                                    size_t smem, int grid, cudaStream_t st);
 int stage1d_batched_blocks_per_sm(bool fp64, int equation, size_t smem);
+// One SSP-RK3 step (stage arguments A3[0..2]) as one cooperative launch with grid barriers;
+// bar: two zeroed device words (arrival count, generation).
+cudaError_t launch_step1d(const frsg_config& cfg, bool fp64, const StageArgs* A3, unsigned* bar, int* grid,
+                          cudaStream_t st);
 cudaError_t launch_limit(bool fp64, const LimitArgs& A, cudaStream_t st);
 cudaError_t launch_project(bool fp64, const double* u0, void* uhat, int E, int Np, int M, int Q, int S,
                            const double* tab, TabOff off, cudaStream_t st);

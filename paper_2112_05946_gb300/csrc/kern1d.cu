@@ -17,6 +17,8 @@
 //   a10 filter of flagged elements (§4.1, Eq. 34) and one coalesced store.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "epilogue.cuh"
 #include "internal.h"
 #include "physics.cuh"
@@ -441,6 +443,67 @@ __global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
     stage1d_tile<T, NP, S, EQ>(A, e0, min(A.TE, A.E - e0), tq, te, te * A.Q + tq, A.Q * A.TE, smem_raw);
 }
 
+// Grid-wide barrier for a cooperative launch (all CTAs resident).  Arrival counter and
+// generation word in global memory; the wait is bounded by kBarrierCycles of the SM clock,
+// after which the CTA latches kErrTimeout and reports failure instead of waiting on.
+constexpr long long kBarrierCycles = 4000000000LL;   // about 2 s at 2 GHz
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, unsigned* err,
+                                             int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd((unsigned*)gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// One SSP-RK3 step of one 1D problem in a single cooperative launch: the three stages
+// (args[0..2]) run over all tiles with a grid barrier between them.
+template <typename T, int NP, int S, int EQ>
+__global__ void __launch_bounds__(512) stage1d_step_kernel(const StageArgs a0, const StageArgs a1, const StageArgs a2,
+                                                           unsigned* bar) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_ok;
+    const int TE = a0.TE;
+    const int ntiles = (a0.E + TE - 1) / TE;
+    const int tq = threadIdx.x, te = threadIdx.y;
+    const int tid = te * a0.Q + tq, nthr = a0.Q * TE;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        stage1d_tile<T, NP, S, EQ>(a0, t * TE, min(TE, a0.E - t * TE), tq, te, tid, nthr, smem_raw);
+        __syncthreads();
+    }
+    if (!grid_barrier(bar, bar + 1, gridDim.x, a0.err, &s_ok)) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        stage1d_tile<T, NP, S, EQ>(a1, t * TE, min(TE, a1.E - t * TE), tq, te, tid, nthr, smem_raw);
+        __syncthreads();
+    }
+    if (!grid_barrier(bar, bar + 1, gridDim.x, a0.err, &s_ok)) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        stage1d_tile<T, NP, S, EQ>(a2, t * TE, min(TE, a2.E - t * TE), tq, te, tid, nthr, smem_raw);
+        __syncthreads();
+    }
+}
+
 // Persistent kernel over the tiles of many 1D problems (one StageArgs per problem): CTA b
 // takes tiles b, b + gridDim.x, ...; the shared-memory carve-up follows each tile's sizes.
 template <typename T, int S, int EQ>
@@ -524,6 +587,58 @@ cudaError_t launch_stage1d(const frsg_config& cfg, bool fp64, const StageArgs& A
 }
 
 namespace {
+template <typename T, int NP, int S, int EQ>
+cudaError_t step_typed(const StageArgs* A3, unsigned* bar, int* grid_out, cudaStream_t st) {
+    const int TE = A3[0].TE;
+    const size_t smem = smem1d_bytes<T>(TE, NP, A3[0].M, A3[0].Q, S);
+    auto kern = stage1d_step_kernel<T, NP, S, EQ>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int threads = A3[0].Q * TE;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (A3[0].E + TE - 1) / TE;
+    const int grid = std::max(1, std::min(ntiles, per_sm * sms));
+    if (grid_out) *grid_out = grid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(A3[0].Q, TE);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, A3[0], A3[1], A3[2], bar);
+}
+
+template <typename T, int NP>
+cudaError_t step_eq(int eq, const StageArgs* A3, unsigned* bar, int* g, cudaStream_t st) {
+    switch (eq) {
+        case FRSG_EQ_ADVECTION: return step_typed<T, NP, 1, FRSG_EQ_ADVECTION>(A3, bar, g, st);
+        case FRSG_EQ_BURGERS: return step_typed<T, NP, 1, FRSG_EQ_BURGERS>(A3, bar, g, st);
+        case FRSG_EQ_EULER: return step_typed<T, NP, 3, FRSG_EQ_EULER>(A3, bar, g, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t step_np(const frsg_config& cfg, const StageArgs* A3, unsigned* bar, int* g, cudaStream_t st) {
+    switch (cfg.P + 1) {
+        case 2: return step_eq<T, 2>(cfg.equation, A3, bar, g, st);
+        case 3: return step_eq<T, 3>(cfg.equation, A3, bar, g, st);
+        case 4: return step_eq<T, 4>(cfg.equation, A3, bar, g, st);
+        case 5: return step_eq<T, 5>(cfg.equation, A3, bar, g, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, int EQ>
 cudaError_t batched_typed(const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,
                           cudaStream_t st) {
@@ -555,6 +670,11 @@ cudaError_t launch_stage1d_batched(bool fp64, int equation, const StageArgs* arg
         return fp64 ? batched_typed<double, FRSG_EQ_BURGERS>(args, tiles, ntiles, smem, grid, st)
                     : batched_typed<float, FRSG_EQ_BURGERS>(args, tiles, ntiles, smem, grid, st);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step1d(const frsg_config& cfg, bool fp64, const StageArgs* A3, unsigned* bar, int* grid,
+                          cudaStream_t st) {
+    return fp64 ? step_np<double>(cfg, A3, bar, grid, st) : step_np<float>(cfg, A3, bar, grid, st);
 }
 
 int stage1d_batched_blocks_per_sm(bool fp64, int equation, size_t smem) {

@@ -100,7 +100,7 @@ def test_cfl_dt(name):
 
 
 @pytest.mark.parametrize("tile", [1, 3])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_one_step_burgers_with_filter(tile, variant):
     """One SSP-RK3 step with the detector-switched exponential filter, from a state with
     a steep front so that some elements are flagged and others are not."""
@@ -178,12 +178,14 @@ def test_burgers_run_past_shock_with_replayed_decisions():
     rec = []
     ref = integrate.run(prob, u0, dt, nsteps, record=rec)
     assert np.any(np.concatenate(rec))
-    s = solver(wl)
-    gpu_initial(s, wl)
-    s.set_replay(np.array(rec, dtype=np.uint8))
-    s.rk_step(dt, nsteps, graph=True)
-    s.check()
-    assert rel_l2(s.get_state(), ref) < 1e-11
+    for variant in (0, 1, 2):
+        s = solver(wl)
+        s.set_variant(variant)
+        gpu_initial(s, wl)
+        s.set_replay(np.array(rec, dtype=np.uint8))
+        s.rk_step(dt, nsteps, graph=True)
+        s.check()
+        assert rel_l2(s.get_state(), ref) < 1e-11, variant
     # free run: decisions compared stage by stage
     s2 = solver(wl)
     gpu_initial(s2, wl)
@@ -298,3 +300,23 @@ def test_autotuned_choice_keeps_parity(name, precision, tol):
     # a second context of the same shape takes the cached choice
     s2 = solver(wl, precision=precision)
     assert s2.autotune() == (variant, tile)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", 1e-5)])
+def test_one_launch_step_full_size(precision, tol):
+    """Variant 2 (three stages in one cooperative launch) on the 1024-element Burgers
+    workload: 50 steps against the oracle and against the three-launch path."""
+    wl = workloads.burgers_1d()
+    prob = oracle_problem(wl)
+    dt = wl["cfl"] * prob.dx / wl["lam0"]
+    ref = integrate.run(prob, oracle_initial(prob, wl), dt, 50)
+    outs = []
+    for variant in (2, 0):
+        s = solver(wl, precision=precision)
+        s.set_variant(variant)
+        gpu_initial(s, wl)
+        s.rk_step(dt, 50, graph=True)
+        s.check()
+        outs.append(s.get_state())
+        assert rel_l2(outs[-1], ref) < tol
+    assert rel_l2(outs[0], outs[1]) < (1e-14 if precision == "fp64" else 1e-6)
