@@ -72,6 +72,19 @@ def ssp_rk3_step(prob, tabs, uhat, dt, record=None, replay=None, stage_offset=0)
     return u3
 
 
+def rk4_step(prob, tabs, uhat, dt):
+    """One step of the classical four-stage Runge-Kutta scheme (the integrator of the
+    advection study, §5.1 setup table): k1 = L(u), k2 = L(u + dt/2 k1), k3 = L(u + dt/2 k2),
+    k4 = L(u + dt k3), u + dt/6 (k1 + 2 k2 + 2 k3 + k4).  No limiter or filter (the detector
+    switches the filter off in that study)."""
+    L = scheme.rhs
+    k1 = L(prob, tabs, uhat)
+    k2 = L(prob, tabs, uhat + 0.5 * dt * k1)
+    k3 = L(prob, tabs, uhat + 0.5 * dt * k2)
+    k4 = L(prob, tabs, uhat + dt * k3)
+    return uhat + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+
+
 def run(prob, uhat, dt, nsteps, record=None, replay=None):
     """nsteps SSP-RK3 steps of size dt."""
     tabs = prob.tabs()
