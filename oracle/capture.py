@@ -110,13 +110,72 @@ def filter_strengths(prob, dt):
     raise ValueError(prob.filter)
 
 
+def legendre_l1_norms(n):
+    """||psi_m||_1 for m < n: the L1 norm, under the uniform probability density on [-1, 1],
+    of the orthonormal Legendre function psi_m = sqrt(2m+1) P_m.  Between consecutive roots of
+    P_m the integrand is a plain polynomial of degree m, integrated exactly by Gauss
+    quadrature on each piece."""
+    from numpy.polynomial import legendre as npl
+    g, w = np.polynomial.legendre.leggauss(max(n, 2))
+    out = np.zeros(n)
+    for m in range(n):
+        c = np.zeros(m + 1)
+        c[m] = 1.0
+        roots = np.sort(np.real(npl.legroots(c))) if m > 0 else np.array([])
+        edges = np.concatenate([[-1.0], roots, [1.0]])
+        total = 0.0
+        for a, b in zip(edges[:-1], edges[1:]):
+            x = 0.5 * (b - a) * g + 0.5 * (a + b)
+            total += 0.5 * (b - a) * np.sum(w * np.abs(npl.legval(x, c)))
+        out[m] = 0.5 * np.sqrt(2 * m + 1) * total
+    return out
+
+
+def lasso_filter_modal(prob, ut):
+    """Lasso filter (§4.1.3) on the modal coefficients ut [E, m, k, S] of 1D elements.
+
+    Theorem 1 of §4.1.3: u*_{m,k} = ReLU(1 - (a1 m(m+1) + a2 k(k+1)) ||Psi_m Phi_k||_1 / |u_{m,k}|) u_{m,k}
+    (a coefficient equal to zero stays zero).  The strengths are chosen per element and
+    conserved variable so that the top physical coefficient u_{P,0} and the top random
+    coefficient u_{0,N} are set to zero:
+        a1 = |u_{P,0}| / (P (P+1) ||Psi_P Phi_0||_1),  a2 = |u_{0,N}| / (N (N+1) ||Psi_0 Phi_N||_1),
+    (N_p - 1 = P in the paper's notation), with a2 = 0 when N = 0.  Psi and Phi are the
+    orthonormal bases of the element and of the random space, so ||Psi_m Phi_k||_1 =
+    ||psi_m||_1 ||psi_k||_1."""
+    if prob.dim != 1:
+        raise ValueError("the Lasso filter is defined here for 1D elements")
+    P, N = prob.P, prob.N
+    lx = legendre_l1_norms(P + 1)
+    lz = legendre_l1_norms(N + 1)
+    norm = lx[:, None] * lz[None, :]                                     # [m, k]
+    m = np.arange(P + 1, dtype=np.float64)[:, None]
+    k = np.arange(N + 1, dtype=np.float64)[None, :]
+    out = np.empty_like(ut)
+    for e in range(ut.shape[0]):
+        for s in range(ut.shape[3]):
+            u = ut[e, :, :, s]
+            a1 = abs(u[P, 0]) / (P * (P + 1) * norm[P, 0])
+            a2 = abs(u[0, N]) / (N * (N + 1) * norm[0, N]) if N > 0 else 0.0
+            thr = (a1 * m * (m + 1) + a2 * k * (k + 1)) * norm
+            with np.errstate(divide="ignore", invalid="ignore"):
+                factor = np.where(u != 0.0, np.maximum(0.0, 1.0 - thr / np.abs(u)), 0.0)
+            out[e, :, :, s] = factor * u
+    return out
+
+
 def apply_filter(prob, tabs, uhat, dt, flags):
     """Filter the flagged elements: uhat <- Vx (Lambda o (Vx^{-1} uhat)) for every
-    conserved variable (§4.1, Eq. 34).  Unflagged elements are returned unchanged."""
+    conserved variable (§4.1, Eq. 34), or the Lasso filter on the modal coefficients
+    (§4.1.3).  Unflagged elements are returned unchanged."""
     if prob.filter == "none":
         return uhat.copy()
-    lam = filter_strengths(prob, dt)
     ut = to_modal_x(prob, tabs, uhat)
+    if prob.filter == "lasso":
+        filtered = to_nodal_x(prob, tabs, lasso_filter_modal(prob, ut))
+        out = uhat.copy()
+        out[flags] = filtered[flags]
+        return out
+    lam = filter_strengths(prob, dt)
     filtered = to_nodal_x(prob, tabs, ut * lam[None, ..., None])
     out = uhat.copy()
     out[flags] = filtered[flags]

@@ -72,17 +72,28 @@ def ssp_rk3_step(prob, tabs, uhat, dt, record=None, replay=None, stage_offset=0)
     return u3
 
 
-def rk4_step(prob, tabs, uhat, dt):
+def rk4_step(prob, tabs, uhat, dt, record=None, replay=None, stage_offset=0):
     """One step of the classical four-stage Runge-Kutta scheme (the integrator of the
-    advection study, §5.1 setup table): k1 = L(u), k2 = L(u + dt/2 k1), k3 = L(u + dt/2 k2),
-    k4 = L(u + dt k3), u + dt/6 (k1 + 2 k2 + 2 k3 + k4).  No limiter or filter (the detector
-    switches the filter off in that study)."""
+    advection study, §5.1 setup table):
+        y1 = u0 + dt/2 L(u0),  y2 = u0 + dt/2 L(y1),  y3 = u0 + dt L(y2),
+        u^{n+1} = u0 + dt/6 (L(u0) + 2 L(y1) + 2 L(y2) + L(y3)),
+    with u0 = lim(u^n).  Each stage is treated like an SSP stage (Eq. 53 per stage): its
+    input is limited before L is taken and its output y_i (and u^{n+1}) goes through the
+    detector and filter; the weighted sum of the L's is not a state and is not filtered.
+    With the filter and limiter off this is the textbook scheme."""
     L = scheme.rhs
-    k1 = L(prob, tabs, uhat)
-    k2 = L(prob, tabs, uhat + 0.5 * dt * k1)
-    k3 = L(prob, tabs, uhat + 0.5 * dt * k2)
-    k4 = L(prob, tabs, uhat + dt * k3)
-    return uhat + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    u0 = capture.limit(prob, tabs, uhat)
+    k = L(prob, tabs, u0)
+    acc = u0 + (dt / 6.0) * k
+    y = _finish_stage(prob, tabs, u0 + 0.5 * dt * k, dt, record, replay, stage_offset + 0)
+    for i, (cy, cacc) in enumerate(((0.5, 1.0 / 3.0), (1.0, 1.0 / 3.0))):
+        v = capture.limit(prob, tabs, y)
+        k = L(prob, tabs, v)
+        acc = acc + (cacc * dt) * k
+        y = _finish_stage(prob, tabs, u0 + (cy * dt) * k, dt, record, replay, stage_offset + 1 + i)
+    v = capture.limit(prob, tabs, y)
+    u = acc + (dt / 6.0) * L(prob, tabs, v)
+    return _finish_stage(prob, tabs, u, dt, record, replay, stage_offset + 3)
 
 
 def run(prob, uhat, dt, nsteps, record=None, replay=None):

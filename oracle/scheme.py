@@ -38,7 +38,7 @@ class Problem:
     equation: str = "advection"  # 'advection' | 'burgers' | 'euler'
     adv_speed: float = 1.0
     gamma: float = 1.4
-    filter: str = "none"  # 'none' | 'exp' | 'l2'
+    filter: str = "none"  # 'none' | 'exp' | 'l2' | 'lasso'
     sensor: bool = True  # filter only elements the detector flags (theta < 0.99)
     f_alpha: float = 36.0
     f_s: float = 4.0
