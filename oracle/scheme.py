@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY.  Plain FP64 numpy, every step in the paper's order:
 evaluate the gPC expansion at the random-space quadrature points (§2.1, Eq. 2),
 pointwise flux (§3.2, Eq. 15), Galerkin projection of the flux (§2.1, Eq. 6 with the
 quadrature of Eq. 5), Lagrange interpolation of solution and flux to the element faces
-(§3.3), a Lax-Friedrichs interface flux (§3.3), and the total-flux derivative with the
+(§3.3), a Lax-Friedrichs or HLL interface flux (§3.3; §5 setup tables), and the total-flux derivative with the
 Radau correction derivatives (§3.4, Eq. 21; multi-D tensor form §3.5, Eq. 24).
 
 State layout (shared with the library's ABI): uhat[e, j, k, s], e = element
@@ -47,6 +47,7 @@ class Problem:
     s0: float = 0.0
     kappa: float = 4.0
     limiter: bool = False
+    flux: str = "llf"  # interface flux: 'llf' | 'hll'
 
     @property
     def E(self):
@@ -160,6 +161,51 @@ def llf(prob, uL, uR, direction=0):
     return 0.5 * (flux(prob, uL, direction) + flux(prob, uR, direction)) - 0.5 * alpha[..., None] * (uR - uL)
 
 
+def signal_speeds(prob, uL, uR, direction=0):
+    """Wave-speed estimates of the HLL flux (Davis): S_L = min of the smallest characteristic
+    speed of the two states, S_R = max of the largest.  Characteristic speeds: a (advection),
+    u (Burgers), v_n -+ c (Euler)."""
+    if prob.equation == "advection":
+        lo_l = hi_l = prob.adv_speed * np.ones(uL.shape[:-1])
+        lo_r = hi_r = prob.adv_speed * np.ones(uR.shape[:-1])
+    elif prob.equation == "burgers":
+        lo_l = hi_l = uL[..., 0]
+        lo_r = hi_r = uR[..., 0]
+    else:
+        def speeds(u):
+            rho = u[..., 0]
+            c = np.sqrt(prob.gamma * pressure(u, prob.gamma, prob.dim) / rho)
+            vn = u[..., 1 + direction] / rho
+            return vn - c, vn + c
+        lo_l, hi_l = speeds(uL)
+        lo_r, hi_r = speeds(uR)
+    return np.minimum(lo_l, lo_r), np.maximum(hi_l, hi_r)
+
+
+def hll_from_speeds(fL, fR, uL, uR, SL, SR):
+    """HLL flux for given signal speeds: the flux of the single intermediate state that
+    conserves the Riemann fan between S_L and S_R; F_L when S_L >= 0, F_R when S_R <= 0,
+    else (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L)."""
+    SL = SL[..., None]
+    SR = SR[..., None]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mid = (SR * fL - SL * fR + SL * SR * (uR - uL)) / (SR - SL)
+    return np.where(SL >= 0.0, fL, np.where(SR <= 0.0, fR, mid))
+
+
+def hll(prob, uL, uR, direction=0):
+    """HLL interface flux at each z-node (the flux of the Euler setup tables, §5.3-5.4)."""
+    SL, SR = signal_speeds(prob, uL, uR, direction)
+    return hll_from_speeds(flux(prob, uL, direction), flux(prob, uR, direction), uL, uR, SL, SR)
+
+
+def interface_flux(prob, uL, uR, direction=0):
+    """The problem's interface flux: local Lax-Friedrichs or HLL, pointwise per z-node."""
+    if prob.flux == "hll":
+        return hll(prob, uL, uR, direction)
+    return llf(prob, uL, uR, direction)
+
+
 def ghost(prob, side, interior, direction):
     """Ghost (outside) state for a boundary face, modal in z: [..., M, S]."""
     kind = prob.bc[side]
@@ -210,7 +256,7 @@ def rhs_1d(prob, tabs, uhat):
         left[0] = ghost(prob, 0, uL[0], 0)
         left[E] = uR[E - 1]
         right[E] = ghost(prob, 1, uR[E - 1], 0)
-    fI_nodal = llf(prob, np.einsum("qk,fks->fqs", Vz, left), np.einsum("qk,fks->fqs", Vz, right))
+    fI_nodal = interface_flux(prob, np.einsum("qk,fks->fqs", Vz, left), np.einsum("qk,fks->fqs", Vz, right))
     fI = np.einsum("kq,fqs->fks", Pz, fI_nodal) / J
     fIL, fIR = fI[0:E], fI[1:E + 1]
     # a7: total flux derivative at r_j (Eq. 21), residual = -d f / dr (Eq. 12)
@@ -264,8 +310,8 @@ def _faces_along(prob, tabs, U, Fh, direction):
         left[0] = ghost(prob, sides[0], uL[0], direction)
         left[nel] = uR[nel - 1]
         right[nel] = ghost(prob, sides[1], uR[nel - 1], direction)
-    fI_nodal = llf(prob, np.einsum("qk,...ks->...qs", Vz, left),
-                   np.einsum("qk,...ks->...qs", Vz, right), direction)
+    fI_nodal = interface_flux(prob, np.einsum("qk,...ks->...qs", Vz, left),
+                              np.einsum("qk,...ks->...qs", Vz, right), direction)
     fI = np.einsum("kq,...qs->...ks", Pz, fI_nodal) / J
     fIL = np.moveaxis(fI[0:nel], 0, ax)
     fIR = np.moveaxis(fI[1:nel + 1], 0, ax)
