@@ -142,6 +142,18 @@ frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt);
  * use_graph = 1 replays the three stage launches from a captured CUDA graph. */
 frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph);
 
+/* Advance the context's state by nsteps steps of size dt of the classical four-stage
+ * Runge-Kutta scheme (the integrator of the advection study, §5.1 setup table):
+ * y1 = u + dt/2 L(u), y2 = u + dt/2 L(y1), y3 = u + dt L(y2),
+ * u <- u + dt/6 (L(u) + 2 L(y1) + 2 L(y2) + L(y3)).  Each stage limits its input (§4.3, if
+ * enabled) and runs the detector and filter on its output y_i and on the new state (§4.1-4.2,
+ * if enabled); the weighted sum of the residuals is not filtered.  The first call allocates
+ * one more state-sized device buffer, kept until fr_sg_destroy.  Decisions loaded by
+ * fr_sg_set_replay are consumed one row per stage (four per step); steps taken while rows
+ * remain run without the graph.  use_graph = 1 replays the four stage launches from a
+ * captured CUDA graph.  Asynchronous; device errors as fr_sg_rk_step. */
+frsg_status fr_sg_rk4_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph);
+
 /* Issue stage `stage` (0, 1, 2) of one SSP-RK3 step of size dt: stage 0 reads the state
  * and writes the first stage buffer, stage 1 reads it and writes the second, stage 2 reads
  * the second and writes the state.  Calling stages 0, 1, 2 in order is one

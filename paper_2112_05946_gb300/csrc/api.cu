@@ -40,8 +40,8 @@ struct frsg_ctx {
     double* d_dt = nullptr;       // step size read by the stage kernels (graphs do not depend on dt)
     unsigned* d_bar = nullptr;    // grid-barrier words of the one-launch step (count, generation)
     double dt_set = -1.0;         // value last written to d_dt
-    uint8_t* d_flags = nullptr;   // [3][E]
-    double* d_beta = nullptr;     // [3][E]
+    uint8_t* d_flags = nullptr;   // [4][E] (rows 0..2 SSP-RK3 stages, row 3 the last RK4 stage)
+    double* d_beta = nullptr;     // [4][E]
     unsigned* d_err = nullptr;
     unsigned long long* d_speed = nullptr;
     uint8_t* d_replay = nullptr;
@@ -51,6 +51,8 @@ struct frsg_ctx {
     int TE = 1, TE_lim = 1;
     int wide = 0;                 // 1D stage kernel layout: 1 = thread per (z-node, point)
     cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphExec_t graph_rk4 = nullptr;
+    void* d_u3 = nullptr;         // RK4 weighted sum of the stage residuals (allocated on first use)
     // recorded run for the adjoint: checkpoints every rec_k steps, filter decisions per stage
     int rec_nsteps = 0, rec_k = 0, rec_cap_ckpt = 0, rec_cap_steps = 0, rec_cap_seg = 0;
     double rec_dt = 0.0;
@@ -391,6 +393,57 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
     return cudaSuccess;
 }
 
+// Cached step graphs depend on the tile and layout; drop them when either changes.
+void drop_graphs(frsg_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph_rk4) cudaGraphExecDestroy(c->graph_rk4);
+    c->graph_exec = nullptr;
+    c->graph_rk4 = nullptr;
+}
+
+// Stage s of a classical RK4 step (§5.1 setup table).  Buffers: u = u^n (limited in
+// place by stage 0), y1 -> u1, y2 -> u2, y3 -> u1, running sum of the residuals -> u3:
+//   s = 0: y1 = u + dt/2 L(u),   acc = u + dt/6 L(u)
+//   s = 1: y2 = u + dt/2 L(y1),  acc += dt/3 L(y1)
+//   s = 2: y3 = u + dt L(y2),    acc += dt/3 L(y2)
+//   s = 3: u^{n+1} = acc + dt/6 L(y3)   (written over u^n)
+// Each stage limits its input and filters its output like an SSP-RK3 stage; replayed
+// filter decisions, if loaded, are consumed one row per stage.
+cudaError_t issue_rk4_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
+    const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
+    void* bin[4] = {c->d_u, c->d_u1, c->d_u2, c->d_u1};
+    void* bout[4] = {c->d_u1, c->d_u2, c->d_u1, c->d_u};
+    const double cy[4] = {0.5, 0.5, 1.0, 1.0 / 6.0};
+    if (c->cfg.limiter) {
+        cudaError_t e = launch_limiter(c, bin[s], c->d_beta + (size_t)s * c->E);
+        if (e != cudaSuccess) return e;
+    }
+    StageArgs A = base_args(c);
+    A.uin = bin[s];
+    A.uout = bout[s];
+    A.ubase = s == 3 ? c->d_u3 : c->d_u;
+    A.a = s == 0 ? 0.0 : 1.0;
+    A.b = s == 0 ? 1.0 : 0.0;
+    A.c = cy[s];
+    A.dtp = c->d_dt;
+    A.dt_filter = dt;
+    A.do_filter = filt ? 1 : 0;
+    A.flags = c->d_flags + (size_t)s * c->E;
+    A.replay = nullptr;
+    if (use_replay && c->replay_pos < c->replay_rows) {
+        A.replay = c->d_replay + (size_t)c->replay_pos * c->E;
+        c->replay_pos += 1;
+    }
+    if (s < 3) {
+        A.acc_out = c->d_u3;
+        A.acc_in = s == 0 ? nullptr : c->d_u3;
+        A.acc_a = s == 0 ? 0.0 : 1.0;
+        A.acc_b = s == 0 ? 1.0 : 0.0;
+        A.acc_c = s == 0 ? 1.0 / 6.0 : 1.0 / 3.0;
+    }
+    return launch_stage(c, A);
+}
+
 bool tile_fits_1d(const frsg_ctx* c, int te, int wide) {
     const int thr = te * c->Q * (wide ? c->Np : 1);
     const size_t sm = wide ? frsg::stage1d_wide_smem_bytes(c->fp64, te, c->Np, c->M, c->Q, c->S)
@@ -475,17 +528,17 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     if ((e = cudaMalloc(&ctx->d_dt, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "dt");
     if ((e = cudaMalloc(&ctx->d_bar, 2 * sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "barrier");
     if ((e = cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "barrier");
-    if ((e = cudaMalloc(&ctx->d_flags, 3 * (size_t)ctx->E)) != cudaSuccess) return cleanup_fail(e, "flags");
-    if ((e = cudaMalloc(&ctx->d_beta, 3 * sizeof(double) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "beta");
+    if ((e = cudaMalloc(&ctx->d_flags, 4 * (size_t)ctx->E)) != cudaSuccess) return cleanup_fail(e, "flags");
+    if ((e = cudaMalloc(&ctx->d_beta, 4 * sizeof(double) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "beta");
     if ((e = cudaMalloc(&ctx->d_err, sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "err");
     if ((e = cudaMalloc(&ctx->d_speed, sizeof(unsigned long long))) != cudaSuccess) return cleanup_fail(e, "speed");
     e = cudaMemcpyAsync(ctx->d_tab, ctx->htab.data(), sizeof(double) * ctx->off.total, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_ghost, 0, sizeof(double) * 4 * ctx->M * ctx->S, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_u, 0, ctx->esz * nstate, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flags, 0, 3 * (size_t)ctx->E, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flags, 0, 4 * (size_t)ctx->E, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream);
     if (e == cudaSuccess) {
-        std::vector<double> ones(3 * (size_t)ctx->E, 1.0);
+        std::vector<double> ones(4 * (size_t)ctx->E, 1.0);
         e = cudaMemcpyAsync(ctx->d_beta, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     }
@@ -509,6 +562,8 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
 void fr_sg_destroy(frsg_ctx* ctx) {
     if (!ctx) return;
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph_rk4) cudaGraphExecDestroy(ctx->graph_rk4);
+    cudaFree(ctx->d_u3);
     cudaFree(ctx->d_tab);
     cudaFree(ctx->d_tabf);
     cudaFree(ctx->d_ghost);
@@ -722,6 +777,56 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     return FRSG_OK;
 }
 
+frsg_status fr_sg_rk4_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
+    if (nsteps == 0) return FRSG_OK;
+    if (!ctx->d_u3) {
+        const size_t nstate = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+        CK(cudaMalloc(&ctx->d_u3, ctx->esz * nstate));
+    }
+    CK(set_dt(ctx, dt));
+    const int kernels_per_step = 4 * (ctx->cfg.limiter ? 2 : 1);
+    for (int n = 0; n < nsteps; ++n) {
+        const bool replaying = ctx->replay_pos < ctx->replay_rows;
+        if (use_graph && !replaying) {
+            if (!ctx->graph_rk4) {
+                cudaStream_t cap = ctx->stream;
+                bool own = false;
+                if (cap == nullptr) {
+                    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+                    own = true;
+                }
+                cudaStream_t saved = ctx->stream;
+                ctx->stream = cap;
+                const uint64_t before = ctx->launches;
+                cudaGraph_t graph = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e1 = cudaSuccess;
+                    for (int s = 0; s < 4 && e1 == cudaSuccess; ++s) e1 = issue_rk4_stage(ctx, s, dt, false);
+                    e = cudaStreamEndCapture(cap, &graph);
+                    if (e1 != cudaSuccess) e = e1;
+                }
+                ctx->launches = before;
+                ctx->stream = saved;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_rk4, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (own) {
+                    cudaStreamSynchronize(cap);
+                    cudaStreamDestroy(cap);
+                }
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+            }
+            CK(cudaGraphLaunch(ctx->graph_rk4, ctx->stream));
+            ctx->launches += kernels_per_step;
+        } else {
+            for (int s = 0; s < 4; ++s) CK(issue_rk4_stage(ctx, s, dt, true));
+        }
+    }
+    return FRSG_OK;
+}
+
 frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt) {
     if (!ctx) return FRSG_E_INVAL;
     if (stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt))
@@ -865,10 +970,7 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
         if (it != g_tune_cache.end()) {
             ctx->wide = it->second.first;
             ctx->TE = it->second.second;
-            if (ctx->graph_exec) {
-                cudaGraphExecDestroy(ctx->graph_exec);
-                ctx->graph_exec = nullptr;
-            }
+            drop_graphs(ctx);
             if (variant_out) *variant_out = ctx->wide;
             if (te_out) *te_out = ctx->TE;
             return FRSG_OK;
@@ -923,10 +1025,7 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
     ctx->wide = best_w;
     ctx->TE = best_te;
-    if (ctx->graph_exec) {
-        cudaGraphExecDestroy(ctx->graph_exec);
-        ctx->graph_exec = nullptr;
-    }
+    drop_graphs(ctx);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = {best_w, best_te};
@@ -942,10 +1041,7 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
     if (ctx->cfg.dim != 1) return variant == 0 ? FRSG_OK : fail(ctx, FRSG_E_UNSUPPORTED, "2D has one layout");
     if (variant == 2 && ctx->cfg.limiter)
         return fail(ctx, FRSG_E_UNSUPPORTED, "the one-launch step does not run the limiter");
-    if (ctx->graph_exec) {
-        cudaGraphExecDestroy(ctx->graph_exec);
-        ctx->graph_exec = nullptr;
-    }
+    drop_graphs(ctx);
     ctx->wide = variant;
     ctx->TE = choose_tile_1d(ctx);
     return FRSG_OK;
@@ -1256,10 +1352,7 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out) {
             frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) > 220 * 1024)
             return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
     }
-    if (want != ctx->TE && ctx->graph_exec) {
-        cudaGraphExecDestroy(ctx->graph_exec);
-        ctx->graph_exec = nullptr;
-    }
+    if (want != ctx->TE) drop_graphs(ctx);
     ctx->TE = want;
     if (te_out) *te_out = ctx->TE;
     return FRSG_OK;

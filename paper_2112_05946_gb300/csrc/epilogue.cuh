@@ -43,12 +43,34 @@ __device__ inline void load_filter_strengths(const StageArgs& A, int NP, T* sLam
     }
 }
 
+// Second output of a stage, element-offset global pointers (see StageArgs::acc_out).
+template <typename T>
+struct AccTerm {
+    T* dst;
+    const T* src;
+    T a, b, c;
+};
+
+template <typename T>
+__device__ inline AccTerm<T> acc_term(const StageArgs& A, size_t off, double dt) {
+    AccTerm<T> r{nullptr, nullptr, T(0), T(0), T(0)};
+    if (A.acc_out) {
+        r.dst = static_cast<T*>(A.acc_out) + off;
+        r.src = A.acc_in ? static_cast<const T*>(A.acc_in) + off : nullptr;
+        r.a = (T)A.acc_a;
+        r.b = (T)A.acc_b;
+        r.c = (T)(A.dtp ? A.acc_c * dt : A.acc_c);
+    }
+    return r;
+}
+
 // a4 + a8 for one element: uhat_new[j][k][s] = cb*U + cc*sum_q Pz[k][q] G[j][s][q] + ca*B.
 // G is the element's nodal residual [NP][S][Q]; U, B its stage input and SSP base [NP][M][S].
-// Writes the result to dst (shared memory or global).
-template <typename T, int NP, int S>
-__device__ inline bool project_combine(const T* G, const T* U, const T* B, const T* sPz, T* dst, int M, int Q, int kl,
-                                       int nk, int ml, int nm, T ca, T cb, T cc, bool use_base) {
+// Writes the result to dst (shared memory or global), and the accumulator X if ACC.
+template <typename T, int NP, int S, bool ACC>
+__device__ inline bool project_combine_impl(const T* G, const T* U, const T* B, const T* sPz, T* dst, int M, int Q,
+                                            int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
+                                            const AccTerm<T>& X) {
     bool bad = false;
     for (int k = kl; k < M; k += nk) {
         for (int j = ml; j < NP; j += nm) {
@@ -64,14 +86,29 @@ __device__ inline bool project_combine(const T* G, const T* U, const T* B, const
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 const int o = (j * M + k) * S + s;
-                T val = cb * U[o] + cc * acc[s];
+                const T uo = U[o];          // dst may alias U (in-place tile update)
+                T val = cb * uo + cc * acc[s];
                 if (use_base) val += ca * B[o];
                 dst[o] = val;
                 bad |= !finite_val(val);
+                if constexpr (ACC) {
+                    T w = X.b * uo + X.c * acc[s];
+                    if (X.src) w += X.a * X.src[o];
+                    X.dst[o] = w;
+                }
             }
         }
     }
     return bad;
+}
+
+template <typename T, int NP, int S>
+__device__ inline bool project_combine(const T* G, const T* U, const T* B, const T* sPz, T* dst, int M, int Q, int kl,
+                                       int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
+                                       const AccTerm<T>& X) {
+    if (X.dst)
+        return project_combine_impl<T, NP, S, true>(G, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base, X);
+    return project_combine_impl<T, NP, S, false>(G, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base, X);
 }
 
 // a9 + a10 for the tile.  Us: the tile's new coefficients [ne][NP][M][S] in shared memory;

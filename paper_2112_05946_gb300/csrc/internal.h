@@ -65,6 +65,11 @@ struct StageArgs {
     unsigned* err;
     int TE;                // elements per block
     int wide;              // 1D: one thread per (z-node, point) instead of per z-node
+    // optional second output of the same residual (the RK4 weighted sum of the L's):
+    // acc_out = acc_a*acc_in + acc_b*uin + acc_c*dt*L(uin), unfiltered; null = none
+    void* acc_out;
+    const void* acc_in;
+    double acc_a, acc_b, acc_c;
 };
 
 struct LimitArgs {

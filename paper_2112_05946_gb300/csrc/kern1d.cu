@@ -228,7 +228,8 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
         bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
-                                         Q, 0, 1, ca, cb, cc, A.a != 0.0);
+                                         Q, 0, 1, ca, cb, cc, A.a != 0.0,
+                                         acc_term<T>(A, gbase + (size_t)te * elsz, dt));
     }
     if (A.do_filter) {
         __syncthreads();
@@ -425,7 +426,8 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
         bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
-                                         Q, tj, NP, ca, cb, cc, A.a != 0.0);
+                                         Q, tj, NP, ca, cb, cc, A.a != 0.0,
+                                         acc_term<T>(A, gbase + (size_t)te * elsz, dt));
     }
     if (A.do_filter) {
         __syncthreads();
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
 }
 
 template <typename T, int NP, int S, int EQ>
-__global__ void __launch_bounds__(512) stage1d_kernel(const StageArgs A) {
+__global__ void __launch_bounds__(512, 1) stage1d_kernel(const StageArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int e0 = blockIdx.x * A.TE;
     const int tq = threadIdx.x, te = threadIdx.y;

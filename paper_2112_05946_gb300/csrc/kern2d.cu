@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
         bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
-                                         Q, tl, N1, ca, cb, cc, A.a != 0.0);
+                                         Q, tl, N1, ca, cb, cc, A.a != 0.0,
+                                         acc_term<T>(A, gbase + (size_t)te * elsz, dt));
     }
     if (A.do_filter) {
         __syncthreads();

@@ -68,6 +68,7 @@ _SIGNATURES = [
     ("fr_sg_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_rk_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_rk4_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_stage", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     ("fr_sg_filter", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     ("fr_sg_limit", ctypes.c_int, [ctypes.c_void_p]),
@@ -254,6 +255,10 @@ class Solver:
 
     def rk_step(self, dt, nsteps=1, graph=True):
         self._ck(self.lib.fr_sg_rk_step(self.h, float(dt), int(nsteps), int(bool(graph))), "rk_step")
+
+    def rk4_step(self, dt, nsteps=1, graph=True):
+        """Classical RK4 steps (the advection study's integrator)."""
+        self._ck(self.lib.fr_sg_rk4_step(self.h, float(dt), int(nsteps), int(bool(graph))), "rk4_step")
 
     def stage(self, stage, dt):
         self._ck(self.lib.fr_sg_stage(self.h, int(stage), float(dt)), "stage")

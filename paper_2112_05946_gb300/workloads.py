@@ -71,6 +71,35 @@ def sod_1d(nx=4096, P=3, N=6, Q=12):
     )
 
 
+def sod_location_1d(nx=100, P=2, N=9, Q=17, sigma=0.05, filter="lasso"):
+    """Sod tube with a stochastic discontinuity location (§5.3, second case, setup table of
+    §5.3): rho/u/p = (1, 0, 1) left of x_c = 0.5 + sigma z and (0.125, 0, 0.1) right of it,
+    sigma = 0.05; x in [0, 1], 100 elements, N_p = 3 (P = 2), N_c = 9, N_q = 17, HLL flux,
+    Dirichlet ends, CFL 0.1, t_end = 0.15; the Lasso filter on every element (or the L2 filter,
+    eps1 = 0.6, eps2 = 0.6, behind the detector with s0 = -3 log10(N_p - 1), kappa = 4) and
+    the positivity limiter.  SSP-RK3 replaces the paper's Bogacki-Shampine integrator."""
+    left = np.array([1.0, 0.0, 1.0 / (GAMMA - 1.0)])
+    right = np.array([0.125, 0.0, 0.1 / (GAMMA - 1.0)])
+
+    def ic(x, z):
+        return np.where((x < 0.5 + sigma * z)[..., None], left, right)
+
+    solver = dict(dim=1, nx=nx, x0=0.0, x1=1.0, bc=("dirichlet", "dirichlet", "periodic", "periodic"),
+                  P=P, N=N, Q=Q, equation="euler", gamma=GAMMA, flux="hll", limiter=True,
+                  s0=-3.0 * math.log10(P), kappa=4.0)
+    if filter == "lasso":
+        solver.update(filter="lasso", sensor=False)
+    else:
+        solver.update(filter="l2", sensor=True, f_eps1=0.6, f_eps2=0.6)
+    return dict(
+        name=f"sod_location_E{nx}_P{P}_N{N}_Q{Q}_{filter}",
+        solver=solver,
+        ic=ic,
+        boundary={0: lambda z: left.copy(), 1: lambda z: right.copy()},
+        cfl=0.1, t_end=0.15, lam0=None,
+    )
+
+
 def _rh_downstream(ma, rho1=1.0, p1=1.0):
     """Normal-shock jump for upstream Mach number ma (stationary shock, ideal gas)."""
     g = GAMMA
