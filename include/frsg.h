@@ -52,7 +52,7 @@ typedef enum {
 
 enum { FRSG_BC_PERIODIC = 0, FRSG_BC_DIRICHLET = 1, FRSG_BC_OUTFLOW = 2, FRSG_BC_REFLECT = 3 };
 enum { FRSG_EQ_ADVECTION = 0, FRSG_EQ_BURGERS = 1, FRSG_EQ_EULER = 2 };
-enum { FRSG_FILTER_NONE = 0, FRSG_FILTER_EXP = 1, FRSG_FILTER_L2 = 2 };
+enum { FRSG_FILTER_NONE = 0, FRSG_FILTER_EXP = 1, FRSG_FILTER_L2 = 2, FRSG_FILTER_LASSO = 3 };
 enum { FRSG_FP64 = 0, FRSG_FP32 = 1 };
 enum { FRSG_HOST = 0, FRSG_DEVICE = 1 };
 
@@ -69,7 +69,9 @@ typedef struct {
     int32_t equation;         /* FRSG_EQ_* */
     double adv_speed;         /* advection speed a (FRSG_EQ_ADVECTION) */
     double gamma;             /* ratio of specific heats (FRSG_EQ_EULER) */
-    int32_t filter;           /* FRSG_FILTER_*: exponential (§4.1.1) or L2 (§4.1.2) */
+    int32_t filter;           /* FRSG_FILTER_*: exponential (§4.1.1), L2 (§4.1.2) or Lasso (§4.1.3,
+                                 1D only: soft threshold with strengths picked per element and
+                                 variable so that the top physical and random modes vanish) */
     int32_t sensor;           /* 1: filter only elements with theta < 0.99 (§4.2); 0: every element */
     double f_alpha, f_s;      /* exponential filter strength alpha and order s (N_* = 0) */
     double f_eps1, f_eps2;    /* L2 filter damping of the last physical / random mode (§4.1.2, Eq. 39) */

@@ -101,7 +101,8 @@ std::string validate(const frsg_config& c) {
     if (c.dim == 2 && c.bc[2] == FRSG_BC_PERIODIC && c.ny < 2) return "periodic y needs ny >= 2";
     if (!(c.x1 > c.x0) || (c.dim == 2 && !(c.y1 > c.y0))) return "empty domain";
     if (c.equation < FRSG_EQ_ADVECTION || c.equation > FRSG_EQ_EULER) return "unknown equation";
-    if (c.filter < FRSG_FILTER_NONE || c.filter > FRSG_FILTER_L2) return "unknown filter";
+    if (c.filter < FRSG_FILTER_NONE || c.filter > FRSG_FILTER_LASSO) return "unknown filter";
+    if (c.filter == FRSG_FILTER_LASSO && c.dim != 1) return "the Lasso filter is implemented for 1D elements";
     if (c.precision != FRSG_FP64 && c.precision != FRSG_FP32) return "unknown precision";
     if (c.limiter && c.equation != FRSG_EQ_EULER) return "the positivity limiter is defined for Euler only";
     if (c.dim == 2 && c.equation != FRSG_EQ_EULER) return "2D supports the Euler equations only";
@@ -204,6 +205,8 @@ void build_table_block(TableCtx* c, const frsg::HostTables& t, std::vector<doubl
                     if (cf.dim == 2) val += std::pow((double)mb / P, cf.f_s);
                 }
                 if (N > 0) val += std::pow((double)k / N, cf.f_s);
+            } else if (cf.filter == FRSG_FILTER_LASSO) {
+                val = t.l1x[ma] * t.l1z[k];              // ||Psi_m Phi_k||_1 (1D only)
             } else if (cf.filter == FRSG_FILTER_L2) {
                 const double np1 = n1;
                 const double a1 = n1 > 1 ? 1.0 / (cf.f_eps1 * np1 * np1 * (np1 - 1) * (np1 - 1)) : 0.0;
@@ -222,6 +225,12 @@ void build_table_block(TableCtx* c, const frsg::HostTables& t, std::vector<doubl
     c->off.Vfinv = put(Vfi);
     c->off.top = put(top);
     c->off.lam = put(lam);
+    std::vector<double> lc(2, 0.0);
+    if (cf.filter == FRSG_FILTER_LASSO) {
+        lc[0] = 1.0 / (P * (P + 1.0) * t.l1x[P] * t.l1z[0]);
+        lc[1] = N > 0 ? 1.0 / (N * (N + 1.0) * t.l1x[0] * t.l1z[N]) : 0.0;
+    }
+    c->off.lc = put(lc);
     c->off.total = (int)v.size();
 }
 
@@ -1049,9 +1058,11 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
 
 static frsg_status adjoint_supported(frsg_ctx* ctx) {
     const frsg_config& c = ctx->cfg;
-    if (c.dim != 1 || !ctx->fp64 || c.equation == FRSG_EQ_EULER || c.limiter || c.bc[0] != FRSG_BC_PERIODIC)
+    if (c.dim != 1 || !ctx->fp64 || c.equation == FRSG_EQ_EULER || c.limiter || c.bc[0] != FRSG_BC_PERIODIC ||
+        c.filter == FRSG_FILTER_LASSO)
         return fail(ctx, FRSG_E_UNSUPPORTED,
-                    "the adjoint covers 1D periodic advection/Burgers contexts in FRSG_FP64 without limiter");
+                    "the adjoint covers 1D periodic advection/Burgers contexts in FRSG_FP64 without limiter "
+                    "and with a linear (exponential or L2) filter");
     return FRSG_OK;
 }
 

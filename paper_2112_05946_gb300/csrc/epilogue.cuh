@@ -11,8 +11,8 @@
 // first variable (orthonormal bases: inner products are plain sums) and flags elements with
 // theta < 0.99 (§4.2, Eq. 47).  theta falls monotonically with S_e = top/total energy, so
 // the test is S_e > 10^(s0 - (2 kappa/pi) asin 0.98), with no logarithm or sine per element.
-// Flagged elements get Vf (Lambda o modal) (§4.1, Eq. 34).  Everything runs in the state's
-// precision T.
+// Flagged elements get Vf (Lambda o modal) (§4.1, Eq. 34), or Vf (soft-thresholded modal)
+// for the Lasso filter (§4.1.3).  Everything runs in the state's precision T.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -111,6 +111,27 @@ __device__ inline bool project_combine(const T* G, const T* U, const T* B, const
     return project_combine_impl<T, NP, S, false>(G, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base, X);
 }
 
+// One Lasso-filtered nodal coefficient (§4.1.3) of a 1D element from its modal coefficients
+// me [NP][M][S]: Vf applied to the soft threshold sign(u) max(|u| - t, 0) (which equals
+// ReLU(1 - t/|u|) u) with t = (a1 m(m+1) + a2 k(k+1)) ||Psi_m Phi_k||_1 and
+// a1 = |u_{P,0}| c1, a2 = |u_{0,N}| c2.  Kept out of line so that the other filters' register
+// allocation does not carry it.
+template <typename T, int NP, int S>
+__device__ __noinline__ T lasso_value(const T* me, const T* sVf, const T* sNorm, int j, int k, int s, int M, T c1,
+                                      T c2) {
+    const T a1 = fabs(me[((NP - 1) * M) * S + s]) * c1;
+    const T a2 = fabs(me[(M - 1) * S + s]) * c2;
+    const T kk = T(k * (k + 1));
+    T val = T(0);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const T um = me[(m * M + k) * S + s];
+        const T t = (a1 * T(m * (m + 1)) + a2 * kk) * sNorm[m * M + k];
+        val += sVf[j * NP + m] * copysign(fmax(fabs(um) - t, T(0)), um);
+    }
+    return val;
+}
+
 // a9 + a10 for the tile.  Us: the tile's new coefficients [ne][NP][M][S] in shared memory;
 // Mod: scratch of the same size; te: this thread's element; active: te < ne.
 template <typename T, int NP, int S>
@@ -183,13 +204,21 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
     bool bad = false;
     if (active) {
         const bool flag = sFlag[te] != 0;
+        const bool lasso = A.filter == FRSG_FILTER_LASSO;   // 1D: NP = P + 1
+        T c1 = T(0), c2 = T(0);
+        if (lasso) {
+            c1 = table_block<T>(A)[A.off.lc];
+            c2 = table_block<T>(A)[A.off.lc + 1];
+        }
         T* dst = uout + gbase + (size_t)te * elsz;
         for (int k = kl; k < M; k += nk) {
             for (int j = ml; j < NP; j += nm) {
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     T val;
-                    if (flag) {
+                    if (flag && lasso) {
+                        val = lasso_value<T, NP, S>(me, sVf, sLam, j, k, s, M, c1, c2);
+                    } else if (flag) {
                         val = T(0);
 #pragma unroll
                         for (int m = 0; m < NP; ++m) val += sVf[j * NP + m] * sLam[m * M + k] * me[(m * M + k) * S + s];

@@ -29,6 +29,7 @@ struct HostTables {
     std::vector<double> z, wz;       // Q nodes, probability weights (sum 1)
     std::vector<double> VzT;         // M*Q, VzT[k*Q+q] = Phi_k(z_q)
     std::vector<double> Pz;          // M*Q, Pz[k*Q+q] = wz_q Phi_k(z_q)
+    std::vector<double> l1x, l1z;    // n1 / M: L1 norms of the orthonormal Legendre functions
 };
 void build_tables(int P, int N, int Q, HostTables* t);
 
@@ -37,7 +38,9 @@ struct TabOff {
     int D, lm, lp, dhL, dhR, Vx, Vxinv, VzT, Pz, w, Lpts, total;
     int Vf, Vfinv;   // Np x Np element Vandermonde (tensor product in 2D) and its inverse
     int top;         // Np: 1 where the physical mode has degree P in some direction
-    int lam;         // Np x M: exponential filter exponent sum eta^s, or the L2 factor
+    int lam;         // Np x M: exponential filter exponent sum eta^s, the L2 factor, or the
+                     // Lasso norm ||Psi_m Phi_k||_1
+    int lc;          // 2: Lasso strength constants 1/(P(P+1)||Psi_P Phi_0||_1), 1/(N(N+1)||Psi_0 Phi_N||_1)
     int NL;   // rows of Lpts: solution points then face flux points (limiter, §4.3)
 };
 

@@ -206,6 +206,10 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
         std::fprintf(stderr, "fr_sg_rk_step_noalloc: only 1D problems in FRSG_FP64\n");
         return FRSG_E_UNSUPPORTED;
     }
+    if (cfg->filter == FRSG_FILTER_LASSO) {
+        std::fprintf(stderr, "fr_sg_rk_step_noalloc: the exponential and L2 filters only\n");
+        return FRSG_E_UNSUPPORTED;
+    }
     const int n1 = cfg->P + 1, M = cfg->N + 1, Q = cfg->Q, E = cfg->nx;
     const int S = cfg->equation == FRSG_EQ_EULER ? 3 : 1;
     const size_t nstate = (size_t)E * n1 * M * S;

@@ -1,7 +1,8 @@
 // Host construction of the FR-SG tables: Gauss-Legendre points, Lagrange derivative
 // matrix, face interpolation, Radau correction derivatives (§3.2-3.4), orthonormal
-// Legendre gPC evaluation / projection matrices (§2.1, Eqs. 2-6) and the physical-space
-// Vandermonde matrix with its inverse (§4, Eq. 28).
+// Legendre gPC evaluation / projection matrices (§2.1, Eqs. 2-6), the physical-space
+// Vandermonde matrix with its inverse (§4, Eq. 28) and the L1 norms of the orthonormal
+// Legendre functions (Lasso filter, §4.1.3).
 #include <cmath>
 #include <stdexcept>
 
@@ -53,6 +54,28 @@ void gauss_legendre(int n, std::vector<double>* x, std::vector<double>* w) {
         (*x)[n - 1 - i] = xi;
         (*w)[n - 1 - i] = 2.0 / ((1.0 - xi * xi) * dp * dp);
     }
+}
+
+// ||psi_m||_1 under the uniform probability density, psi_m = sqrt(2m+1) P_m.  P_m keeps one
+// sign between consecutive roots (the m-point Gauss nodes), and (P_{m+1} - P_{m-1})/(2m+1)
+// is an antiderivative of P_m, so the integral of |P_m| is a sum of antiderivative jumps.
+double legendre_l1(int m) {
+    if (m == 0) return 1.0;
+    std::vector<double> roots, unused;
+    gauss_legendre(m, &roots, &unused);
+    auto anti = [m](double x) {
+        double a, b, da, db;
+        legendre(m + 1, x, &a, &da);
+        legendre(m - 1, x, &b, &db);
+        return (a - b) / (2.0 * m + 1.0);
+    };
+    double total = 0.0, prev = -1.0;
+    for (int i = 0; i <= m; ++i) {
+        const double next = i < m ? roots[i] : 1.0;
+        total += std::fabs(anti(next) - anti(prev));
+        prev = next;
+    }
+    return 0.5 * std::sqrt(2.0 * m + 1.0) * total;
 }
 
 }  // namespace
@@ -127,6 +150,11 @@ void build_tables(int P, int N, int Q, HostTables* t) {
             t->VzT[k * Q + q] = phi;
             t->Pz[k * Q + q] = t->wz[q] * phi;   // <Phi_k^2> = 1
         }
+    // L1 norms of the orthonormal bases (Lasso filter, §4.1.3)
+    t->l1x.assign(n1, 0.0);
+    t->l1z.assign(M, 0.0);
+    for (int m = 0; m < n1; ++m) t->l1x[m] = legendre_l1(m);
+    for (int k = 0; k < M; ++k) t->l1z[k] = legendre_l1(k);
 }
 
 }  // namespace frsg

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfrsg.so")
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_POSITIVITY, E_TIMEOUT, E_UNSUPPORTED = range(8)
 BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 EQUATION = {"advection": 0, "burgers": 1, "euler": 2}
-FILTER = {"none": 0, "exp": 1, "l2": 2}
+FILTER = {"none": 0, "exp": 1, "l2": 2, "lasso": 3}
 PRECISION = {"fp64": 0, "fp32": 1}
 HOST, DEVICE = 0, 1
 
