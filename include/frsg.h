@@ -53,6 +53,9 @@ typedef enum {
 enum { FRSG_BC_PERIODIC = 0, FRSG_BC_DIRICHLET = 1, FRSG_BC_OUTFLOW = 2, FRSG_BC_REFLECT = 3 };
 enum { FRSG_EQ_ADVECTION = 0, FRSG_EQ_BURGERS = 1, FRSG_EQ_EULER = 2 };
 enum { FRSG_FILTER_NONE = 0, FRSG_FILTER_EXP = 1, FRSG_FILTER_L2 = 2, FRSG_FILTER_LASSO = 3 };
+/* Interface flux: local Lax-Friedrichs, or HLL with the Davis signal speeds
+ * S_L = min(lambda_min(u_L), lambda_min(u_R)), S_R = max(lambda_max(u_L), lambda_max(u_R)). */
+enum { FRSG_FLUX_LLF = 0, FRSG_FLUX_HLL = 1 };
 enum { FRSG_FP64 = 0, FRSG_FP32 = 1 };
 enum { FRSG_HOST = 0, FRSG_DEVICE = 1 };
 
@@ -78,6 +81,8 @@ typedef struct {
     double s0, kappa;         /* detector parameters (§4.2, Eq. 47), log10 scale */
     int32_t limiter;          /* 1: positivity-preserving limiter on every stage input (§4.3) */
     int32_t precision;        /* FRSG_FP64 or FRSG_FP32 */
+    int32_t flux;             /* FRSG_FLUX_LLF (§3.3) or FRSG_FLUX_HLL (Euler setup tables of §5.3-5.4),
+                                 evaluated pointwise at every z-node of every face */
 } frsg_config;
 
 /* Create a context: validates the configuration, builds the tables of §2.1 and §3 on
@@ -130,7 +135,7 @@ frsg_status fr_sg_get_state(frsg_ctx* ctx, double* uhat, int where);
 
 /* Semi-discrete residual dudt = L(u) of the FR-SG system, no limiter and no filter:
  * z-evaluation (§2.1, Eq. 2), flux (§3.2, Eq. 15), Galerkin projection (Eq. 6), face
- * interpolation and local Lax-Friedrichs interface flux (§3.3), total-flux derivative
+ * interpolation and the interface flux (LLF or HLL, §3.3), total-flux derivative
  * with the Radau correction (§3.4, Eq. 21; 2D §3.5, Eq. 24).  u and dudt: DEVICE arrays
  * [E][Np][M][S] in the context's precision; they must not overlap.  Boundary ghost
  * states come from the context. */

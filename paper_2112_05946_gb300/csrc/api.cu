@@ -110,6 +110,7 @@ std::string validate(const frsg_config& c) {
         if (c.bc[i] < FRSG_BC_PERIODIC || c.bc[i] > FRSG_BC_REFLECT) return "unknown boundary kind";
     if (!periodic_pair_ok(c)) return "periodic boundaries must come in pairs";
     if (c.equation == FRSG_EQ_EULER && !(c.gamma > 1.0)) return "gamma must exceed 1";
+    if (c.flux != FRSG_FLUX_LLF && c.flux != FRSG_FLUX_HLL) return "unknown interface flux";
     if (c.filter == FRSG_FILTER_L2 && (!(c.f_eps1 > 0) || !(c.f_eps2 > 0))) return "L2 filter needs eps1, eps2 > 0";
     if (c.filter != FRSG_FILTER_NONE && c.sensor && !(c.kappa > 0)) return "detector needs kappa > 0";
     return "";
@@ -257,6 +258,7 @@ StageArgs base_args(frsg_ctx* c) {
     A.adv = c->cfg.adv_speed;
     A.gamma = c->cfg.gamma;
     A.filter = c->cfg.filter;
+    A.flux = c->cfg.flux;
     A.sensor = c->cfg.sensor;
     A.f_alpha = c->cfg.f_alpha;
     A.f_s = c->cfg.f_s;
@@ -1059,10 +1061,10 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
 static frsg_status adjoint_supported(frsg_ctx* ctx) {
     const frsg_config& c = ctx->cfg;
     if (c.dim != 1 || !ctx->fp64 || c.equation == FRSG_EQ_EULER || c.limiter || c.bc[0] != FRSG_BC_PERIODIC ||
-        c.filter == FRSG_FILTER_LASSO)
+        c.filter == FRSG_FILTER_LASSO || c.flux != FRSG_FLUX_LLF)
         return fail(ctx, FRSG_E_UNSUPPORTED,
-                    "the adjoint covers 1D periodic advection/Burgers contexts in FRSG_FP64 without limiter "
-                    "and with a linear (exponential or L2) filter");
+                    "the adjoint covers 1D periodic advection/Burgers contexts in FRSG_FP64 without limiter, "
+                    "with the LLF flux and a linear (exponential or L2) filter");
     return FRSG_OK;
 }
 

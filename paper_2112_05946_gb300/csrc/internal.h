@@ -61,6 +61,7 @@ struct StageArgs {
     int bc[4];
     double adv, gamma;
     int do_filter, filter, sensor;
+    int flux;              // FRSG_FLUX_LLF or FRSG_FLUX_HLL
     double f_alpha, f_s, f_eps1, f_eps2, s0, kappa;
     double det_ratio;      // theta < 0.99  <=>  S_e > det_ratio (theta decreases with S_e)
     const uint8_t* replay; // [E] filter decisions to use instead of the detector, or null

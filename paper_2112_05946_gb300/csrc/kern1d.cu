@@ -204,8 +204,8 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
             nL[s] = sTr[(te * 2 + 1) * S * Q + s * Q + tq];
             nR[s] = sTr[((te + 2) * 2 + 0) * S * Q + s * Q + tq];
         }
-        llf<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma);
-        llf<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma);
+        face_flux<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma, A.flux);
+        face_flux<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma, A.flux);
         const T invJ = (T)A.invJx;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
@@ -404,8 +404,8 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
         } else {
             ghost_from_interior<T, EQ, S, 0>(A.bc[1], uRf, nR);
         }
-        llf<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma);
-        llf<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma);
+        face_flux<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma, A.flux);
+        face_flux<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma, A.flux);
         const T invJ = (T)A.invJx;
 #pragma unroll
         for (int s = 0; s < S; ++s) {

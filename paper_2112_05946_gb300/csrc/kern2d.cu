@@ -277,8 +277,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             nL[s] = sTx[(((te * 2 + 1) * N1 + b) * S + s) * Q + tq];
             nR[s] = sTx[((((te + 2) * 2 + 0) * N1 + b) * S + s) * Q + tq];
         }
-        llf<T, EQ, S, 2, 0>(nL, tL, fIL, adv, gamma);
-        llf<T, EQ, S, 2, 0>(tR, nR, fIR, adv, gamma);
+        face_flux<T, EQ, S, 2, 0>(nL, tL, fIL, adv, gamma, A.flux);
+        face_flux<T, EQ, S, 2, 0>(tR, nR, fIR, adv, gamma, A.flux);
         const T invJ = (T)A.invJx;
 #pragma unroll
         for (int a = 0; a < N1; ++a)
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             ghost_from_interior<T, EQ, S, 1>(A.bc[2], tB, ybot);
         if (ey == ny - 1 && A.bc[3] != FRSG_BC_PERIODIC && A.bc[3] != FRSG_BC_DIRICHLET)
             ghost_from_interior<T, EQ, S, 1>(A.bc[3], tT, ytop);
-        llf<T, EQ, S, 2, 1>(ybot, tB, gIB, adv, gamma);
-        llf<T, EQ, S, 2, 1>(tT, ytop, gIT, adv, gamma);
+        face_flux<T, EQ, S, 2, 1>(ybot, tB, gIB, adv, gamma, A.flux);
+        face_flux<T, EQ, S, 2, 1>(tT, ytop, gIT, adv, gamma, A.flux);
         const T invJ = (T)A.invJy;
 #pragma unroll
         for (int b = 0; b < N1; ++b)

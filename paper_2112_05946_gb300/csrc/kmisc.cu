@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
     double vd[S][NPT];
     double ubar[S];
     double rho_bar = 1.0, eps = 0.0;
+    double eps_r = 0.0, eps_p = 0.0;   // density / pressure targets (eps, raised for float states)
     bool admissible = true;
     if (is_cand) {
         const T* ue = u + (size_t)e * elsz;
@@ -205,6 +206,13 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
         const double p_bar = pressure_d<S>(ubar, gamma);
         admissible = rho_bar > 0.0 && p_bar > 0.0;
         eps = fmin(1e-8, fmin(rho_bar, p_bar));
+        eps_r = eps_p = eps;
+        if (!exact) {
+            // a float state is rounded after limiting: aim 1e-5 of the mean density / energy
+            // above eps so that the rounded coefficients keep rho, p > 0 at every point
+            eps_r = fmin(eps + 1e-5 * rho_bar, 0.5 * rho_bar);
+            eps_p = fmin(eps + 1e-5 * fabs(ubar[S - 1]), 0.5 * p_bar);
+        }
 #pragma unroll
         for (int j = 0; j < NPT; ++j)
 #pragma unroll
@@ -234,13 +242,13 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
         el[te * 4 + 0] = a;
         el[te * 4 + 1] = b;
         double beta1 = 1.0;
-        if (rho_bar - a > 0.0) beta1 = fmin((rho_bar - eps) / (rho_bar - a), 1.0);
+        if (rho_bar - a > 0.0) beta1 = fmin((rho_bar - eps_r) / (rho_bar - a), 1.0);
         el[te * 4 + 2] = beta1;
         if (!admissible) atomicOr(A.err, kErrPositivity);
         if (!(a == a) || !(b == b)) atomicOr(A.err, kErrNonFinite);
     }
     __syncthreads();
-    const bool trig = is_cand && admissible && fmin(el[te * 4 + 0], el[te * 4 + 1]) < eps;
+    const bool trig = is_cand && admissible && (el[te * 4 + 0] < eps_r || el[te * 4 + 1] < eps_p);
     if (trig) {
         const double beta1 = el[te * 4 + 2];
         double bmin = 1.0;
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
 #pragma unroll
             for (int d = 0; d < S; ++d) us[d] = w[d];
             us[0] = beta1 * (us[0] - rho_bar) + rho_bar;
-            if (pressure_d<S>(us, gamma) < eps) bmin = fmin(bmin, pressure_root<S>(ubar, us, eps, gamma));
+            if (pressure_d<S>(us, gamma) < eps_p) bmin = fmin(bmin, pressure_root<S>(ubar, us, eps_p, gamma));
         });
         red[(te * Q + tq) * 2 + 0] = bmin;
     }

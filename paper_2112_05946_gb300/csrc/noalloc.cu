@@ -271,6 +271,7 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
     A.adv = cfg->adv_speed;
     A.gamma = cfg->gamma;
     A.filter = cfg->filter;
+    A.flux = cfg->flux;
     A.sensor = cfg->sensor;
     A.f_alpha = cfg->f_alpha;
     A.f_s = cfg->f_s;

@@ -1,5 +1,6 @@
 // Device physics of the FR-SG stage: pointwise fluxes (§3.2, Eq. 15; Euler §5.3-5.4),
-// flux-Jacobian spectral radius, local Lax-Friedrichs interface flux (§3.3).
+// flux-Jacobian spectral radius, local Lax-Friedrichs and HLL interface fluxes (§3.3; the
+// Euler setup tables of §5.3-5.4 name HLL).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -88,6 +89,61 @@ __device__ __forceinline__ void llf(const T (&uL)[S], const T (&uR)[S], T (&fI)[
                      wave_speed<T, EQ, S, DIM, DIR>(uR, adv, gamma));
 #pragma unroll
     for (int s = 0; s < S; ++s) fI[s] = T(0.5) * (fL[s] + fR[s]) - T(0.5) * a * (uR[s] - uL[s]);
+}
+
+// Euler flux along DIR with the normal velocity and sound speed of the state.
+template <typename T, int S, int DIR>
+__device__ __forceinline__ void euler_flux_vc(const T (&u)[S], T (&f)[S], T gamma, T* vn, T* c) {
+    const T ir = T(1) / u[0];
+    T m2 = T(0);
+#pragma unroll
+    for (int d = 1; d < S - 1; ++d) m2 += u[d] * u[d];
+    const T p = (gamma - T(1)) * (u[S - 1] - T(0.5) * m2 * ir);
+    *vn = u[1 + DIR] * ir;
+#pragma unroll
+    for (int s = 0; s < S; ++s) f[s] = u[s] * *vn;
+    f[1 + DIR] += p;
+    f[S - 1] += p * *vn;
+    *c = sqrt(gamma * p * ir);
+}
+
+// HLL with the Davis signal speeds: F_L if S_L >= 0, F_R if S_R <= 0, else
+// (S_R F_L - S_L F_R + S_L S_R (u_R - u_L)) / (S_R - S_L).
+template <typename T, int EQ, int S, int DIM, int DIR>
+__device__ __forceinline__ void hll(const T (&uL)[S], const T (&uR)[S], T (&fI)[S], T adv, T gamma) {
+    T fL[S], fR[S], sl, sr;
+    if constexpr (EQ == FRSG_EQ_EULER) {
+        T vl, cl, vr, cr;
+        euler_flux_vc<T, S, DIR>(uL, fL, gamma, &vl, &cl);
+        euler_flux_vc<T, S, DIR>(uR, fR, gamma, &vr, &cr);
+        sl = fmin(vl - cl, vr - cr);
+        sr = fmax(vl + cl, vr + cr);
+    } else {
+        phys_flux<T, EQ, S, DIM, DIR>(uL, fL, adv, gamma);
+        phys_flux<T, EQ, S, DIM, DIR>(uR, fR, adv, gamma);
+        const T al = EQ == FRSG_EQ_ADVECTION ? adv : uL[0];
+        const T ar = EQ == FRSG_EQ_ADVECTION ? adv : uR[0];
+        sl = fmin(al, ar);
+        sr = fmax(al, ar);
+    }
+    if (sl >= T(0)) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) fI[s] = fL[s];
+    } else if (sr <= T(0)) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) fI[s] = fR[s];
+    } else {
+        const T inv = T(1) / (sr - sl);
+#pragma unroll
+        for (int s = 0; s < S; ++s) fI[s] = (sr * fL[s] - sl * fR[s] + sl * sr * (uR[s] - uL[s])) * inv;
+    }
+}
+
+// The context's interface flux at one face point.
+template <typename T, int EQ, int S, int DIM, int DIR>
+__device__ __forceinline__ void face_flux(const T (&uL)[S], const T (&uR)[S], T (&fI)[S], T adv, T gamma, int kind) {
+    if (kind == FRSG_FLUX_HLL) hll<T, EQ, S, DIM, DIR>(uL, uR, fI, adv, gamma);
+    else llf<T, EQ, S, DIM, DIR>(uL, uR, fI, adv, gamma);
 }
 
 // Ghost state of a non-periodic side from the interior trace (nodal in z at one node).

@@ -18,6 +18,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_NONFINITE, E_POSITIVITY, E_TIMEOUT, E_UNSUPPORTE
 BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 EQUATION = {"advection": 0, "burgers": 1, "euler": 2}
 FILTER = {"none": 0, "exp": 1, "l2": 2, "lasso": 3}
+FLUX = {"llf": 0, "hll": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
 HOST, DEVICE = 0, 1
 
@@ -48,6 +49,7 @@ class Config(ctypes.Structure):
         ("s0", ctypes.c_double), ("kappa", ctypes.c_double),
         ("limiter", ctypes.c_int32),
         ("precision", ctypes.c_int32),
+        ("flux", ctypes.c_int32),
     ]
 
 
@@ -118,7 +120,7 @@ def exported_names():
 
 def make_config(dim=1, nx=32, ny=1, x0=0.0, x1=2.0, y0=0.0, y1=1.0, bc=("periodic",) * 4, P=2, N=4, Q=8,
                 equation="advection", adv_speed=1.0, gamma=1.4, filter="none", sensor=True, f_alpha=36.0,
-                f_s=4.0, f_eps1=0.6, f_eps2=0.6, s0=0.0, kappa=4.0, limiter=False, precision="fp64"):
+                f_s=4.0, f_eps1=0.6, f_eps2=0.6, s0=0.0, kappa=4.0, limiter=False, precision="fp64", flux="llf"):
     c = Config()
     c.struct_size = ctypes.sizeof(Config)
     c.dim, c.nx, c.ny = dim, nx, ny
@@ -133,6 +135,7 @@ def make_config(dim=1, nx=32, ny=1, x0=0.0, x1=2.0, y0=0.0, y1=1.0, bc=("periodi
     c.f_alpha, c.f_s, c.f_eps1, c.f_eps2, c.s0, c.kappa = f_alpha, f_s, f_eps1, f_eps2, s0, kappa
     c.limiter = int(bool(limiter))
     c.precision = PRECISION[precision]
+    c.flux = FLUX[flux] if isinstance(flux, str) else int(flux)
     return c
 
 
