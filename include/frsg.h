@@ -128,6 +128,17 @@ frsg_status fr_sg_set_boundary_nodal(frsg_ctx* ctx, int side, const double* g);
  * uhat_k(x_j) = sum_q w_q u0(x_j, z_q) Phi_k(z_q)   (§2.1, Eq. 6, third line, with Eq. 5). */
 frsg_status fr_sg_set_initial_nodal(frsg_ctx* ctx, const double* u0, int where);
 
+/* Galerkin projection of nodal values onto the gPC modes, out of place and without touching
+ * the context's state (§2.1, Eq. 6, third line): uhat[e][j][k][s] = sum_q wz_q Phi_k(z_q)
+ * u0[e][j][q][s].  u0 [E][Np][Q][S] and uhat [E][Np][M][S]: DEVICE double arrays on the
+ * context's stream (FRSG_E_INVAL for FRSG_HOST).  Asynchronous. */
+frsg_status fr_sg_project(frsg_ctx* ctx, const double* u0, double* uhat, int where);
+
+/* Transpose of fr_sg_project, for gradients with respect to the initial data and the
+ * parameters it depends on: g[e][j][q][s] = sum_k wz_q Phi_k(z_q) gbar[e][j][k][s].  gbar
+ * [E][Np][M][S] and g [E][Np][Q][S]: DEVICE double arrays.  Asynchronous. */
+frsg_status fr_sg_project_transpose(frsg_ctx* ctx, const double* gbar, double* g, int where);
+
 /* Copy the state in (set) or out (get) in the canonical double layout [E][Np][M][S],
  * converting from or to float in FRSG_FP32 contexts.  HOST variants synchronise. */
 frsg_status fr_sg_set_state(frsg_ctx* ctx, const double* uhat, int where);

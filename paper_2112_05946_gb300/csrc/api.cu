@@ -693,6 +693,28 @@ frsg_status fr_sg_set_initial_nodal(frsg_ctx* ctx, const double* u0, int where) 
     return FRSG_OK;
 }
 
+frsg_status fr_sg_project(frsg_ctx* ctx, const double* u0, double* uhat, int where) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!u0 || !uhat) return fail(ctx, FRSG_E_INVAL, "null array");
+    if (where != FRSG_DEVICE) return fail(ctx, FRSG_E_INVAL, "fr_sg_project takes device arrays");
+    ctx->launches += 1;
+    cudaError_t e = frsg::launch_project(true, u0, uhat, ctx->E, ctx->Np, ctx->M, ctx->Q, ctx->S, ctx->d_tab,
+                                         ctx->off, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project");
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_project_transpose(frsg_ctx* ctx, const double* gbar, double* g, int where) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!gbar || !g) return fail(ctx, FRSG_E_INVAL, "null array");
+    if (where != FRSG_DEVICE) return fail(ctx, FRSG_E_INVAL, "fr_sg_project_transpose takes device arrays");
+    ctx->launches += 1;
+    cudaError_t e = frsg::launch_project_transpose(gbar, g, ctx->E, ctx->Np, ctx->M, ctx->Q, ctx->S, ctx->d_tab,
+                                                   ctx->off, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project transpose");
+    return FRSG_OK;
+}
+
 frsg_status fr_sg_set_state(frsg_ctx* ctx, const double* uhat, int where) {
     if (!ctx) return FRSG_E_INVAL;
     if (!uhat) return fail(ctx, FRSG_E_INVAL, "null state");

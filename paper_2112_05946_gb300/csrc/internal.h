@@ -109,6 +109,9 @@ cudaError_t launch_max_speed(bool fp64, const void* uhat, int E, int Np, int M, 
                              int equation, double adv, double gamma, const double* tab, TabOff off,
                              unsigned long long* out_bits, cudaStream_t st);
 // Discrete adjoint kernels (kadjoint.cu), 1D scalar FP64.
+// Transpose of the initial projection: g[e][j][q][s] = sum_k Pz[k][q] gbar[e][j][k][s] (double).
+cudaError_t launch_project_transpose(const double* gbar, double* g, int E, int Np, int M, int Q, int S,
+                                     const double* tab, TabOff off, cudaStream_t st);
 cudaError_t launch_filter_transpose(int P, const double* mu, double* out, const uint8_t* flags, const double* tab,
                                     TabOff off, int filter, double alpha_dt, int E, int M, int S, cudaStream_t st);
 cudaError_t launch_adjoint_stage1d(int P, int equation, const double* v, const double* y, double* lam_v,

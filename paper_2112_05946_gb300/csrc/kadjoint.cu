@@ -234,6 +234,39 @@ cudaError_t adj_launch(int eq, const T* v, const T* y, T* lam_v, T* lam_base, do
 
 }  // namespace
 
+namespace {
+
+// Transpose of the initial projection (§2.1, Eq. 6, third line): the projection maps nodal
+// values u0[e][j][q][s] to uhat[e][j][k][s] = sum_q Pz[k][q] u0[e][j][q][s]; its transpose
+// maps a cotangent of uhat to g[e][j][q][s] = sum_k Pz[k][q] gbar[e][j][k][s].  One thread
+// per output value, grid-stride.
+__global__ void project_transpose_kernel(const double* gbar, double* g, int E, int Np, int M, int Q, int S,
+                                         const double* Pz) {
+    const size_t n = (size_t)E * Np * Q * S;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % S);
+        const size_t r = i / S;
+        const int q = (int)(r % Q);
+        const size_t ej = r / Q;
+        const double* src = gbar + ej * M * S + s;
+        double acc = 0.0;
+        for (int k = 0; k < M; ++k) acc += Pz[k * Q + q] * src[(size_t)k * S];
+        g[i] = acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_project_transpose(const double* gbar, double* g, int E, int Np, int M, int Q, int S,
+                                     const double* tab, TabOff off, cudaStream_t st) {
+    const size_t n = (size_t)E * Np * Q * S;
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    project_transpose_kernel<<<(int)blocks, 256, 0, st>>>(gbar, g, E, Np, M, Q, S, tab + off.Pz);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_filter_transpose(int P, const double* mu, double* out, const uint8_t* flags, const double* tab,
                                     TabOff off, int filter, double alpha_dt, int E, int M, int S, cudaStream_t st) {
     const size_t n = (size_t)E * M * S;

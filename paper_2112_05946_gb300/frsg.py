@@ -71,6 +71,8 @@ _SIGNATURES = [
     ("fr_sg_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_rk_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_rk4_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_project_transpose", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_stage", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     ("fr_sg_filter", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     ("fr_sg_limit", ctypes.c_int, [ctypes.c_void_p]),
@@ -258,6 +260,14 @@ class Solver:
 
     def rk_step(self, dt, nsteps=1, graph=True):
         self._ck(self.lib.fr_sg_rk_step(self.h, float(dt), int(nsteps), int(bool(graph))), "rk_step")
+
+    def project(self, u0, uhat):
+        """fr_sg_project: device float64 tensors [E, Np, Q, S] -> [E, Np, M, S]."""
+        self._ck(self.lib.fr_sg_project(self.h, _ptr(u0), _ptr(uhat), DEVICE), "project")
+
+    def project_transpose(self, gbar, g):
+        """fr_sg_project_transpose: device float64 tensors [E, Np, M, S] -> [E, Np, Q, S]."""
+        self._ck(self.lib.fr_sg_project_transpose(self.h, _ptr(gbar), _ptr(g), DEVICE), "project_transpose")
 
     def rk4_step(self, dt, nsteps=1, graph=True):
         """Classical RK4 steps (the advection study's integrator)."""

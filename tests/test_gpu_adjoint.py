@@ -134,3 +134,47 @@ def test_adjoint_rejects_unsupported_contexts():
     with pytest.raises(frsg.FrsgError) as ei:
         s.forward_record(1e-4, 2, 1)
     assert ei.value.status == frsg.E_UNSUPPORTED
+
+
+def test_parameter_gradient_of_uncertainty_magnitude():
+    """d QoI / d sigma for u0 = sin(pi x) + 0.3 + sigma z, through FRSGProject -> FRSGRun ->
+    a torch QoI.  (a) Var[int u dx] is conserved without a filter (periodic, conservative
+    scheme), so its gradient is the closed form 2 sigma L^2 / 3 (int u dx has the gPC
+    coefficient I_1 = sigma L / sqrt(3), z = Phi_1 / sqrt(3)); (b) the energy of the mean
+    field, sum J w_j E[u]^2 at t_end, against central differences of the FP64 oracle run
+    with the filter applied to every element (no detector switching)."""
+    import torch
+    from paper_2112_05946_gb300.autograd import FRSGProject, FRSGRun, qoi_mean_var, quadrature_weights
+    sigma0 = 0.1
+    for filt, sensor in [("none", True), ("exp", False)]:
+        wl = _burgers(nx=32, P=3, N=4, Q=9, filt=filt)
+        wl["solver"]["sensor"] = sensor
+        prob = oracle_problem(wl)
+        s = solver(wl)
+        x, z = s.nodes()
+        dt = 0.1 * prob.dx / 1.4
+        nsteps = 40
+        sig = torch.tensor(sigma0, dtype=torch.float64, device="cuda", requires_grad=True)
+        xt = torch.tensor(x, device="cuda")
+        zt = torch.tensor(z, device="cuda")
+        nodal = (torch.sin(np.pi * xt) + 0.3)[:, :, None, None] + sig * zt[None, None, :, None]
+        uT = FRSGRun.apply(FRSGProject.apply(nodal, s), s, dt, nsteps, 8)
+        Jw = quadrature_weights(s)
+        if filt == "none":
+            _, var = qoi_mean_var(Jw, uT)
+            (g,) = torch.autograd.grad(var, sig)
+            L = prob.x1 - prob.x0
+            assert float(g) == pytest.approx(2 * sigma0 * L ** 2 / 3, rel=1e-10)
+        else:
+            energy = torch.sum(Jw[None, :] * uT[:, :, 0, 0] ** 2)
+            (g,) = torch.autograd.grad(energy, sig)
+
+            def oracle_energy(sg):
+                u0 = integrate.project_initial(prob, lambda xx, zz: (np.sin(np.pi * xx) + 0.3 + sg * zz)[..., None])
+                u = integrate.run(prob, u0, dt, nsteps)
+                w = prob.tabs()["w"]
+                return float(np.sum(0.5 * prob.dx * w[None, :] * u[:, :, 0, 0] ** 2))
+            h = 1e-5
+            fd = (oracle_energy(sigma0 + h) - oracle_energy(sigma0 - h)) / (2 * h)
+            assert float(g) == pytest.approx(fd, rel=1e-6)
+        s.check()
