@@ -256,12 +256,21 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out);
  * tile is re-chosen automatically.  2D contexts accept only 0 (FRSG_E_UNSUPPORTED otherwise). */
 frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant);
 
-/* Autotuner: times whole SSP-RK3 steps (reps per candidate, CUDA events on the context's
- * stream) for every layout (1D) and tile that fits, keeps the fastest and caches the choice
- * per (dim, P, N, Q, S, precision, elements, filter, equation) for the process.  Saves and
- * restores the state (one temporary device allocation); overwrites the stage buffers and
- * the decision rows.  Synchronises.  variant_out / te_out (may be NULL) receive the choice. */
+/* Autotuner: times graph-replayed SSP-RK3 steps (reps per candidate, default 20; CUDA
+ * events on the context's stream) for every layout (1D) and tile that fits, re-times the
+ * three fastest in five interleaved rounds, keeps the best and caches the choice per
+ * (dim, P, N, Q, S, precision, elements, filter, equation, interface flux, limiter) for the
+ * process.  A cached shape is not re-timed.  Saves and restores the state (one temporary
+ * device allocation); overwrites the stage buffers and the decision rows; replayed decisions
+ * are not consumed.  Synchronises.  variant_out / te_out (may be NULL) receive the choice. */
 frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_out);
+
+/* Write the process-wide autotuner cache to a text file (one line per problem shape), or
+ * merge such a file into it, so that a later process reuses the choices without timing.
+ * Host only; FRSG_E_INVAL for a NULL path, an unreadable or unwritable file, or a malformed
+ * line (nothing is merged then). */
+frsg_status fr_sg_tune_cache_save(const char* path);
+frsg_status fr_sg_tune_cache_load(const char* path);
 
 /* Number of kernel launches issued on this context since creation (graph replays count
  * each captured kernel).  Host counter; never synchronises. */

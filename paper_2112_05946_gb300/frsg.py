@@ -71,6 +71,8 @@ _SIGNATURES = [
     ("fr_sg_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_rk_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_rk4_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_tune_cache_save", ctypes.c_int, [ctypes.c_char_p]),
+    ("fr_sg_tune_cache_load", ctypes.c_int, [ctypes.c_char_p]),
     ("fr_sg_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_project_transpose", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_stage", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
@@ -151,6 +153,20 @@ def _ptr(a):
     if not a.is_contiguous():   # torch tensor: the C ABI reads the row-major layout
         raise ValueError("device tensors must be contiguous")
     return a.data_ptr()
+
+
+def tune_cache_save(path):
+    """fr_sg_tune_cache_save: write the autotuner's per-shape choices to a text file."""
+    st = load_library().fr_sg_tune_cache_save(os.fsencode(path))
+    if st != OK:
+        raise FrsgError(st, f"fr_sg_tune_cache_save({path}) failed")
+
+
+def tune_cache_load(path):
+    """fr_sg_tune_cache_load: merge a file written by tune_cache_save into the cache."""
+    st = load_library().fr_sg_tune_cache_load(os.fsencode(path))
+    if st != OK:
+        raise FrsgError(st, f"fr_sg_tune_cache_load({path}) failed")
 
 
 def rk_step_noalloc(u_in, u_out, dt, nsteps=1, ghost_modes=None, stream=None, **cfg):

@@ -56,3 +56,22 @@ def test_config_struct_size_matches_header_layout(lib):
     fn.argtypes = [ctypes.POINTER(frsg.Config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
     assert fn(ctypes.byref(bad), None, ctypes.byref(h)) == frsg.E_INVAL
     assert not h.value
+
+
+def test_tune_cache_file_roundtrip(tmp_path):
+    """The autotuner cache file is host-only: save, load, and reject malformed files."""
+    from paper_2112_05946_gb300 import frsg
+    frsg.load_library()
+    p = tmp_path / "tune.txt"
+    frsg.tune_cache_save(str(p))
+    assert p.read_text().startswith("frsg-tune 1")
+    p.write_text("frsg-tune 1\n1 3 8 16 1 1 1024 1 1 0 0 1 4\n")
+    frsg.tune_cache_load(str(p))
+    frsg.tune_cache_save(str(p))
+    assert "1 3 8 16 1 1 1024 1 1 0 0 1 4" in p.read_text()
+    bad = tmp_path / "bad.txt"
+    bad.write_text("frsg-tune 1\n1 2 3\n")
+    with pytest.raises(frsg.FrsgError):
+        frsg.tune_cache_load(str(bad))
+    with pytest.raises(frsg.FrsgError):
+        frsg.tune_cache_load(str(tmp_path / "missing.txt"))
