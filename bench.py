@@ -40,7 +40,7 @@ ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5}     # relative L2 vs the FP64 oracle a
 ACC_STEPS = 50
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
@@ -52,7 +52,32 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the Sod, 2D, batched and adjoint lines")
     ap.add_argument("--only", default=None, choices=["burgers", "sod", "shock_vortex", "batch", "adjoint"],
                     help="measure one extra workload alone and print its line (for profiling runs)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def max_over_ranks(torch, v, world, device):
+    """The largest value over all ranks (the step time the whole job is held to); v itself
+    when there is one rank."""
+    if world == 1:
+        return v
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, dof, stages, ms):
+    """DOF-stage updates per second of the whole job: each of the `world` ranks advances its
+    own replica of `dof` unknowns through `stages` stages every `ms` milliseconds."""
+    return world * dof * stages / (ms * 1e-3)
+
+
+def load_tune_cache(frsg):
+    """Merge the autotuner choices of an earlier run (FRSG_TUNE_CACHE) so that a profiler
+    run of the same command times the layouts the plain run chose."""
+    path = os.environ.get("FRSG_TUNE_CACHE")
+    if path and os.path.exists(path):
+        frsg.tune_cache_load(path)
+    return path
 
 
 def dist_env():
@@ -215,10 +240,15 @@ def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracl
     )
 
 
-def measure_extra(torch, frsg, wl, precision, steps, warmup, stream, flush):
+def measure_extra(torch, frsg, wl, precision, steps, warmup, stream, flush, integrator="ssp3"):
     """Throughput of another workload (FP64 or FP32 form): per-step events with the L2
-    flush between steps, dt fixed from the initial CFL condition, plus the stage-kernel
-    duration (limiter launches, if any, timed with their stage)."""
+    flush between steps, dt from the CFL condition refreshed every 20 steps outside the timed
+    events, plus the stage-kernel duration (limiter launches, if any, timed with their
+    stage).  integrator "rk4" times classical RK4 steps (four stages; per-stage time = step
+    time / 4)."""
+    rk4 = integrator == "rk4"
+    nst = 4 if rk4 else 3
+    lim = bool(wl["solver"].get("limiter"))
     E, Np, M, S = workload_sizes(wl)
     dof = E * Np * M * S
     esz = 8 if precision == "fp64" else 4
@@ -233,23 +263,31 @@ def measure_extra(torch, frsg, wl, precision, steps, warmup, stream, flush):
     else:
         s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[2], nodes[1]))
     # half the CFL number of the correctness runs, refreshed every 20 steps outside the timed
-    # events: the Euler wave speeds grow after t = 0
+    # events: the Euler wave speeds grow after t = 0.  With the limiter on, the state is
+    # limited before each refresh (a projection discontinuous in z, or a filtered stage
+    # output, can leave inadmissible z-node states that the next stage would limit anyway).
     cfl = 0.5 * wl["cfl"]
-    dt = s.cfl_dt(cfl)
+
+    def refresh_dt():
+        if lim:
+            s.limit()
+        return s.cfl_dt(cfl)
+    dt = refresh_dt()
+    advance = s.rk4_step if rk4 else s.rk_step
     with torch.cuda.stream(stream):
-        s.rk_step(dt, warmup, graph=True)
+        advance(dt, warmup, graph=True)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         for i in range(steps):
             if i % 20 == 0:
-                dt = s.cfl_dt(cfl)
+                dt = refresh_dt()
             flush.zero_()
             starts[i].record(stream)
-            s.rk_step(dt, 1, graph=True)
+            advance(dt, 1, graph=True)
             ends[i].record(stream)
         stream.synchronize()
         step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-        kst = min(steps, 50)
+        kst = 0 if rk4 else min(steps, 50)
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kst)]
         for i in range(kst):
             flush.zero_()
@@ -260,11 +298,17 @@ def measure_extra(torch, frsg, wl, precision, steps, warmup, stream, flush):
         stream.synchronize()
     s.check()
     s.close()
-    stage = np.mean(np.array([[evs[i][k].elapsed_time(evs[i][k + 1]) for k in range(3)] for i in range(kst)]), axis=0)
     ms = float(np.mean(step_ms))
-    alg = (2 + 3 + 3) * esz * dof
-    return dict(value=dof * 3 / (ms * 1e-3), ms_per_step=ms, dof=dof, stage_us=[float(v * 1e3) for v in stage],
-                achieved_gbs=alg / (float(np.sum(stage)) * 1e-3) / 1e9, limiter=bool(wl["solver"].get("limiter")))
+    if rk4:
+        stage = np.full(4, ms / 4)
+        alg = (3 + 5 + 5 + 3) * esz * dof      # arrays per stage: y, u, sum of residuals
+    else:
+        stage = np.mean(np.array([[evs[i][k].elapsed_time(evs[i][k + 1]) for k in range(3)]
+                                  for i in range(kst)]), axis=0)
+        alg = (2 + 3 + 3) * esz * dof
+    return dict(value=dof * nst / (ms * 1e-3), ms_per_step=ms, dof=dof, stage_us=[float(v * 1e3) for v in stage],
+                achieved_gbs=alg / (float(np.sum(stage)) * 1e-3) / 1e9, limiter=lim, integrator=integrator,
+                filter=wl["solver"].get("filter"), flux=wl["solver"].get("flux", "llf"))
 
 
 def measure_batch(torch, frsg, precision, steps, warmup, stream, flush):
@@ -382,6 +426,7 @@ def run_only(args):
     from paper_2112_05946_gb300 import frsg
     _b.build()
     frsg.load_library()
+    tune_file = load_tune_cache(frsg)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if args.only == "burgers":
@@ -396,6 +441,8 @@ def run_only(args):
         wl = workloads.ALL[args.only]()
         out = {p: measure_extra(torch, frsg, wl, p, args.steps, args.warmup, stream, flush) for p in ("fp64", "fp32")}
     print(json.dumps({"only": args.only, "result": out}))
+    if tune_file:
+        frsg.tune_cache_save(tune_file)
 
 
 def run_ours(args):
@@ -414,6 +461,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     frsg.load_library()
+    tune_file = load_tune_cache(frsg)
     wl = workloads.ALL[args.workload]()
     ref = oracle_reference(wl, ACC_STEPS)
     stream = torch.cuda.Stream()
@@ -438,6 +486,18 @@ def run_ours(args):
             ewl = workloads.ALL[name]()
             extra[ewl["name"]] = {prec: measure_extra(torch, frsg, ewl, prec, xsteps, 3, stream, flush)
                                   for prec in ("fp64", "fp32")}
+        # the headline workload with the Lasso filter (every element), and with classical RK4
+        lwl = workloads.burgers_1d()
+        lwl["solver"].update(filter="lasso", sensor=False)
+        extra[lwl["name"] + "_lasso"] = {prec: measure_extra(torch, frsg, lwl, prec, xsteps, 3, stream, flush)
+                                         for prec in ("fp64", "fp32")}
+        rwl = workloads.burgers_1d()
+        extra[rwl["name"] + "_rk4"] = {prec: measure_extra(torch, frsg, rwl, prec, xsteps, 3, stream, flush, "rk4")
+                                       for prec in ("fp64", "fp32")}
+        # the paper's second Sod case (stochastic shock location, HLL, Lasso) at 4096 elements
+        hwl = workloads.sod_location_1d(nx=4096)
+        extra[hwl["name"]] = {prec: measure_extra(torch, frsg, hwl, prec, xsteps, 3, stream, flush)
+                              for prec in ("fp64", "fp32")}
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -445,12 +505,8 @@ def run_ours(args):
 
     ok = [f for f in forms.values() if f["err_vs_oracle"] <= f["err_bound"]]
     chosen = max(ok, key=lambda f: f["value"]) if ok else forms["fp64"]
-    ms = chosen["ms_per_step"]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * chosen["dof"] * 3 / (ms * 1e-3)
+    ms = max_over_ranks(torch, chosen["ms_per_step"], world, "cuda")
+    value = whole_job_value(world, chosen["dof"], 3, ms)
 
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -495,11 +551,15 @@ def run_ours(args):
         "other_workloads": {
             k: {p: {"value": f["value"], "ms_per_step": f["ms_per_step"], "dof": f["dof"], "stage_us": f["stage_us"],
                     "stage_gbs": f["achieved_gbs"], "stage_hbm_frac": f["achieved_gbs"] / hbm_peak,
-                    "limiter": f["limiter"]} for p, f in v.items()}
+                    "limiter": f["limiter"], "integrator": f["integrator"], "filter": f["filter"],
+                    "flux": f["flux"]}
+                for p, f in v.items()}
             for k, v in extra.items()},
     }
     if rank == 0:
         print(json.dumps(line))
+        if tune_file:
+            frsg.tune_cache_save(tune_file)
     if world > 1:
         torch.distributed.destroy_process_group()
 
