@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libfrsg.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "tables.cpp", "kern1d.cu", "kern2d.cu", "kmisc.cu", "noalloc.cu", "kadjoint.cu"]
+SOURCES = ["api.cu", "tables.cpp", "kern1d.cu", "kern2d.cu", "kmisc.cu", "noalloc.cu", "kadjoint.cu", "kadjoint_euler.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -301,13 +301,14 @@ cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
 // Stage s of an SSP-RK3 step (Shu-Osher form): limit the stage input, then
 // uout = a_s u^n + b_s (uin + dt L(uin)) followed by detector + filter.
 //   s = 0: u -> u1,  s = 1: u1 -> u2,  s = 2: u2 -> u (in place on u^n, element-local).
-cudaError_t issue_stage_ex(frsg_ctx* c, int s, double dt, uint8_t* flags_out, const uint8_t* replay_in) {
+cudaError_t issue_stage_ex(frsg_ctx* c, int s, double dt, uint8_t* flags_out, const uint8_t* replay_in,
+                           bool with_limiter = true) {
     const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
     void* bufs_in[3] = {c->d_u, c->d_u1, c->d_u2};
     void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
-    if (c->cfg.limiter) {
+    if (c->cfg.limiter && with_limiter) {
         cudaError_t e = launch_limiter(c, bufs_in[s], c->d_beta + (size_t)s * c->E);
         if (e != cudaSuccess) return e;
     }
@@ -1162,11 +1163,12 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
 
 static frsg_status adjoint_supported(frsg_ctx* ctx) {
     const frsg_config& c = ctx->cfg;
-    if (c.dim != 1 || !ctx->fp64 || c.equation == FRSG_EQ_EULER || c.limiter || c.bc[0] != FRSG_BC_PERIODIC ||
-        c.filter == FRSG_FILTER_LASSO || c.flux != FRSG_FLUX_LLF)
+    const bool euler = c.equation == FRSG_EQ_EULER;
+    if (c.dim != 1 || !ctx->fp64 || c.filter == FRSG_FILTER_LASSO || c.flux != FRSG_FLUX_LLF ||
+        (!euler && (c.limiter || c.bc[0] != FRSG_BC_PERIODIC)))
         return fail(ctx, FRSG_E_UNSUPPORTED,
-                    "the adjoint covers 1D periodic advection/Burgers contexts in FRSG_FP64 without limiter, "
-                    "with the LLF flux and a linear (exponential or L2) filter");
+                    "the adjoint covers 1D FRSG_FP64 contexts with the LLF flux and a linear (exponential or L2) "
+                    "filter: periodic advection/Burgers, or Euler with any 1D boundary kind and the limiter");
     return FRSG_OK;
 }
 
@@ -1369,7 +1371,9 @@ frsg_status fr_sg_forward_record(frsg_ctx* ctx, double dt, int nsteps, int check
     CK(cudaStreamSynchronize(ctx->stream));
     CK(grow((void**)&ctx->d_ckpt, &ctx->rec_cap_ckpt, nck, sizeof(double) * nstate));
     CK(grow((void**)&ctx->d_log, &ctx->rec_cap_steps, nsteps, 3 * (size_t)ctx->E));
-    CK(grow((void**)&ctx->d_seg, &ctx->rec_cap_seg, 3 * checkpoint_every, sizeof(double) * nstate));
+    // per step: the three stage inputs before the limiter and, with the limiter, after it
+    const int per_step = ctx->cfg.limiter ? 6 : 3;
+    CK(grow((void**)&ctx->d_seg, &ctx->rec_cap_seg, per_step * checkpoint_every, sizeof(double) * nstate));
     CK(grow((void**)&ctx->d_work, &cap_work, 1, 5 * sizeof(double) * nstate));
     CK(set_dt(ctx, dt));
     double* u = static_cast<double*>(ctx->d_u);
@@ -1410,22 +1414,39 @@ frsg_status fr_sg_adjoint(frsg_ctx* ctx, const double* lambda_T, double* grad_u0
     const int nseg = (nsteps + k - 1) / k;
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const bool euler = c.equation == FRSG_EQ_EULER;
+    const bool lim = c.limiter != 0;
+    const int per_step = lim ? 6 : 3;
+    void* bufs_in[3] = {ctx->d_u, ctx->d_u1, ctx->d_u2};
+    // lim'(y)^T applied to a cotangent (the identity without the limiter)
+    auto limiter_back = [&](const double* y, const double* vb, double* out) -> cudaError_t {
+        if (!lim) return cudaMemcpyAsync(out, vb, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream);
+        ctx->launches += 1;
+        return frsg::launch_limiter_adjoint1d(c.P, y, vb, out, ctx->E, ctx->M, ctx->Q, ctx->d_tab, ctx->off, c.gamma,
+                                              ctx->stream);
+    };
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int n0 = sg * k, n1 = std::min(nsteps, n0 + k);
         CK(cudaMemcpyAsync(u, ctx->d_ckpt + (size_t)sg * nstate, sizeof(double) * nstate, cudaMemcpyDeviceToDevice,
                            ctx->stream));
+        // recompute the segment: stage inputs before (Y) and after (V) the limiter
         for (int n = n0; n < n1; ++n) {
-            double* seg = ctx->d_seg + (size_t)3 * (n - n0) * nstate;
-            CK(cudaMemcpyAsync(seg, u, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+            double* seg = ctx->d_seg + (size_t)per_step * (n - n0) * nstate;
             for (int s = 0; s < 3; ++s) {
-                CK(issue_stage_ex(ctx, s, dt, nullptr, ctx->d_log + (size_t)(3 * n + s) * ctx->E));
-                if (s < 2)
-                    CK(cudaMemcpyAsync(seg + (size_t)(s + 1) * nstate, s == 0 ? ctx->d_u1 : ctx->d_u2,
-                                       sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+                CK(cudaMemcpyAsync(seg + (size_t)s * nstate, bufs_in[s], sizeof(double) * nstate,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+                if (lim) {
+                    CK(launch_limiter(ctx, bufs_in[s], ctx->d_beta + (size_t)s * ctx->E));
+                    CK(cudaMemcpyAsync(seg + (size_t)(3 + s) * nstate, bufs_in[s], sizeof(double) * nstate,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+                }
+                CK(issue_stage_ex(ctx, s, dt, nullptr, ctx->d_log + (size_t)(3 * n + s) * ctx->E, false));
             }
         }
         for (int n = n1 - 1; n >= n0; --n) {
-            const double* seg = ctx->d_seg + (size_t)3 * (n - n0) * nstate;
+            const double* seg = ctx->d_seg + (size_t)per_step * (n - n0) * nstate;
+            const double* segY = seg;
+            const double* segV = lim ? seg + (size_t)3 * nstate : seg;
             const double* mu = lam;
             for (int s = 2; s >= 0; --s) {
                 const uint8_t* fl = ctx->d_log + (size_t)(3 * n + s) * ctx->E;
@@ -1437,16 +1458,25 @@ frsg_status fr_sg_adjoint(frsg_ctx* ctx, const double* lambda_T, double* grad_u0
                     y = t1;
                 }
                 ctx->launches += 1;
-                CK(frsg::launch_adjoint_stage1d(c.P, c.equation, seg + (size_t)s * nstate, y, t2, lb, ca[s], cb[s],
-                                                cb[s] * dt, s == 2 ? 1 : 0, s == 0 ? 1 : 0, ctx->d_tab, ctx->off,
-                                                ctx->E, ctx->M, ctx->Q, ctx->TE, invJx, c.adv_speed, ctx->stream));
+                if (euler) {
+                    CK(frsg::launch_adjoint_stage_euler1d(c.P, segV + (size_t)s * nstate, y, t2, lb, ca[s], cb[s],
+                                                          cb[s] * dt, s == 2 ? 1 : 0, s == 0 ? 1 : 0, ctx->d_tab,
+                                                          ctx->off, ctx->E, ctx->M, ctx->Q, invJx, c.gamma, c.bc[0],
+                                                          c.bc[1], ctx->d_ghost, ctx->stream));
+                } else {
+                    CK(frsg::launch_adjoint_stage1d(c.P, c.equation, segV + (size_t)s * nstate, y, t2, lb, ca[s],
+                                                    cb[s], cb[s] * dt, s == 2 ? 1 : 0, s == 0 ? 1 : 0, ctx->d_tab,
+                                                    ctx->off, ctx->E, ctx->M, ctx->Q, ctx->TE, invJx, c.adv_speed,
+                                                    ctx->stream));
+                }
                 if (s > 0) {
-                    // the next stage down receives the cotangent of this stage's input
-                    CK(cudaMemcpyAsync(lam, t2, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+                    // the next stage down receives the cotangent of this stage's (pre-limit) input
+                    CK(limiter_back(segY + (size_t)s * nstate, t2, lam));
                     mu = lam;
                 }
             }
-            CK(cudaMemcpyAsync(lam, lb, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));
+            // lb: cotangent of the limited step input v_0 = lim(u^n)
+            CK(limiter_back(segY, lb, lam));
         }
     }
     CK(cudaMemcpyAsync(grad_u0, lam, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, ctx->stream));

@@ -114,6 +114,13 @@ cudaError_t launch_project_transpose(const double* gbar, double* g, int E, int N
                                      const double* tab, TabOff off, cudaStream_t st);
 cudaError_t launch_filter_transpose(int P, const double* mu, double* out, const uint8_t* flags, const double* tab,
                                     TabOff off, int filter, double alpha_dt, int E, int M, int S, cudaStream_t st);
+// Reverse of one 1D Euler stage residual (LLF, any 1D boundary kind) and of the limiter (double).
+cudaError_t launch_adjoint_stage_euler1d(int P, const double* v, const double* y, double* lam_v, double* lam_base,
+                                         double a, double b, double cdt, int base_init, int accumulate,
+                                         const double* tab, TabOff off, int E, int M, int Q, double invJx,
+                                         double gamma, int bcL, int bcR, const double* ghost, cudaStream_t st);
+cudaError_t launch_limiter_adjoint1d(int P, const double* y, const double* vbar, double* ybar, int E, int M, int Q,
+                                     const double* tab, TabOff off, double gamma, cudaStream_t st);
 cudaError_t launch_adjoint_stage1d(int P, int equation, const double* v, const double* y, double* lam_v,
                                    double* lam_base, double a, double b, double cdt, int base_init, int accumulate,
                                    const double* tab, TabOff off, int E, int M, int Q, int TE, double invJx,
