@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libfrsg.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "tables.cpp", "kern1d.cu", "kern2d.cu", "kmisc.cu", "noalloc.cu", "kadjoint.cu", "kadjoint_euler.cu"]
+SOURCES = ["api.cu", "tables.cpp", "kern1d.cu", "kern1d_f32.cu", "kern1d_f64.cu", "kern2d.cu", "kmisc.cu", "noalloc.cu",
+           "kadjoint.cu", "kadjoint_euler.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

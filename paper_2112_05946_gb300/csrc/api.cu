@@ -1266,6 +1266,7 @@ frsg_status fr_sg_batch_create(frsg_ctx* const* ctxs, int n, void* stream, frsg_
         fr_sg_batch_destroy(b);
         return FRSG_E_INVAL;
     }
+    for (auto& a : args) frsg::prepare_float_scalars(a);
     e = cudaMalloc(&b->d_args, sizeof(frsg::StageArgs) * args.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(int4) * t4.size());
     if (e == cudaSuccess)

@@ -30,17 +30,80 @@ __device__ inline const double* table_block<double>(const StageArgs& A) { return
 template <>
 __device__ inline const float* table_block<float>(const StageArgs& A) { return A.tabf; }
 
-// Lambda[m][k] for this launch: exp(-alpha dt E[m][k]) (exponential, E = sum eta^s) or the
-// stored L2 factor.
+// The launch's scalars in the kernel's precision.  Float kernels take the float copies the
+// host prepared (prepare_float_scalars) and convert only dt, once per thread; double-typed
+// conversions and compares would otherwise go through the slow FP64 pipe in every thread.
 template <typename T>
-__device__ inline void load_filter_strengths(const StageArgs& A, int NP, T* sLam, int tid, int nthr, double dt) {
+struct StageConsts {
+    T ca, cb, cc;              // uout = ca base + cb uin + cc L(uin)   (cc = c dt)
+    T adv, gamma, invJx, invJy;
+    T det;                     // detector ratio
+    T adt;                     // alpha dt of the exponential filter
+    T xa, xb, xc;              // accumulator: xa acc_in + xb uin + xc L(uin)
+    int use_base;
+};
+
+__device__ inline bool nonzero(double x) { return (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0; }
+
+template <typename T>
+__device__ inline StageConsts<T> make_consts(const StageArgs& A);
+
+template <>
+__device__ inline StageConsts<double> make_consts<double>(const StageArgs& A) {
+    const double dt = A.dtp ? *A.dtp : A.dt_filter;
+    StageConsts<double> K;
+    K.ca = A.a;
+    K.cb = A.b;
+    K.cc = A.dtp ? A.c * dt : A.c;
+    K.adv = A.adv;
+    K.gamma = A.gamma;
+    K.invJx = A.invJx;
+    K.invJy = A.invJy;
+    K.det = A.det_ratio;
+    K.adt = A.f_alpha * dt;
+    K.xa = A.acc_a;
+    K.xb = A.acc_b;
+    K.xc = A.dtp ? A.acc_c * dt : A.acc_c;
+    K.use_base = nonzero(A.a) ? 1 : 0;
+    return K;
+}
+
+template <>
+__device__ inline StageConsts<float> make_consts<float>(const StageArgs& A) {
+    const float dt = (float)(A.dtp ? *A.dtp : A.dt_filter);
+    StageConsts<float> K;
+    K.ca = A.fa;
+    K.cb = A.fb;
+    K.cc = A.dtp ? A.fc * dt : A.fc;
+    K.adv = A.fadv;
+    K.gamma = A.fgamma;
+    K.invJx = A.finvJx;
+    K.invJy = A.finvJy;
+    K.det = A.fdet;
+    K.adt = A.falpha * dt;
+    K.xa = A.fxa;
+    K.xb = A.fxb;
+    K.xc = A.dtp ? A.fxc * dt : A.fxc;
+    K.use_base = nonzero(A.a) ? 1 : 0;
+    return K;
+}
+
+// Lambda[m][k] for this launch: exp(-alpha dt E[m][k]) (exponential, E = sum eta^s) or the
+// stored L2 / Lasso table.  Two halves, so that the table's global loads join the kernel's
+// first load sweep and only the exponential waits for dt: load_filter_table copies the raw
+// table; finish_filter_strengths (after the first barrier) maps each thread's own entries.
+template <typename T>
+__device__ inline void load_filter_table(const StageArgs& A, int NP, T* sLam, int tid, int nthr) {
     const int n = NP * A.M;
     const T* tab = table_block<T>(A);
-    const T adt = (T)(A.f_alpha * dt);
-    for (int i = tid; i < n; i += nthr) {
-        const T v = tab[A.off.lam + i];
-        sLam[i] = A.filter == FRSG_FILTER_EXP ? exp(-adt * v) : v;
-    }
+    for (int i = tid; i < n; i += nthr) sLam[i] = tab[A.off.lam + i];
+}
+
+template <typename T>
+__device__ inline void finish_filter_strengths(const StageArgs& A, int NP, T* sLam, int tid, int nthr, T adt) {
+    if (A.filter != FRSG_FILTER_EXP) return;
+    const int n = NP * A.M;
+    for (int i = tid; i < n; i += nthr) sLam[i] = exp(-adt * sLam[i]);
 }
 
 // Second output of a stage, element-offset global pointers (see StageArgs::acc_out).
@@ -52,14 +115,14 @@ struct AccTerm {
 };
 
 template <typename T>
-__device__ inline AccTerm<T> acc_term(const StageArgs& A, size_t off, double dt) {
+__device__ inline AccTerm<T> acc_term(const StageArgs& A, size_t off, const StageConsts<T>& K) {
     AccTerm<T> r{nullptr, nullptr, T(0), T(0), T(0)};
     if (A.acc_out) {
         r.dst = static_cast<T*>(A.acc_out) + off;
         r.src = A.acc_in ? static_cast<const T*>(A.acc_in) + off : nullptr;
-        r.a = (T)A.acc_a;
-        r.b = (T)A.acc_b;
-        r.c = (T)(A.dtp ? A.acc_c * dt : A.acc_c);
+        r.a = K.xa;
+        r.b = K.xb;
+        r.c = K.xc;
     }
     return r;
 }
@@ -138,8 +201,7 @@ template <typename T, int NP, int S>
 __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T* Mod, const T* sVf, const T* sVfinv,
                                              const T* sLam, const T* sTop, T* sRed, int* sFlag, int te, int kl,
                                              int nk, int ml, int nm, bool active, bool member, int e0, T* uout,
-                                             size_t gbase) {
-    const int M = A.M;
+                                             size_t gbase, T det, int M) {
     const int elsz = NP * M * S;
     const T* ue = Us + te * elsz;
     T* me = Mod + te * elsz;
@@ -159,14 +221,37 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
         }
     }
     const int lt = ml * nk + kl, nlt = nk * nm;
-    if (member) {
+    // Energy sums over the element's nlt threads.  The element's threads are consecutive in
+    // the block (thread te*nlt + lt), so when nlt is a power of two and the block is whole
+    // warps, a group is a lane-aligned piece of a warp (nlt <= 32) or whole warps: shuffle
+    // sums, then at most a few partials per element through shared memory.  Otherwise every
+    // thread's partial goes through shared memory and one thread per element adds them.
+    // Measured on the benchmark shapes, the shuffle wins for double states (a serial chain of
+    // double adds is long) and loses slightly for float ones, so float keeps the serial sum.
+    const int nblk = blockDim.x * blockDim.y * blockDim.z;
+    const bool shuffle = sizeof(T) == 8 && (nlt & (nlt - 1)) == 0 && (nblk & 31) == 0;
+    T t0 = tot, t1 = top;
+    int parts = nlt;
+    if (shuffle) {
+        const int width = nlt < 32 ? nlt : 32;
+        for (int o = width >> 1; o > 0; o >>= 1) {
+            t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+            t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        }
+        parts = nlt / width;
+        if (member && (lt & (width - 1)) == 0) {
+            sRed[(te * nlt + lt / width) * 2 + 0] = t0;
+            sRed[(te * nlt + lt / width) * 2 + 1] = t1;
+        }
+    } else if (member) {
         sRed[(te * nlt + lt) * 2 + 0] = tot;
         sRed[(te * nlt + lt) * 2 + 1] = top;
     }
     __syncthreads();
     if (active && lt == 0) {
-        T t0 = T(0), t1 = T(0);
-        for (int i = 0; i < nlt; ++i) {
+        t0 = T(0);
+        t1 = T(0);
+        for (int i = 0; i < parts; ++i) {
             t0 += sRed[(te * nlt + i) * 2 + 0];
             t1 += sRed[(te * nlt + i) * 2 + 1];
         }
@@ -174,7 +259,7 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
         int fl;
         if (A.replay) fl = A.replay[e] ? 1 : 0;
         else if (!A.sensor) fl = 1;
-        else fl = (t1 > T(0) && t1 > (T)A.det_ratio * t0) ? 1 : 0;
+        else fl = (t1 > T(0) && t1 > det * t0) ? 1 : 0;
         sFlag[te] = fl;
         if (A.flags) A.flags[e] = (uint8_t)fl;
     }

@@ -74,7 +74,25 @@ struct StageArgs {
     void* acc_out;
     const void* acc_in;
     double acc_a, acc_b, acc_c;
+    // the same scalars in float for FP32 kernels (prepare_float_scalars fills them on the host,
+    // so that float kernels issue no double-precision conversions per thread)
+    float fa, fb, fc, fadv, fgamma, finvJx, finvJy, fdet, falpha, fxa, fxb, fxc;
 };
+
+inline void prepare_float_scalars(StageArgs& A) {
+    A.fa = (float)A.a;
+    A.fb = (float)A.b;
+    A.fc = (float)A.c;
+    A.fadv = (float)A.adv;
+    A.fgamma = (float)A.gamma;
+    A.finvJx = (float)A.invJx;
+    A.finvJy = (float)A.invJy;
+    A.fdet = (float)A.det_ratio;
+    A.falpha = (float)A.f_alpha;
+    A.fxa = (float)A.acc_a;
+    A.fxb = (float)A.acc_b;
+    A.fxc = (float)A.acc_c;
+}
 
 struct LimitArgs {
     void* u;               // state limited in place

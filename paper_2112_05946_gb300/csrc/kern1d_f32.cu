@@ -1,0 +1,27 @@
+// Instantiations of the 1D stage kernels for float states (the kernel templates are in
+// kern1d.cuh; one translation unit per precision keeps the build parallel).
+#include "kern1d.cuh"
+
+namespace frsg {
+
+cudaError_t k1d_stage_f32(const frsg_config& cfg, const StageArgs& A, cudaStream_t st) {
+    return launch_np<float>(cfg, A, st);
+}
+
+cudaError_t k1d_step_f32(const frsg_config& cfg, const StageArgs* A3, unsigned* bar, int* grid, cudaStream_t st) {
+    return step_np<float>(cfg, A3, bar, grid, st);
+}
+
+cudaError_t k1d_batched_f32(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,
+                          cudaStream_t st) {
+    if (equation == FRSG_EQ_ADVECTION) return batched_typed<float, FRSG_EQ_ADVECTION>(args, tiles, ntiles, smem, grid, st);
+    if (equation == FRSG_EQ_BURGERS) return batched_typed<float, FRSG_EQ_BURGERS>(args, tiles, ntiles, smem, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+int k1d_batched_occ_f32(int equation, size_t smem) {
+    if (equation == FRSG_EQ_ADVECTION) return batched_occ<float, FRSG_EQ_ADVECTION>(smem);
+    return batched_occ<float, FRSG_EQ_BURGERS>(smem);
+}
+
+}  // namespace frsg

@@ -45,6 +45,30 @@ size_t smem2d_bytes_t(int TE, int n1, int M, int Q, int S) {
     return smem2d_elems<T>(TE, n1, M, Q, S) * sizeof(T) + (size_t)TE * sizeof(int) + 16;
 }
 
+// The S consecutive variables at p; one 16-byte shared-memory load per 4 floats (2 per 4
+// doubles) when S = 4 (the offsets used here are multiples of 4 elements from a 16-byte
+// aligned base).
+template <typename T, int S>
+__device__ __forceinline__ void ldv(const T* p, T (&o)[S]) {
+    if constexpr (S == 4 && sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    } else if constexpr (S == 4 && sizeof(T) == 8) {
+        const double2 v0 = *reinterpret_cast<const double2*>(p);
+        const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = v0.x;
+        o[1] = v0.y;
+        o[2] = v1.x;
+        o[3] = v1.y;
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) o[s] = p[s];
+    }
+}
+
 // Trace of element `e` at z-node q along a line: sum over the n1 points of the line of
 // w[i] * sum_k Phi_k(z_q) uhat[point(i)][k][s].  Row line (fixed b) or column (fixed a).
 template <typename T, int N1, int S>
@@ -58,18 +82,21 @@ __device__ inline void line_trace(const T* ue, int M, const T* Vzq_stride, int Q
         for (int i = 0; i < N1; ++i) {
             const int j = column ? (i * N1 + line) : (line * N1 + i);
             const T wv = w[i] * v;
+            T x[S];
+            ldv<T, S>(ue + (j * M + k) * S, x);
 #pragma unroll
-            for (int s = 0; s < S; ++s) out[s] += wv * ue[(j * M + k) * S + s];
+            for (int s = 0; s < S; ++s) out[s] += wv * x[s];
         }
     }
 }
 
-template <typename T, int N1, int S>
+// MC, QC: the mode and z-node counts when fixed at compile time (0: taken from A).
+template <typename T, int N1, int S, int MC = 0, int QC = 0>
 __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     constexpr int NP = N1 * N1;
     constexpr int EQ = FRSG_EQ_EULER;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Q = A.Q, M = A.M, TE = A.TE;
+    const int Q = QC ? QC : A.Q, M = MC ? MC : A.M, TE = A.TE;
     const int tq = threadIdx.x, tl = threadIdx.y, te = threadIdx.z;
     const int tid = (te * N1 + tl) * Q + tq, nthr = Q * N1 * TE;
     const int nx = A.nx, ny = A.ny;
@@ -78,8 +105,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     const int ne = min(TE, nx - ex0);
     const int e0 = ey * nx + ex0;
     const int elsz = NP * M * S;
-    const T gamma = (T)A.gamma, adv = (T)A.adv;
     const T* uin = static_cast<const T*>(A.uin);
+    const StageConsts<T> sK = make_consts<T>(A);
 
     T* p = reinterpret_cast<T*>(smem_raw);
     T* sU = p; p += (size_t)(3 * TE + 2) * elsz;
@@ -113,14 +140,13 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
         sdhL[i] = tab[A.off.dhL + i];
         sdhR[i] = tab[A.off.dhR + i];
     }
-    const double dt = A.dtp ? *A.dtp : A.dt_filter;
     if (A.do_filter) {
         for (int i = tid; i < NP * NP; i += nthr) {
             sVf[i] = tab[A.off.Vf + i];
             sVfinv[i] = tab[A.off.Vfinv + i];
         }
         for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
-        load_filter_strengths<T>(A, NP, sLam, tid, nthr, dt);
+        load_filter_table<T>(A, NP, sLam, tid, nthr);
     }
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool xper = A.bc[0] == FRSG_BC_PERIODIC, yper = A.bc[2] == FRSG_BC_PERIODIC;
@@ -147,12 +173,14 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             const T* src = uin + ((size_t)eyn * nx + ex0) * elsz;
             for (int i = tid; i < ne * elsz; i += nthr) dst[i] = src[i];
         }
-        if (A.a != 0.0) {
+        if (nonzero(A.a)) {
             const T* src = ubase + (size_t)e0 * elsz;
             for (int i = tid; i < ne * elsz; i += nthr) sB[i] = src[i];
         }
     }
     __syncthreads();
+    const T gamma = sK.gamma, adv = sK.adv;
+    if (A.do_filter) finish_filter_strengths<T>(A, NP, sLam, tid, nthr, sK.adt);   // read after later barriers
 
     const bool active = te < ne;
     const int ex = ex0 + te;
@@ -168,9 +196,12 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
         for (int k = 0; k < M; ++k) {
             const T v = sVz[k * Q + tq];
 #pragma unroll
-            for (int a = 0; a < N1; ++a)
+            for (int a = 0; a < N1; ++a) {
+                T x[S];
+                ldv<T, S>(ue + ((b * N1 + a) * M + k) * S, x);
 #pragma unroll
-                for (int s = 0; s < S; ++s) u[a][s] += v * ue[((b * N1 + a) * M + k) * S + s];
+                for (int s = 0; s < S; ++s) u[a][s] += v * x[s];
+            }
         }
 #pragma unroll
         for (int a = 0; a < N1; ++a)
@@ -279,7 +310,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
         }
         face_flux<T, EQ, S, 2, 0>(nL, tL, fIL, adv, gamma, A.flux);
         face_flux<T, EQ, S, 2, 0>(tR, nR, fIR, adv, gamma, A.flux);
-        const T invJ = (T)A.invJx;
+        const T invJ = sK.invJx;
 #pragma unroll
         for (int a = 0; a < N1; ++a)
 #pragma unroll
@@ -325,7 +356,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             ghost_from_interior<T, EQ, S, 1>(A.bc[3], tT, ytop);
         face_flux<T, EQ, S, 2, 1>(ybot, tB, gIB, adv, gamma, A.flux);
         face_flux<T, EQ, S, 2, 1>(tT, ytop, gIT, adv, gamma, A.flux);
-        const T invJ = (T)A.invJy;
+        const T invJ = sK.invJy;
 #pragma unroll
         for (int b = 0; b < N1; ++b)
 #pragma unroll
@@ -339,7 +370,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     __syncthreads();
 
     // ---- projection + SSP combination
-    const T ca = (T)A.a, cb = (T)A.b, cc = (T)(A.dtp ? A.c * dt : A.c);
+    const T ca = sK.ca, cb = sK.cb, cc = sK.cc;
     T* uout = static_cast<T*>(A.uout);
     T* sTile = sU + elsz;
     const size_t gbase = (size_t)e0 * elsz;
@@ -347,22 +378,22 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
         bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
-                                         Q, tl, N1, ca, cb, cc, A.a != 0.0,
-                                         acc_term<T>(A, gbase + (size_t)te * elsz, dt));
+                                         Q, tl, N1, ca, cb, cc, sK.use_base != 0,
+                                         acc_term<T>(A, gbase + (size_t)te * elsz, sK));
     }
     if (A.do_filter) {
         __syncthreads();
         bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tl, N1,
-                                              active, true, e0, uout, gbase);
+                                              active, true, e0, uout, gbase, sK.det, M);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }
 
-template <typename T, int N1>
-cudaError_t launch2d_typed(const StageArgs& A, cudaStream_t st) {
+template <typename T, int N1, int MC, int QC>
+cudaError_t launch2d_mq(const StageArgs& A, cudaStream_t st) {
     const int TE = A.TE;
     const size_t smem = smem2d_bytes_t<T>(TE, N1, A.M, A.Q, 4);
-    auto kern = stage2d_kernel<T, N1, 4>;
+    auto kern = stage2d_kernel<T, N1, 4, MC, QC>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -371,6 +402,16 @@ cudaError_t launch2d_typed(const StageArgs& A, cudaStream_t st) {
     dim3 grid((A.nx + TE - 1) / TE, A.ny);
     kern<<<grid, block, smem, st>>>(A);
     return cudaGetLastError();
+}
+
+// P = 3 with N = 4, Q = 8 has its mode / z-node counts compiled in; other shapes run the
+// general instantiation.
+template <typename T, int N1>
+cudaError_t launch2d_typed(const StageArgs& A, cudaStream_t st) {
+    if constexpr (N1 == 4) {
+        if (A.M == 5 && A.Q == 8) return launch2d_mq<T, N1, 5, 8>(A, st);
+    }
+    return launch2d_mq<T, N1, 0, 0>(A, st);
 }
 
 template <typename T>
@@ -391,7 +432,9 @@ size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S) {
 
 cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st) {
     if (cfg.equation != FRSG_EQ_EULER) return cudaErrorInvalidValue;
-    return fp64 ? launch2d_np<double>(cfg, A, st) : launch2d_np<float>(cfg, A, st);
+    StageArgs B = A;
+    prepare_float_scalars(B);
+    return fp64 ? launch2d_np<double>(cfg, B, st) : launch2d_np<float>(cfg, B, st);
 }
 
 }  // namespace frsg
