@@ -1,10 +1,10 @@
 // Projection / combination and detector + modal filter epilogue shared by the 1D and 2D
 // stage kernels (§2.1 Eq. 6; §4.1-4.2).
 //
-// Thread layout inside an element: "k-lane" kl in [0, nk) owns the gPC modes k = kl,
-// kl + nk, ...; "m-lane" ml in [0, nm) owns the point / physical-mode rows ml, ml + nm, ...
-// Loops over points, physical modes and variables have compile-time bounds, so no index
-// is decoded by integer division.
+// Thread layout inside an element: thread lt = ml * nk + kl of the element's nk * nm threads
+// takes the (row, mode) pairs lt, lt + nk * nm, ... of its element (PairWalk), rows being
+// points or physical modes.  Loops over points, physical modes and variables have
+// compile-time bounds; the pair index is decoded by one division per element.
 //
 // The detector transforms every element to the modal basis Psi_m Phi_k with the element
 // Vandermonde inverse (§4, Eqs. 27-28, nodal = V modal), sums the squared coefficients of the
@@ -106,6 +106,24 @@ __device__ inline void finish_filter_strengths(const StageArgs& A, int NP, T* sL
     for (int i = tid; i < n; i += nthr) sLam[i] = exp(-adt * sLam[i]);
 }
 
+// Walk over the (row, mode) pairs r * M + k of an element, r < NR, by the element's nlt
+// threads: thread lt takes pairs lt, lt + nlt, ...  Consecutive threads take consecutive
+// pairs, which are consecutive coefficients in memory.  One division at the start; the step
+// (nlt = dr rows + dk modes) is added without dividing.
+struct PairWalk {
+    int r, k, dr, dk, M;
+    __device__ PairWalk(int lt, int nlt, int M_) : r(lt / M_), k(lt - (lt / M_) * M_), dr(nlt / M_),
+                                                   dk(nlt - (nlt / M_) * M_), M(M_) {}
+    __device__ void next() {
+        k += dk;
+        r += dr;
+        if (k >= M) {
+            k -= M;
+            ++r;
+        }
+    }
+};
+
 // Second output of a stage, element-offset global pointers (see StageArgs::acc_out).
 template <typename T>
 struct AccTerm {
@@ -135,8 +153,9 @@ __device__ inline bool project_combine_impl(const T* G, const T* U, const T* B, 
                                             int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
                                             const AccTerm<T>& X) {
     bool bad = false;
-    for (int k = kl; k < M; k += nk) {
-        for (int j = ml; j < NP; j += nm) {
+    for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
+        const int j = w.r, k = w.k;
+        {
             T acc[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) acc[s] = T(0);
@@ -208,16 +227,15 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
     T tot = T(0), top = T(0);
     // pass A0: modal coefficients of variable 0 for every element; its energies
     if (active) {
-        for (int k = kl; k < M; k += nk) {
-            for (int m = ml; m < NP; m += nm) {
-                T acc = T(0);
+        for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
+            const int m = w.r, k = w.k;
+            T acc = T(0);
 #pragma unroll
-                for (int j = 0; j < NP; ++j) acc += sVfinv[m * NP + j] * ue[(j * M + k) * S];
-                me[(m * M + k) * S] = acc;
-                const T v2 = acc * acc;
-                tot += v2;
-                if (sTop[m] != T(0) || k == M - 1) top += v2;
-            }
+            for (int j = 0; j < NP; ++j) acc += sVfinv[m * NP + j] * ue[(j * M + k) * S];
+            me[(m * M + k) * S] = acc;
+            const T v2 = acc * acc;
+            tot += v2;
+            if (sTop[m] != T(0) || k == M - 1) top += v2;
         }
     }
     const int lt = ml * nk + kl, nlt = nk * nm;
@@ -267,8 +285,9 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
     // pass A1: the other variables' modal coefficients, flagged elements only
     if constexpr (S > 1) {
         if (active && sFlag[te]) {
-            for (int k = kl; k < M; k += nk) {
-                for (int m = ml; m < NP; m += nm) {
+            for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
+                const int m = w.r, k = w.k;
+                {
                     T acc[S];
 #pragma unroll
                     for (int s = 1; s < S; ++s) acc[s] = T(0);
@@ -296,8 +315,9 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
             c2 = table_block<T>(A)[A.off.lc + 1];
         }
         T* dst = uout + gbase + (size_t)te * elsz;
-        for (int k = kl; k < M; k += nk) {
-            for (int j = ml; j < NP; j += nm) {
+        for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
+            const int j = w.r, k = w.k;
+            {
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     T val;

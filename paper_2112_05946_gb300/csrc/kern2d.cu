@@ -7,9 +7,9 @@
 // and stage:
 //   a2  u(r_a, s_b, z_q) = sum_k Phi_k(z_q) uhat_(b,a),k          (§2.1, Eq. 2)
 //   a5  traces on the four faces by ell(+-1) along rows / columns (§3.3)
-//   a6  LLF fluxes on x-faces (f, |v_x| + c) and y-faces (g, |v_y| + c); one coalesced
-//       sweep loads the tile, its two x-neighbours and the rows of elements below and
-//       above it, so every neighbour trace is computed from shared memory
+//   a6  interface fluxes on x-faces (f) and y-faces (g); one sweep loads the tile and reduces
+//       the facing rows / columns of the x-neighbours and of the elements below and above
+//       straight from global memory to modal face traces, which each z-node evaluates
 //   a3/a7 total-flux derivative per direction with the 1D Radau correction along each
 //       line (§3.5, Eq. 24, minus sign of Eq. 12): -(1/Jx) df/dr - (1/Jy) dg/ds
 //   a4  projection of the nodal residual onto the modes (§2.1, Eq. 6)
@@ -28,7 +28,8 @@ template <typename T>
 __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int S) {
     const int Np = n1 * n1;
     size_t n = 0;
-    n += (size_t)(3 * TE + 2) * Np * M * S; // U: x-halo + tile, row below, row above (tile later the new state)
+    n += (size_t)TE * Np * M * S;           // U: the tile (later the new state)
+    n += (size_t)(2 + 2 * TE) * n1 * M * S; // modal face traces of the neighbours (x-halo, below, above)
     n += (size_t)TE * Np * M * S;           // B: SSP base state of the tile
     n += (size_t)TE * Np * S * Q;           // Un (nodal values)
     n += (size_t)TE * Np * S * (Q > M ? Q : M);   // G (nodal residual, later the modal coefficients)
@@ -69,24 +70,18 @@ __device__ __forceinline__ void ldv(const T* p, T (&o)[S]) {
     }
 }
 
-// Trace of element `e` at z-node q along a line: sum over the n1 points of the line of
-// w[i] * sum_k Phi_k(z_q) uhat[point(i)][k][s].  Row line (fixed b) or column (fixed a).
-template <typename T, int N1, int S>
-__device__ inline void line_trace(const T* ue, int M, const T* Vzq_stride, int Q, const T* w, bool column, int line,
-                                  T (&out)[S]) {
+// A neighbour's trace at z-node q from its modal face trace ft [k][s] (one line of a face):
+// sum_k Phi_k(z_q) ft[k][s].
+template <typename T, int S>
+__device__ inline void face_eval(const T* ft, int M, const T* Vzq_stride, int Q, T (&out)[S]) {
 #pragma unroll
     for (int s = 0; s < S; ++s) out[s] = T(0);
     for (int k = 0; k < M; ++k) {
         const T v = Vzq_stride[k * Q];
+        T x[S];
+        ldv<T, S>(ft + k * S, x);
 #pragma unroll
-        for (int i = 0; i < N1; ++i) {
-            const int j = column ? (i * N1 + line) : (line * N1 + i);
-            const T wv = w[i] * v;
-            T x[S];
-            ldv<T, S>(ue + (j * M + k) * S, x);
-#pragma unroll
-            for (int s = 0; s < S; ++s) out[s] += wv * x[s];
-        }
+        for (int s = 0; s < S; ++s) out[s] += v * x[s];
     }
 }
 
@@ -109,7 +104,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     const StageConsts<T> sK = make_consts<T>(A);
 
     T* p = reinterpret_cast<T*>(smem_raw);
-    T* sU = p; p += (size_t)(3 * TE + 2) * elsz;
+    T* sU = p; p += (size_t)TE * elsz;
+    T* sFT = p; p += (size_t)(2 + 2 * TE) * N1 * M * S;   // [face][line][k][s]
     T* sB = p; p += (size_t)TE * elsz;
     T* sUn = p; p += (size_t)TE * NP * S * Q;
     T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
@@ -151,27 +147,49 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool xper = A.bc[0] == FRSG_BC_PERIODIC, yper = A.bc[2] == FRSG_BC_PERIODIC;
     {
-        // slots 0..ne+1: left neighbour, tile, right neighbour (row ey);
-        // slots TE+2..TE+1+ne: row below; slots 2TE+2..2TE+1+ne: row above
+        // the tile, and the neighbours' modal face traces straight from global memory: face 0
+        // the right face (r = +1) of the left neighbour, face 1 the left face of the right
+        // neighbour, faces 2 + 2 te + side the top face of the element below (side 0) and the
+        // bottom face of the element above (side 1) element te; [line][k][s] with line = row b
+        // (x faces) or column a (y faces): sum over the other index of ell(+-1) uhat
         const int nl = ex0 - 1, nr = ex0 + ne;
         const bool hasL = nl >= 0 || xper, hasR = nr < nx || xper;
-        const T* srcL = uin + ((size_t)ey * nx + (nl < 0 ? nx - 1 : nl)) * elsz;
-        const T* srcR = uin + ((size_t)ey * nx + (nr >= nx ? 0 : nr)) * elsz;
-        for (int i = tid; i < elsz; i += nthr) {
-            if (hasL) sU[i] = srcL[i];
-            if (hasR) sU[(ne + 1) * elsz + i] = srcR[i];
-        }
         const T* srcT = uin + (size_t)e0 * elsz;
-        for (int i = tid; i < ne * elsz; i += nthr) sU[elsz + i] = srcT[i];
-        for (int side = 0; side < 2; ++side) {
-            int eyn = side == 0 ? ey - 1 : ey + 1;
-            if (eyn < 0 || eyn >= ny) {
-                if (!yper) continue;
-                eyn = eyn < 0 ? ny - 1 : 0;
+        for (int i = tid; i < ne * elsz; i += nthr) sU[i] = srcT[i];
+        const int fpairs = N1 * M;
+        for (int idx = tid; idx < (2 + 2 * ne) * fpairs; idx += nthr) {
+            const int f = idx / fpairs, r = idx - f * fpairs;
+            const int line = r / M, k = r - line * M;
+            long long nb = -1;
+            bool xdir = true, plus = true;
+            if (f == 0) {
+                if (hasL) nb = (long long)ey * nx + (nl < 0 ? nx - 1 : nl);
+            } else if (f == 1) {
+                if (hasR) nb = (long long)ey * nx + (nr >= nx ? 0 : nr);
+                plus = false;
+            } else {
+                const int tf = (f - 2) >> 1, side = (f - 2) & 1;
+                int eyn = side == 0 ? ey - 1 : ey + 1;
+                if (eyn < 0 || eyn >= ny) eyn = yper ? (eyn < 0 ? ny - 1 : 0) : -1;
+                if (eyn >= 0) nb = (long long)eyn * nx + ex0 + tf;
+                xdir = false;
+                plus = side == 0;
             }
-            T* dst = sU + (size_t)(TE + 2 + side * TE) * elsz;
-            const T* src = uin + ((size_t)eyn * nx + ex0) * elsz;
-            for (int i = tid; i < ne * elsz; i += nthr) dst[i] = src[i];
+            if (nb < 0) continue;
+            const T* w = tab + (plus ? A.off.lp : A.off.lm);
+            const T* un = uin + (size_t)nb * elsz;
+            T acc[S];
+#pragma unroll
+            for (int q = 0; q < S; ++q) acc[q] = T(0);
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                const int pt = xdir ? line * N1 + i : i * N1 + line;
+                const T wi = w[i];
+#pragma unroll
+                for (int q = 0; q < S; ++q) acc[q] += wi * un[(pt * M + k) * S + q];
+            }
+#pragma unroll
+            for (int q = 0; q < S; ++q) sFT[((f * N1 + line) * M + k) * S + q] = acc[q];
         }
         if (nonzero(A.a)) {
             const T* src = ubase + (size_t)e0 * elsz;
@@ -187,7 +205,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     T u[N1][S];                     // row b = tl: values at (a, b), a = 0..N1-1
     T ybot[S], ytop[S];             // column a = tl: neighbours' facing traces (y)
     if (active) {
-        const T* ue = sU + (te + 1) * elsz;
+        const T* ue = sU + te * elsz;
         const int b = tl;
 #pragma unroll
         for (int a = 0; a < N1; ++a)
@@ -231,8 +249,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             const int bc = side == 0 ? A.bc[0] : A.bc[1];
             T g[S];
             if ((nbx >= 0 && nbx < nx) || xper) {
-                const T* un = sU + (size_t)(side == 0 ? 0 : ne + 1) * elsz;
-                line_trace<T, N1, S>(un, M, sVz + tq, Q, side == 0 ? slp : slm, false, b, g);
+                face_eval<T, S>(sFT + (size_t)(side * N1 + b) * M * S, M, sVz + tq, Q, g);
             } else if (bc == FRSG_BC_DIRICHLET) {
                 const double* gh = A.ghost + (size_t)side * M * S;
 #pragma unroll
@@ -260,8 +277,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             const int bc = side == 0 ? A.bc[2] : A.bc[3];
             T g[S];
             if ((nby >= 0 && nby < ny) || yper) {
-                const T* un = sU + (size_t)(TE + 2 + side * TE + te) * elsz;
-                line_trace<T, N1, S>(un, M, sVz + tq, Q, side == 0 ? slp : slm, true, a, g);
+                face_eval<T, S>(sFT + (size_t)(((2 + 2 * te + side) * N1) + a) * M * S, M, sVz + tq, Q, g);
             } else if (bc == FRSG_BC_DIRICHLET) {
                 const double* gh = A.ghost + (size_t)(2 + side) * M * S;
 #pragma unroll
@@ -372,7 +388,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     // ---- projection + SSP combination
     const T ca = sK.ca, cb = sK.cb, cc = sK.cc;
     T* uout = static_cast<T*>(A.uout);
-    T* sTile = sU + elsz;
+    T* sTile = sU;
     const size_t gbase = (size_t)e0 * elsz;
     bool bad = false;
     if (active) {
