@@ -106,6 +106,24 @@ struct LimitArgs {
     int TE;
 };
 
+// Launch with programmatic stream serialization allowed (the kernel calls pdl_trigger /
+// pdl_wait, see epilogue.cuh): the launch may begin while the previous kernel in the stream
+// finishes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kern, args...);
+}
+
 // Launch wrappers (kern1d.cu / kern2d.cu / kmisc.cu).  Return cudaGetLastError().
 cudaError_t launch_stage1d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st);
 cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st);

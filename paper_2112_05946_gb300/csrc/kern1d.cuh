@@ -54,6 +54,7 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     const T* uin = static_cast<const T*>(A.uin);
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool periodic = A.bc[0] == FRSG_BC_PERIODIC;
+    pdl_trigger();
     const StageConsts<T> sK = make_consts<T>(A);
 
     T* p = reinterpret_cast<T*>(smem_raw);
@@ -96,6 +97,7 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
         for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
         load_filter_table<T>(A, NP, sLam, tid, nthr);
     }
+    pdl_wait();
     {
         // slot 0: left neighbour, slots 1..ne: the tile, slot ne+1: right neighbour
         // (neighbours wrap when periodic and are absent at a physical boundary)
@@ -274,6 +276,7 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     const T* uin = static_cast<const T*>(A.uin);
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool periodic = A.bc[0] == FRSG_BC_PERIODIC;
+    pdl_trigger();
     const StageConsts<T> sK = make_consts<T>(A);
 
     T* p = reinterpret_cast<T*>(smem_raw);
@@ -316,6 +319,7 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
         for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
         load_filter_table<T>(A, NP, sLam, tid, nthr);
     }
+    pdl_wait();
     const int nl = e0 - 1, nr = e0 + ne;
     const bool hasL = nl >= 0 || periodic, hasR = nr < E || periodic;
     {
@@ -544,8 +548,7 @@ cudaError_t launch_mq(const StageArgs& A, cudaStream_t st) {
         }
         dim3 block(A.Q, NP, TE);
         dim3 grid((A.E + TE - 1) / TE);
-        kern<<<grid, block, smem, st>>>(A);
-        return cudaGetLastError();
+        return launch_pdl(kern, grid, block, smem, st, A);
     }
     const size_t smem = smem1d_bytes<T>(TE, NP, A.M, A.Q, S);
     auto kern = stage1d_kernel<T, NP, S, EQ, MC, QC>;
@@ -555,8 +558,7 @@ cudaError_t launch_mq(const StageArgs& A, cudaStream_t st) {
     }
     dim3 block(A.Q, TE);
     dim3 grid((A.E + TE - 1) / TE);
-    kern<<<grid, block, smem, st>>>(A);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, block, smem, st, A);
 }
 
 // Shapes with the mode / z-node counts compiled in (loops fully unrolled, index arithmetic

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     const int e0 = ey * nx + ex0;
     const int elsz = NP * M * S;
     const T* uin = static_cast<const T*>(A.uin);
+    pdl_trigger();
     const StageConsts<T> sK = make_consts<T>(A);
 
     T* p = reinterpret_cast<T*>(smem_raw);
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     }
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool xper = A.bc[0] == FRSG_BC_PERIODIC, yper = A.bc[2] == FRSG_BC_PERIODIC;
+    pdl_wait();
     {
         // the tile, and the neighbours' modal face traces straight from global memory: face 0
         // the right face (r = +1) of the left neighbour, face 1 the left face of the right
@@ -416,8 +418,7 @@ cudaError_t launch2d_mq(const StageArgs& A, cudaStream_t st) {
     }
     dim3 block(A.Q, N1, TE);
     dim3 grid((A.nx + TE - 1) / TE, A.ny);
-    kern<<<grid, block, smem, st>>>(A);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, block, smem, st, A);
 }
 
 // P = 3 with N = 4, Q = 8 has its mode / z-node counts compiled in; other shapes run the
