@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "pdl.cuh"
 #include "physics.cuh"
 
 namespace frsg {
@@ -29,14 +30,6 @@ template <>
 __device__ inline const double* table_block<double>(const StageArgs& A) { return A.tab; }
 template <>
 __device__ inline const float* table_block<float>(const StageArgs& A) { return A.tabf; }
-
-// Programmatic dependent launch: a stage kernel lets the next launch in its stream start as
-// soon as all of its CTAs are running (launch_dependents), and waits for the previous kernel's
-// completion and memory (wait) only before it touches the state.  Everything before the wait
-// reads launch-invariant data (tables, scalars, dt written before the launch); all global
-// writes come after it.  Without a programmatic dependency both instructions are no-ops.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // The launch's scalars in the kernel's precision.  Float kernels take the float copies the
 // host prepared (prepare_float_scalars) and convert only dt, once per thread; double-typed

@@ -5,6 +5,7 @@
 
 #include "internal.h"
 #include "limiter.cuh"
+#include "pdl.cuh"
 #include "physics.cuh"
 
 namespace frsg {
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
     const int tq = threadIdx.x, te = threadIdx.y;
     const int e = blockIdx.x * TE + te;
     const bool active = e < A.E;
+    pdl_trigger();
     double* red = lsm;                                    // [TE][Q][2]
     double* el = red + (size_t)TE * Q * 2;                // [TE][4]: rho_min, p_min, beta1, beta2
     int* cand = reinterpret_cast<int*>(el + (size_t)TE * 4);   // [TE]
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
     }
 
     const bool exact = sizeof(T) == sizeof(double);
+    pdl_wait();
     if (active) {
         const T* ue = u + (size_t)e * elsz;
         // screen in T: element mean, nodal values at the solution points, every limiter point
@@ -322,8 +325,7 @@ cudaError_t limit_typed(const LimitArgs& A, cudaStream_t st) {
     auto kern = limit_kernel<T, N1, DIM, S>;
     dim3 block(A.Q, A.TE);
     dim3 grid((A.E + A.TE - 1) / A.TE);
-    kern<<<grid, block, smem, st>>>(A);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, block, smem, st, A);
 }
 
 template <typename T>
