@@ -148,8 +148,9 @@ frsg_status fr_sg_get_state(frsg_ctx* ctx, double* uhat, int where);
  * z-evaluation (§2.1, Eq. 2), flux (§3.2, Eq. 15), Galerkin projection (Eq. 6), face
  * interpolation and the interface flux (LLF or HLL, §3.3), total-flux derivative
  * with the Radau correction (§3.4, Eq. 21; 2D §3.5, Eq. 24).  u and dudt: DEVICE arrays
- * [E][Np][M][S] in the context's precision; they must not overlap.  Boundary ghost
- * states come from the context. */
+ * [E][Np][M][S] in the context's precision, 16-byte aligned (FRSG_E_INVAL otherwise: the
+ * kernels move four-variable states with vector loads and stores); they must not overlap.
+ * Boundary ghost states come from the context. */
 frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt);
 
 /* Advance the context's state by nsteps steps of size dt of the SSP-RK3 scheme, each

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -753,6 +754,8 @@ frsg_status fr_sg_get_state(frsg_ctx* ctx, double* uhat, int where) {
 frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt) {
     if (!ctx) return FRSG_E_INVAL;
     if (!u || !dudt || u == dudt) return fail(ctx, FRSG_E_INVAL, "rhs needs distinct, non-null buffers");
+    if ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(dudt)) % 16 != 0)
+        return fail(ctx, FRSG_E_INVAL, "rhs buffers must be 16-byte aligned");
     StageArgs A = base_args(ctx);
     A.uin = u;
     A.ubase = nullptr;

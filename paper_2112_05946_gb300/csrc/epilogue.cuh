@@ -107,6 +107,44 @@ __device__ inline void finish_filter_strengths(const StageArgs& A, int NP, T* sL
     for (int i = tid; i < n; i += nthr) sLam[i] = exp(-adt * sLam[i]);
 }
 
+// The S consecutive variables at p: one 16-byte load per 4 floats (2 per 4 doubles) when
+// S = 4 (every offset used is a multiple of 4 elements from a 16-byte aligned base, in shared
+// memory or in the state arrays); element by element otherwise.
+template <typename T, int S>
+__device__ __forceinline__ void ldv(const T* p, T (&o)[S]) {
+    if constexpr (S == 4 && sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    } else if constexpr (S == 4 && sizeof(T) == 8) {
+        const double2 v0 = *reinterpret_cast<const double2*>(p);
+        const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = v0.x;
+        o[1] = v0.y;
+        o[2] = v1.x;
+        o[3] = v1.y;
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) o[s] = p[s];
+    }
+}
+
+// Store counterpart of ldv.
+template <typename T, int S>
+__device__ __forceinline__ void stv(T* p, const T (&o)[S]) {
+    if constexpr (S == 4 && sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (S == 4 && sizeof(T) == 8) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) p[s] = o[s];
+    }
+}
+
 // Walk over the (row, mode) pairs r * M + k of an element, r < NR, by the element's nlt
 // threads: thread lt takes pairs lt, lt + nlt, ...  Consecutive threads take consecutive
 // pairs, which are consecutive coefficients in memory.  One division at the start; the step
@@ -147,11 +185,13 @@ __device__ inline AccTerm<T> acc_term(const StageArgs& A, size_t off, const Stag
 }
 
 // a4 + a8 for one element: uhat_new[j][k][s] = cb*U + cc*sum_q Pz[k][q] G[j][s][q] + ca*B.
-// G is the element's nodal residual [NP][S][Q]; U, B its stage input and SSP base [NP][M][S].
+// G is the element's nodal residual [NP][S][Q] with row stride gr >= S*Q per point (padded
+// so that threads on different points hit different banks); U, B its stage input and SSP
+// base [NP][M][S].
 // Writes the result to dst (shared memory or global), and the accumulator X if ACC.
 template <typename T, int NP, int S, bool ACC>
-__device__ inline bool project_combine_impl(const T* G, const T* U, const T* B, const T* sPz, T* dst, int M, int Q,
-                                            int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
+__device__ inline bool project_combine_impl(const T* G, int gr, const T* U, const T* B, const T* sPz, T* dst, int M,
+                                            int Q, int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
                                             const AccTerm<T>& X) {
     bool bad = false;
     for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
@@ -160,24 +200,32 @@ __device__ inline bool project_combine_impl(const T* G, const T* U, const T* B, 
             T acc[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) acc[s] = T(0);
-            const T* g = G + j * S * Q;
+            const T* g = G + j * gr;
             for (int q = 0; q < Q; ++q) {
                 const T pz = sPz[k * Q + q];
 #pragma unroll
                 for (int s = 0; s < S; ++s) acc[s] += pz * g[s * Q + q];
             }
+            const int o = (j * M + k) * S;
+            T uo[S], val[S];
+            ldv<T, S>(U + o, uo);           // dst may alias U (in-place tile update)
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int o = (j * M + k) * S + s;
-                const T uo = U[o];          // dst may alias U (in-place tile update)
-                T val = cb * uo + cc * acc[s];
-                if (use_base) val += ca * B[o];
-                dst[o] = val;
-                bad |= !finite_val(val);
-                if constexpr (ACC) {
-                    T w = X.b * uo + X.c * acc[s];
-                    if (X.src) w += X.a * X.src[o];
-                    X.dst[o] = w;
+            for (int s = 0; s < S; ++s) val[s] = cb * uo[s] + cc * acc[s];
+            if (use_base) {
+                T bo[S];
+                ldv<T, S>(B + o, bo);
+#pragma unroll
+                for (int s = 0; s < S; ++s) val[s] += ca * bo[s];
+            }
+            stv<T, S>(dst + o, val);
+#pragma unroll
+            for (int s = 0; s < S; ++s) bad |= !finite_val(val[s]);
+            if constexpr (ACC) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    T w = X.b * uo[s] + X.c * acc[s];
+                    if (X.src) w += X.a * X.src[o + s];
+                    X.dst[o + s] = w;
                 }
             }
         }
@@ -186,12 +234,14 @@ __device__ inline bool project_combine_impl(const T* G, const T* U, const T* B, 
 }
 
 template <typename T, int NP, int S>
-__device__ inline bool project_combine(const T* G, const T* U, const T* B, const T* sPz, T* dst, int M, int Q, int kl,
-                                       int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
+__device__ inline bool project_combine(const T* G, int gr, const T* U, const T* B, const T* sPz, T* dst, int M, int Q,
+                                       int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
                                        const AccTerm<T>& X) {
     if (X.dst)
-        return project_combine_impl<T, NP, S, true>(G, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base, X);
-    return project_combine_impl<T, NP, S, false>(G, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base, X);
+        return project_combine_impl<T, NP, S, true>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base,
+                                                    X);
+    return project_combine_impl<T, NP, S, false>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base,
+                                                 X);
 }
 
 // One Lasso-filtered nodal coefficient (§4.1.3) of a 1D element from its modal coefficients
@@ -318,23 +368,28 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
         T* dst = uout + gbase + (size_t)te * elsz;
         for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
             const int j = w.r, k = w.k;
-            {
+            const int o = (j * M + k) * S;
+            T val[S];
+            if (flag && lasso) {
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    T val;
-                    if (flag && lasso) {
-                        val = lasso_value<T, NP, S>(me, sVf, sLam, j, k, s, M, c1, c2);
-                    } else if (flag) {
-                        val = T(0);
+                for (int s = 0; s < S; ++s) val[s] = lasso_value<T, NP, S>(me, sVf, sLam, j, k, s, M, c1, c2);
+            } else if (flag) {
 #pragma unroll
-                        for (int m = 0; m < NP; ++m) val += sVf[j * NP + m] * sLam[m * M + k] * me[(m * M + k) * S + s];
-                    } else {
-                        val = ue[(j * M + k) * S + s];
-                    }
-                    dst[(j * M + k) * S + s] = val;
-                    bad |= !finite_val(val);
+                for (int s = 0; s < S; ++s) val[s] = T(0);
+#pragma unroll
+                for (int m = 0; m < NP; ++m) {
+                    const T wv = sVf[j * NP + m] * sLam[m * M + k];
+                    T x[S];
+                    ldv<T, S>(me + (m * M + k) * S, x);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) val[s] += wv * x[s];
                 }
+            } else {
+                ldv<T, S>(ue + o, val);
             }
+            stv<T, S>(dst + o, val);
+#pragma unroll
+            for (int s = 0; s < S; ++s) bad |= !finite_val(val[s]);
         }
     }
     return bad;

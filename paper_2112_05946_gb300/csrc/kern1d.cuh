@@ -33,7 +33,7 @@ __host__ __device__ inline size_t smem1d_bytes(int TE, int NP, int M, int Q, int
     size_t n = 0;
     n += (size_t)(TE + 2) * NP * M * S;              // U: halo + tile coefficients (tile later the new state)
     n += (size_t)TE * NP * M * S;                    // B: SSP base state of the tile
-    n += (size_t)TE * NP * S * (Q > M ? Q : M);      // G: nodal residual, later the modal coefficients
+    n += (size_t)TE * NP * (S * (Q > M ? Q : M) + 1);   // G: nodal residual (rows padded), later modal coefficients
     n += (size_t)(TE + 2) * 2 * S * Q;               // Tr: face traces [slot][side][s][q]
     n += 2 * (size_t)M * Q;                          // Vz, Pz
     n += (size_t)NP * NP + 4 * NP;                   // D, lm, lp, dhL, dhR
@@ -60,7 +60,8 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     T* p = reinterpret_cast<T*>(smem_raw);
     T* sU = p; p += (size_t)(TE + 2) * elsz;
     T* sB = p; p += (size_t)TE * elsz;
-    T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
+    const int GR = S * Q + (sizeof(T) == 4 ? 1 : 0);   // row stride of the nodal residual (float: padded)
+    T* sG = p; p += (size_t)TE * NP * (S * (Q > M ? Q : M) + 1);
     T* sTr = p; p += (size_t)(TE + 2) * 2 * S * Q;
     T* sVz = p; p += M * Q;
     T* sPz = p; p += M * Q;
@@ -220,7 +221,7 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
                 T d = (fIL[s] - fDL[s]) * sdhL[j] + (fIR[s] - fDR[s]) * sdhR[j];
 #pragma unroll
                 for (int m = 0; m < NP; ++m) d += sD[j * NP + m] * f[m][s];
-                sG[((te * NP + j) * S + s) * Q + tq] = -invJ * d;
+                sG[(te * NP + j) * GR + s * Q + tq] = -invJ * d;
             }
     }
     __syncthreads();
@@ -233,7 +234,7 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     bool bad = false;
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
-        bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
+        bad |= project_combine<T, NP, S>(sG + te * NP * GR, GR, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
                                          Q, 0, 1, ca, cb, cc, sK.use_base != 0,
                                          acc_term<T>(A, gbase + (size_t)te * elsz, sK));
     }
@@ -255,7 +256,7 @@ __host__ __device__ inline size_t smem1d_wide_bytes(int TE, int NP, int M, int Q
     n += (size_t)TE * NP * M * S;                    // B: SSP base
     n += (size_t)(TE + 2) * NP * S * Q;              // Un: nodal values (halo + tile)
     n += (size_t)TE * NP * S * Q;                    // F: nodal fluxes (tile)
-    n += (size_t)TE * NP * S * (Q > M ? Q : M);      // G: nodal residual, later modal coefficients
+    n += (size_t)TE * NP * (S * (Q > M ? Q : M) + 1);   // G: nodal residual (rows padded), later modal coefficients
     n += 2 * (size_t)M * Q;                          // Vz, Pz
     n += (size_t)NP * NP + 4 * NP;                   // D, lm, lp, dhL, dhR
     n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;  // Vf, Vfinv, Lam, Top
@@ -284,7 +285,8 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     T* sB = p; p += (size_t)TE * elsz;
     T* sUn = p; p += (size_t)(TE + 2) * nsz;
     T* sF = p; p += (size_t)TE * nsz;
-    T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
+    const int GR = S * Q + (sizeof(T) == 4 ? 1 : 0);   // row stride of the nodal residual (float: padded)
+    T* sG = p; p += (size_t)TE * NP * (S * (Q > M ? Q : M) + 1);
     T* sVz = p; p += M * Q;
     T* sPz = p; p += M * Q;
     T* sD = p; p += NP * NP;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
             T d = (fIL[s] - fDL[s]) * sdhL[tj] + (fIR[s] - fDR[s]) * sdhR[tj];
 #pragma unroll
             for (int m = 0; m < NP; ++m) d += sD[tj * NP + m] * fown[(m * S + s) * Q + tq];
-            sG[((te * NP + tj) * S + s) * Q + tq] = -invJ * d;
+            sG[(te * NP + tj) * GR + s * Q + tq] = -invJ * d;
         }
     }
     __syncthreads();
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     bool bad = false;
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
-        bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
+        bad |= project_combine<T, NP, S>(sG + te * NP * GR, GR, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
                                          Q, tj, NP, ca, cb, cc, sK.use_base != 0,
                                          acc_term<T>(A, gbase + (size_t)te * elsz, sK));
     }

@@ -32,7 +32,7 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
     n += (size_t)(2 + 2 * TE) * n1 * M * S; // modal face traces of the neighbours (x-halo, below, above)
     n += (size_t)TE * Np * M * S;           // B: SSP base state of the tile
     n += (size_t)TE * Np * S * Q;           // Un (nodal values)
-    n += (size_t)TE * Np * S * (Q > M ? Q : M);   // G (nodal residual, later the modal coefficients)
+    n += (size_t)TE * Np * (S * (Q > M ? Q : M) + 1);   // G (nodal residual, rows padded; later modal coefficients)
     n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][s][q]
     n += 2 * (size_t)M * Q;                 // Vz, Pz
     n += (size_t)n1 * n1 + 4 * n1;          // D, lm, lp, dhL, dhR
@@ -44,30 +44,6 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
 template <typename T>
 size_t smem2d_bytes_t(int TE, int n1, int M, int Q, int S) {
     return smem2d_elems<T>(TE, n1, M, Q, S) * sizeof(T) + (size_t)TE * sizeof(int) + 16;
-}
-
-// The S consecutive variables at p; one 16-byte shared-memory load per 4 floats (2 per 4
-// doubles) when S = 4 (the offsets used here are multiples of 4 elements from a 16-byte
-// aligned base).
-template <typename T, int S>
-__device__ __forceinline__ void ldv(const T* p, T (&o)[S]) {
-    if constexpr (S == 4 && sizeof(T) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        o[0] = v.x;
-        o[1] = v.y;
-        o[2] = v.z;
-        o[3] = v.w;
-    } else if constexpr (S == 4 && sizeof(T) == 8) {
-        const double2 v0 = *reinterpret_cast<const double2*>(p);
-        const double2 v1 = *reinterpret_cast<const double2*>(p + 2);
-        o[0] = v0.x;
-        o[1] = v0.y;
-        o[2] = v1.x;
-        o[3] = v1.y;
-    } else {
-#pragma unroll
-        for (int s = 0; s < S; ++s) o[s] = p[s];
-    }
 }
 
 // A neighbour's trace at z-node q from its modal face trace ft [k][s] (one line of a face):
@@ -109,7 +85,8 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     T* sFT = p; p += (size_t)(2 + 2 * TE) * N1 * M * S;   // [face][line][k][s]
     T* sB = p; p += (size_t)TE * elsz;
     T* sUn = p; p += (size_t)TE * NP * S * Q;
-    T* sG = p; p += (size_t)TE * NP * S * (Q > M ? Q : M);
+    const int GR = S * Q + (sizeof(T) == 4 ? 1 : 0);   // row stride of the nodal residual (float: padded)
+    T* sG = p; p += (size_t)TE * NP * (S * (Q > M ? Q : M) + 1);
     T* sTx = p; p += (size_t)(TE + 2) * 2 * N1 * S * Q;
     T* sVz = p; p += M * Q;
     T* sPz = p; p += M * Q;
@@ -336,7 +313,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
                 T d = (fIL[s] - fDL[s]) * sdhL[a] + (fIR[s] - fDR[s]) * sdhR[a];
 #pragma unroll
                 for (int m = 0; m < N1; ++m) d += sD[a * N1 + m] * f[m][s];
-                sG[((te * NP + b * N1 + a) * S + s) * Q + tq] = -invJ * d;
+                sG[(te * NP + b * N1 + a) * GR + s * Q + tq] = -invJ * d;
             }
     }
     __syncthreads();
@@ -382,7 +359,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
                 T d = (gIB[s] - gDB[s]) * sdhL[b] + (gIT[s] - gDT[s]) * sdhR[b];
 #pragma unroll
                 for (int m = 0; m < N1; ++m) d += sD[b * N1 + m] * g[m][s];
-                sG[((te * NP + b * N1 + a) * S + s) * Q + tq] -= invJ * d;
+                sG[(te * NP + b * N1 + a) * GR + s * Q + tq] -= invJ * d;
             }
     }
     __syncthreads();
@@ -395,7 +372,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     bool bad = false;
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
-        bad |= project_combine<T, NP, S>(sG + te * NP * S * Q, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
+        bad |= project_combine<T, NP, S>(sG + te * NP * GR, GR, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
                                          Q, tl, N1, ca, cb, cc, sK.use_base != 0,
                                          acc_term<T>(A, gbase + (size_t)te * elsz, sK));
     }
