@@ -32,8 +32,8 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
     n += (size_t)(2 + 2 * TE) * n1 * M * S; // modal face traces of the neighbours (x-halo, below, above)
     n += (size_t)TE * Np * M * S;           // B: SSP base state of the tile
     n += (size_t)TE * Np * S * Q;           // Un (nodal values)
-    n += (size_t)TE * Np * (S * (Q > M ? Q : M) + 1);   // G (nodal residual, rows padded; later modal coefficients)
-    n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][s][q]
+    n += ((size_t)TE * Np * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;   // G (nodal residual, rows padded; later modal coefficients)
+    n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][q][s]
     n += 2 * (size_t)M * Q;                 // Vz, Pz
     n += (size_t)n1 * n1 + 4 * n1;          // D, lm, lp, dhL, dhR
     n += 2 * (size_t)Np * Np + (size_t)Np * M + Np;   // Vf, Vfinv, Lam, Top
@@ -84,10 +84,10 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     T* sU = p; p += (size_t)TE * elsz;
     T* sFT = p; p += (size_t)(2 + 2 * TE) * N1 * M * S;   // [face][line][k][s]
     T* sB = p; p += (size_t)TE * elsz;
-    T* sUn = p; p += (size_t)TE * NP * S * Q;
+    T* sUn = p; p += (size_t)TE * NP * S * Q;            // [te][point][q][s]
     const int GR = S * Q + (sizeof(T) == 4 ? 1 : 0);   // row stride of the nodal residual (float: padded)
-    T* sG = p; p += (size_t)TE * NP * (S * (Q > M ? Q : M) + 1);
-    T* sTx = p; p += (size_t)(TE + 2) * 2 * N1 * S * Q;
+    T* sG = p; p += ((size_t)TE * NP * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;
+    T* sTx = p; p += (size_t)(TE + 2) * 2 * N1 * S * Q;  // [row][side][line][q][s]
     T* sVz = p; p += M * Q;
     T* sPz = p; p += M * Q;
     T* sD = p; p += N1 * N1;
@@ -181,6 +181,12 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
 
     const bool active = te < ne;
     const int ex = ex0 + te;
+    // the S variables of one (point, z-node) sit together, consecutive z-nodes in consecutive
+    // vectors: one vector access per thread, conflict-free across the lines of a warp
+    auto un_at = [&](int pt) { return sUn + ((size_t)(te * NP + pt) * Q + tq) * S; };
+    auto tx_at = [&](int row, int side, int line) {
+        return sTx + ((size_t)((row * 2 + side) * N1 + line) * Q + tq) * S;
+    };
     T u[N1][S];                     // row b = tl: values at (a, b), a = 0..N1-1
     T ybot[S], ytop[S];             // column a = tl: neighbours' facing traces (y)
     if (active) {
@@ -201,9 +207,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             }
         }
 #pragma unroll
-        for (int a = 0; a < N1; ++a)
-#pragma unroll
-            for (int s = 0; s < S; ++s) sUn[((te * NP + b * N1 + a) * S + s) * Q + tq] = u[a][s];
+        for (int a = 0; a < N1; ++a) stv<T, S>(un_at(b * N1 + a), u[a]);
         // own x-traces on row b
         T tL[S], tR[S];
 #pragma unroll
@@ -216,9 +220,9 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             }
             tL[s] = l;
             tR[s] = r;
-            sTx[((((te + 1) * 2 + 0) * N1 + b) * S + s) * Q + tq] = l;
-            sTx[((((te + 1) * 2 + 1) * N1 + b) * S + s) * Q + tq] = r;
         }
+        stv<T, S>(tx_at(te + 1, 0, b), tL);
+        stv<T, S>(tx_at(te + 1, 1, b), tR);
         // x-halo on row b
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
@@ -245,8 +249,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             }
             const int row = side == 0 ? 0 : ne + 1;
             const int nside = side == 0 ? 1 : 0;
-#pragma unroll
-            for (int s = 0; s < S; ++s) sTx[(((row * 2 + nside) * N1 + b) * S + s) * Q + tq] = g[s];
+            stv<T, S>(tx_at(row, nside, b), g);
         }
         // y-neighbours' facing traces on column a = tl (ghosts of walls are formed later)
         const int a = tl;
@@ -300,9 +303,9 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             fDR[s] = r;
             tL[s] = ul;
             tR[s] = ur;
-            nL[s] = sTx[(((te * 2 + 1) * N1 + b) * S + s) * Q + tq];
-            nR[s] = sTx[((((te + 2) * 2 + 0) * N1 + b) * S + s) * Q + tq];
         }
+        ldv<T, S>(tx_at(te, 1, b), nL);
+        ldv<T, S>(tx_at(te + 2, 0, b), nR);
         face_flux<T, EQ, S, 2, 0>(nL, tL, fIL, adv, gamma, A.flux);
         face_flux<T, EQ, S, 2, 0>(tR, nR, fIR, adv, gamma, A.flux);
         const T invJ = sK.invJx;
@@ -323,9 +326,7 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
         const int a = tl;
         T v[N1][S];
 #pragma unroll
-        for (int b = 0; b < N1; ++b)
-#pragma unroll
-            for (int s = 0; s < S; ++s) v[b][s] = sUn[((te * NP + b * N1 + a) * S + s) * Q + tq];
+        for (int b = 0; b < N1; ++b) ldv<T, S>(un_at(b * N1 + a), v[b]);
         T g[N1][S];
 #pragma unroll
         for (int b = 0; b < N1; ++b) phys_flux<T, EQ, S, 2, 1>(v[b], g[b], adv, gamma);
