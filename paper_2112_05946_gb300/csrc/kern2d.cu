@@ -30,7 +30,6 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
     size_t n = 0;
     n += (size_t)TE * Np * M * S;           // U: the tile (later the new state)
     n += (size_t)(2 + 2 * TE) * n1 * M * S; // modal face traces of the neighbours (x-halo, below, above)
-    n += (size_t)TE * Np * M * S;           // B: SSP base state of the tile
     n += (size_t)TE * Np * S * Q;           // Un (nodal values)
     n += ((size_t)TE * Np * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;   // G (nodal residual, rows padded; later modal coefficients)
     n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][q][s]
@@ -62,8 +61,10 @@ __device__ inline void face_eval(const T* ft, int M, const T* Vzq_stride, int Q,
 }
 
 // MC, QC: the mode and z-node counts when fixed at compile time (0: taken from A).
+// Blocks hold at most 512 threads.  Float builds are held to 80 registers: with about 35 KB of
+// shared memory per 4-element CTA that lets six CTAs share an SM (at 86 registers, five).
 template <typename T, int N1, int S, int MC = 0, int QC = 0>
-__global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
+__global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const StageArgs A) {
     constexpr int NP = N1 * N1;
     constexpr int EQ = FRSG_EQ_EULER;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -83,7 +84,6 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     T* p = reinterpret_cast<T*>(smem_raw);
     T* sU = p; p += (size_t)TE * elsz;
     T* sFT = p; p += (size_t)(2 + 2 * TE) * N1 * M * S;   // [face][line][k][s]
-    T* sB = p; p += (size_t)TE * elsz;
     T* sUn = p; p += (size_t)TE * NP * S * Q;            // [te][point][q][s]
     const int GR = S * Q + (sizeof(T) == 4 ? 1 : 0);   // row stride of the nodal residual (float: padded)
     T* sG = p; p += ((size_t)TE * NP * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;
@@ -169,10 +169,6 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
             }
 #pragma unroll
             for (int q = 0; q < S; ++q) sFT[((f * N1 + line) * M + k) * S + q] = acc[q];
-        }
-        if (nonzero(A.a)) {
-            const T* src = ubase + (size_t)e0 * elsz;
-            for (int i = tid; i < ne * elsz; i += nthr) sB[i] = src[i];
         }
     }
     __syncthreads();
@@ -373,7 +369,9 @@ __global__ void __launch_bounds__(512) stage2d_kernel(const StageArgs A) {
     bool bad = false;
     if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
-        bad |= project_combine<T, NP, S>(sG + te * NP * GR, GR, sTile + te * elsz, sB + te * elsz, sPz, dst, M, Q, tq,
+        // the SSP base is read once, straight from global memory
+        const T* base = sK.use_base ? ubase + gbase + (size_t)te * elsz : nullptr;
+        bad |= project_combine<T, NP, S>(sG + te * NP * GR, GR, sTile + te * elsz, base, sPz, dst, M, Q, tq,
                                          Q, tl, N1, ca, cb, cc, sK.use_base != 0,
                                          acc_term<T>(A, gbase + (size_t)te * elsz, sK));
     }
