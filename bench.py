@@ -517,7 +517,7 @@ def run_ours(args):
     kname = {0: "stage1d_kernel", 1: "stage1d_wide_kernel", 2: "stage1d_step_kernel"}[chosen["variant"]]
     # DRAM bytes of one launch from the ncu capture of this kernel build (dram__bytes_read.sum +
     # dram__bytes_write.sum; profiles/stage1d_burgers_E1024_ncu.md); null for any other layout
-    traffic = 333056 if (kname == "stage1d_wide_kernel" and chosen["precision"] == "fp32") else None
+    traffic = 333568 if (kname == "stage1d_wide_kernel" and chosen["precision"] == "fp32") else None
     roofline = {"bound": "hbm", "achieved": round(chosen["achieved_gbs"], 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(chosen["achieved_gbs"] / hbm_peak, 5), "traffic": traffic,
                 "kernel": kname, "peak_source": "measured" if peaks else "fallback",
