@@ -226,7 +226,7 @@ def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracl
     mean_stage = np.mean(np.array(stage_ms), axis=0)           # ms per stage launch
     arrays = [2, 3, 3]                                         # state arrays read+written per stage
     alg_bytes = [a * esz * dof for a in arrays]
-    if variant == 2:
+    if variant in (2, 3):
         # one launch per step: the timed step is the kernel
         achieved = sum(alg_bytes) / (ms * 1e-3) / 1e9
     else:
@@ -514,7 +514,8 @@ def run_ours(args):
         with open(pk) as f:
             peaks = json.load(f)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    kname = {0: "stage1d_kernel", 1: "stage1d_wide_kernel", 2: "stage1d_step_kernel"}[chosen["variant"]]
+    kname = {0: "stage1d_kernel", 1: "stage1d_wide_kernel", 2: "stage1d_step_kernel",
+             3: "step1d_fused_kernel"}[chosen["variant"]]
     # DRAM bytes of one launch from the ncu capture of this kernel build (dram__bytes_read.sum +
     # dram__bytes_write.sum; profiles/stage1d_burgers_E1024_ncu.md); null for any other layout
     traffic = 333568 if (kname == "stage1d_wide_kernel" and chosen["precision"] == "fp32") else None

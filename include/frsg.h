@@ -256,8 +256,17 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out);
  * element's solution points; 1 (the default for 1D) = one thread per (z-node, point,
  * element); 2 = layout 0, with the three stages of an SSP-RK3 step in ONE cooperative launch
  * separated by grid-wide barriers (1D without limiter; a barrier that waits longer than
- * about 2 s latches FRSG_E_TIMEOUT and the kernel returns).  All compute the same stage; the
- * tile is re-chosen automatically.  2D contexts accept only 0 (FRSG_E_UNSUPPORTED otherwise). */
+ * about 2 s latches FRSG_E_TIMEOUT and the kernel returns); 3 = the three stages of an SSP-RK3
+ * step in ONE launch without grid barriers: each CTA loads its tile with three elements of
+ * halo on each side and recomputes the halo's stages on chip, in layout 1's arithmetic (1D
+ * without limiter; FRSG_E_UNSUPPORTED when no tile fits: 7*Q*(P+1) > 1024, or every tile's
+ * grid too large to be resident at once).  Before storing the step, a
+ * CTA waits until the CTAs reading its elements as halo have loaded them (a wait longer than
+ * about 2 s latches FRSG_E_TIMEOUT and the CTA stores nothing); the tile is the number of
+ * elements a CTA finishes, and the launch is refused (FRSG_E_CUDA from the step) when its
+ * grid cannot be resident at once.  With layout 3, single stages (fr_sg_stage, fr_sg_rhs,
+ * the recorded run) run layout 1.  All compute the same stage; the tile is re-chosen
+ * automatically.  2D contexts accept only 0 (FRSG_E_UNSUPPORTED otherwise). */
 frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant);
 
 /* Autotuner: times graph-replayed SSP-RK3 steps (reps per candidate, default 20; CUDA

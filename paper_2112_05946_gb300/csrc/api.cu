@@ -40,6 +40,8 @@ struct frsg_ctx {
     double* d_conv = nullptr;     // FP32 contexts: double staging buffer for set/get_state
     double* d_dt = nullptr;       // step size read by the stage kernels (graphs do not depend on dt)
     unsigned* d_bar = nullptr;    // grid-barrier words of the one-launch step (count, generation)
+    unsigned long long* d_tok = nullptr;   // [E] per-tile load tokens of the halo-recomputing step
+    unsigned long long tok_seq = 0;        // token of its last launch
     double dt_set = -1.0;         // value last written to d_dt
     uint8_t* d_flags = nullptr;   // [4][E] (rows 0..2 SSP-RK3 stages, row 3 the last RK4 stage)
     double* d_beta = nullptr;     // [4][E]
@@ -50,7 +52,7 @@ struct frsg_ctx {
     std::string last_error;
     uint64_t launches = 0;
     int TE = 1, TE_lim = 1;
-    int wide = 0;                 // 1D stage kernel layout: 1 = thread per (z-node, point)
+    int wide = 0;                 // 1D layout: 1 = thread per (z-node, point); 2, 3: one launch per step
     cudaGraphExec_t graph_exec = nullptr;
     cudaGraphExec_t graph_rk4 = nullptr;
     void* d_u3 = nullptr;         // RK4 weighted sum of the stage residuals (allocated on first use)
@@ -242,6 +244,17 @@ void build_device_tables(frsg_ctx* c) {
     c->off = tc.off;
 }
 
+bool tile_fits_1d(const frsg_ctx* c, int te, int wide);
+
+// Layout 3 runs single stages (fr_sg_stage, fr_sg_rhs, the recorded run) in the point-parallel
+// layout, with the largest tile of at most its own that fits there.
+int stage_tile(const frsg_ctx* c) {
+    if (c->cfg.dim != 1 || c->wide != 3) return c->TE;
+    int te = c->TE;
+    while (te > 1 && !tile_fits_1d(c, te, 1)) --te;
+    return te;
+}
+
 StageArgs base_args(frsg_ctx* c) {
     StageArgs A{};
     A.E = c->E;
@@ -269,8 +282,8 @@ StageArgs base_args(frsg_ctx* c) {
     A.kappa = c->cfg.kappa;
     A.det_ratio = frsg::detector_ratio(c->cfg.s0, c->cfg.kappa);
     A.err = c->d_err;
-    A.TE = c->TE;
-    A.wide = c->wide == 1 ? 1 : 0;
+    A.TE = stage_tile(c);
+    A.wide = (c->wide == 1 || c->wide == 3) ? 1 : 0;
     return A;
 }
 
@@ -365,11 +378,14 @@ cudaError_t set_dt(frsg_ctx* c, double dt) {
     return e;
 }
 
-bool one_launch_step(const frsg_ctx* c) { return c->cfg.dim == 1 && c->wide == 2 && !c->cfg.limiter; }
+bool one_launch_step(const frsg_ctx* c) {
+    return c->cfg.dim == 1 && (c->wide == 2 || c->wide == 3) && !c->cfg.limiter;
+}
 
 cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
     if (one_launch_step(c)) {
-        // one cooperative launch for the three stages (variant 2)
+        // one launch for the three stages: cooperative with grid barriers (variant 2), or
+        // halo-recomputing tiles (variant 3)
         const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
         void* bin[3] = {c->d_u, c->d_u1, c->d_u2};
         void* bout[3] = {c->d_u1, c->d_u2, c->d_u};
@@ -397,6 +413,13 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
             A3[s] = A;
         }
         c->launches += 1;
+        if (c->wide == 3) {
+            for (int s = 0; s < 3; ++s) {
+                A3[s].TE = c->TE;
+                A3[s].wide = 1;
+            }
+            return frsg::launch_fused1d(c->cfg, c->fp64, A3, c->d_tok, ++c->tok_seq, c->stream);
+        }
         return frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
     }
     for (int s = 0; s < 3; ++s) {
@@ -457,7 +480,22 @@ cudaError_t issue_rk4_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
     return launch_stage(c, A);
 }
 
+// wide: 0 = thread per (z-node, element), 1 = per (z-node, point, element), 3 = the
+// halo-recomputing one-launch step (also needs its whole grid resident)
 bool tile_fits_1d(const frsg_ctx* c, int te, int wide) {
+    if (wide == 3) {
+        if (te < 1 || (te + 6) * c->Q * c->Np > 1024 ||
+            frsg::stage1d_fused_smem_bytes(c->fp64, te, c->Np, c->M, c->Q, c->S) > 200 * 1024)
+            return false;
+        frsg_ctx* m = const_cast<frsg_ctx*>(c);
+        StageArgs A3[3];
+        for (int s = 0; s < 3; ++s) {
+            A3[s] = base_args(m);
+            A3[s].TE = te;
+            A3[s].do_filter = c->cfg.filter != FRSG_FILTER_NONE ? 1 : 0;
+        }
+        return frsg::launch_fused1d(c->cfg, c->fp64, A3, nullptr, 0, c->stream, true) == cudaSuccess;
+    }
     const int thr = te * c->Q * (wide ? c->Np : 1);
     const size_t sm = wide ? frsg::stage1d_wide_smem_bytes(c->fp64, te, c->Np, c->M, c->Q, c->S)
                            : frsg::stage1d_smem_bytes(c->fp64, te, c->Np, c->M, c->Q, c->S);
@@ -465,6 +503,13 @@ bool tile_fits_1d(const frsg_ctx* c, int te, int wide) {
 }
 
 int choose_tile_1d(const frsg_ctx* c) {
+    if (c->wide == 3) {
+        // the smallest tile (the most CTAs) whose grid can be resident at once
+        const int tmax = 1024 / (c->Q * c->Np) - 6;
+        for (int te = 1; te <= tmax; ++te)
+            if (tile_fits_1d(c, te, 3)) return te;
+        return 1;
+    }
     const int w = c->wide == 1 ? 1 : 0;
     int te = std::max(1, c->E / (2 * 152));
     const int cap = w ? 256 : 512;
@@ -541,6 +586,9 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     if ((e = cudaMalloc(&ctx->d_dt, sizeof(double))) != cudaSuccess) return cleanup_fail(e, "dt");
     if ((e = cudaMalloc(&ctx->d_bar, 2 * sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "barrier");
     if ((e = cudaMemset(ctx->d_bar, 0, 2 * sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "barrier");
+    if ((e = cudaMalloc(&ctx->d_tok, sizeof(unsigned long long) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "tokens");
+    if ((e = cudaMemset(ctx->d_tok, 0, sizeof(unsigned long long) * ctx->E)) != cudaSuccess)
+        return cleanup_fail(e, "tokens");
     if ((e = cudaMalloc(&ctx->d_flags, 4 * (size_t)ctx->E)) != cudaSuccess) return cleanup_fail(e, "flags");
     if ((e = cudaMalloc(&ctx->d_beta, 4 * sizeof(double) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "beta");
     if ((e = cudaMalloc(&ctx->d_err, sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "err");
@@ -586,6 +634,7 @@ void fr_sg_destroy(frsg_ctx* ctx) {
     cudaFree(ctx->d_conv);
     cudaFree(ctx->d_dt);
     cudaFree(ctx->d_bar);
+    cudaFree(ctx->d_tok);
     cudaFree(ctx->d_flags);
     cudaFree(ctx->d_beta);
     cudaFree(ctx->d_err);
@@ -1084,12 +1133,12 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
     ctx->replay_rows = 0;                 // tuning steps never consume replayed decisions
     // candidates: layout x tile that fit
     std::vector<std::pair<int, int>> cand;
-    const int variants = c.dim == 1 ? (c.limiter ? 2 : 3) : 1;
+    const int variants = c.dim == 1 ? (c.limiter ? 2 : 4) : 1;
     for (int w = 0; w < variants; ++w)
         for (int te : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
             bool fits;
             if (c.dim == 1) {
-                fits = tile_fits_1d(ctx, te, w == 1 ? 1 : 0);
+                fits = tile_fits_1d(ctx, te, w == 2 ? 0 : w);
             } else {
                 fits = te * ctx->Q * ctx->n1 <= 512 &&
                        frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) <= 200 * 1024;
@@ -1154,13 +1203,21 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
 
 frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
     if (!ctx) return FRSG_E_INVAL;
-    if (variant < 0 || variant > 2) return fail(ctx, FRSG_E_INVAL, "variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 3) return fail(ctx, FRSG_E_INVAL, "variant must be 0, 1, 2 or 3");
     if (ctx->cfg.dim != 1) return variant == 0 ? FRSG_OK : fail(ctx, FRSG_E_UNSUPPORTED, "2D has one layout");
-    if (variant == 2 && ctx->cfg.limiter)
-        return fail(ctx, FRSG_E_UNSUPPORTED, "the one-launch step does not run the limiter");
+    if ((variant == 2 || variant == 3) && ctx->cfg.limiter)
+        return fail(ctx, FRSG_E_UNSUPPORTED, "the one-launch steps do not run the limiter");
+    const int old_wide = ctx->wide;
     drop_graphs(ctx);
     ctx->wide = variant;
     ctx->TE = choose_tile_1d(ctx);
+    if (variant == 3 && !tile_fits_1d(ctx, ctx->TE, 3)) {
+        ctx->wide = old_wide;
+        ctx->TE = choose_tile_1d(ctx);
+        return fail(ctx, FRSG_E_UNSUPPORTED,
+                    "no tile of the halo-recomputing step fits: 7*Q*(P+1) > 1024 threads, or no grid small "
+                    "enough to be resident at once");
+    }
     return FRSG_OK;
 }
 
@@ -1495,7 +1552,8 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out) {
     if (te == 0) {
         want = ctx->cfg.dim == 1 ? choose_tile_1d(ctx) : choose_tile_2d(ctx);
     } else if (ctx->cfg.dim == 1) {
-        if (!tile_fits_1d(ctx, te, ctx->wide == 1 ? 1 : 0)) return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
+        if (!tile_fits_1d(ctx, te, ctx->wide == 2 ? 0 : ctx->wide))
+            return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
     } else {
         if (te * ctx->Q * ctx->n1 > 512 ||
             frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) > 220 * 1024)

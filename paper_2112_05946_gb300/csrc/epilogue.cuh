@@ -46,12 +46,21 @@ struct StageConsts {
 
 __device__ inline bool nonzero(double x) { return (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0; }
 
+// The launch's step size: *dtp when set (device memory, written before the launch), else
+// dt_filter.  Kernels may load it early and form the constants later.
+__device__ inline double stage_dt(const StageArgs& A) { return A.dtp ? *A.dtp : A.dt_filter; }
+
 template <typename T>
-__device__ inline StageConsts<T> make_consts(const StageArgs& A);
+__device__ inline StageConsts<T> make_consts(const StageArgs& A, double dt_raw);
+
+template <typename T>
+__device__ inline StageConsts<T> make_consts(const StageArgs& A) {
+    return make_consts<T>(A, stage_dt(A));
+}
 
 template <>
-__device__ inline StageConsts<double> make_consts<double>(const StageArgs& A) {
-    const double dt = A.dtp ? *A.dtp : A.dt_filter;
+__device__ inline StageConsts<double> make_consts<double>(const StageArgs& A, double dt_raw) {
+    const double dt = dt_raw;
     StageConsts<double> K;
     K.ca = A.a;
     K.cb = A.b;
@@ -70,8 +79,8 @@ __device__ inline StageConsts<double> make_consts<double>(const StageArgs& A) {
 }
 
 template <>
-__device__ inline StageConsts<float> make_consts<float>(const StageArgs& A) {
-    const float dt = (float)(A.dtp ? *A.dtp : A.dt_filter);
+__device__ inline StageConsts<float> make_consts<float>(const StageArgs& A, double dt_raw) {
+    const float dt = (float)dt_raw;
     StageConsts<float> K;
     K.ca = A.fa;
     K.cb = A.fb;
@@ -266,12 +275,16 @@ __device__ __noinline__ T lasso_value(const T* me, const T* sVf, const T* sNorm,
 }
 
 // a9 + a10 for the tile.  Us: the tile's new coefficients [ne][NP][M][S] in shared memory;
-// Mod: scratch of the same size; te: this thread's element; active: te < ne.
-template <typename T, int NP, int S>
+// Mod: scratch of the same size; te: this thread's element (its slot in Us, Mod, sRed,
+// sFlag); active: te holds an element to finish; e: that element's index in the problem
+// (replayed and recorded decisions); record: store the decision in A.flags; dst: where the
+// element's final coefficients go (global memory, or back over Us).
+// FSHFL: sum float energies with warp shuffles as well (see below).
+template <typename T, int NP, int S, bool FSHFL = false>
 __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T* Mod, const T* sVf, const T* sVfinv,
                                              const T* sLam, const T* sTop, T* sRed, int* sFlag, int te, int kl,
-                                             int nk, int ml, int nm, bool active, bool member, int e0, T* uout,
-                                             size_t gbase, T det, int M) {
+                                             int nk, int ml, int nm, bool active, bool member, int e, bool record,
+                                             T* dst, T det, int M) {
     const int elsz = NP * M * S;
     const T* ue = Us + te * elsz;
     T* me = Mod + te * elsz;
@@ -296,9 +309,9 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
     // sums, then at most a few partials per element through shared memory.  Otherwise every
     // thread's partial goes through shared memory and one thread per element adds them.
     // Measured on the benchmark shapes, the shuffle wins for double states (a serial chain of
-    // double adds is long) and loses slightly for float ones, so float keeps the serial sum.
+    // double adds is long); float states take it where the caller asks (FSHFL).
     const int nblk = blockDim.x * blockDim.y * blockDim.z;
-    const bool shuffle = sizeof(T) == 8 && (nlt & (nlt - 1)) == 0 && (nblk & 31) == 0;
+    const bool shuffle = (sizeof(T) == 8 || FSHFL) && (nlt & (nlt - 1)) == 0 && (nblk & 31) == 0;
     T t0 = tot, t1 = top;
     int parts = nlt;
     if (shuffle) {
@@ -324,13 +337,12 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
             t0 += sRed[(te * nlt + i) * 2 + 0];
             t1 += sRed[(te * nlt + i) * 2 + 1];
         }
-        const int e = e0 + te;
         int fl;
         if (A.replay) fl = A.replay[e] ? 1 : 0;
         else if (!A.sensor) fl = 1;
         else fl = (t1 > T(0) && t1 > det * t0) ? 1 : 0;
         sFlag[te] = fl;
-        if (A.flags) A.flags[e] = (uint8_t)fl;
+        if (A.flags && record) A.flags[e] = (uint8_t)fl;
     }
     __syncthreads();
     // pass A1: the other variables' modal coefficients, flagged elements only
@@ -365,7 +377,6 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
             c1 = table_block<T>(A)[A.off.lc];
             c2 = table_block<T>(A)[A.off.lc + 1];
         }
-        T* dst = uout + gbase + (size_t)te * elsz;
         for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
             const int j = w.r, k = w.k;
             const int o = (j * M + k) * S;

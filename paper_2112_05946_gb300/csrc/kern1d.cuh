@@ -1,8 +1,8 @@
 // Fused FR-SG stage kernel on a 1D mesh.
 //
 // One CTA owns TE consecutive elements; thread (q, te) owns z-node q of element te.
-// One coalesced sweep loads the tile, its two neighbour elements (the halo) and the
-// SSP base state into shared memory; then, on chip:
+// One sweep of asynchronous copies loads the tables, then the tile, its two neighbour
+// elements (the halo) and the SSP base state into shared memory; then, on chip:
 //   a2  u(r_j, z_q) = sum_k Phi_k(z_q) uhat_jk            (§2.1, Eq. 2)
 //   a5  face traces u(+-1, z_q) by ell_j(+-1)             (§3.3), halo traces included
 //   a6  LLF flux at both faces of every element           (§3.3)
@@ -55,7 +55,7 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool periodic = A.bc[0] == FRSG_BC_PERIODIC;
     pdl_trigger();
-    const StageConsts<T> sK = make_consts<T>(A);
+    const double dt_raw = stage_dt(A);   // issued now, used after the loads
 
     T* p = reinterpret_cast<T*>(smem_raw);
     T* sU = p; p += (size_t)(TE + 2) * elsz;
@@ -80,23 +80,23 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     // ---- one sweep of independent loads: tables, halo + tile, SSP base
     const T* tab = table_block<T>(A);
     for (int i = tid; i < M * Q; i += nthr) {
-        sVz[i] = tab[A.off.VzT + i];
-        sPz[i] = tab[A.off.Pz + i];
+        cp_async(sVz + i, tab + A.off.VzT + i);
+        cp_async(sPz + i, tab + A.off.Pz + i);
     }
-    for (int i = tid; i < NP * NP; i += nthr) sD[i] = tab[A.off.D + i];
+    for (int i = tid; i < NP * NP; i += nthr) cp_async(sD + i, tab + A.off.D + i);
     for (int i = tid; i < NP; i += nthr) {
-        slm[i] = tab[A.off.lm + i];
-        slp[i] = tab[A.off.lp + i];
-        sdhL[i] = tab[A.off.dhL + i];
-        sdhR[i] = tab[A.off.dhR + i];
+        cp_async(slm + i, tab + A.off.lm + i);
+        cp_async(slp + i, tab + A.off.lp + i);
+        cp_async(sdhL + i, tab + A.off.dhL + i);
+        cp_async(sdhR + i, tab + A.off.dhR + i);
     }
     if (A.do_filter) {
         for (int i = tid; i < NP * NP; i += nthr) {
-            sVf[i] = tab[A.off.Vf + i];
-            sVfinv[i] = tab[A.off.Vfinv + i];
+            cp_async(sVf + i, tab + A.off.Vf + i);
+            cp_async(sVfinv + i, tab + A.off.Vfinv + i);
         }
-        for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
-        load_filter_table<T>(A, NP, sLam, tid, nthr);
+        for (int i = tid; i < NP; i += nthr) cp_async(sTop + i, tab + A.off.top + i);
+        for (int i = tid; i < NP * M; i += nthr) cp_async(sLam + i, tab + A.off.lam + i);
     }
     pdl_wait();
     {
@@ -107,17 +107,19 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
         const T* srcL = uin + (size_t)(nl < 0 ? E - 1 : nl) * elsz;
         const T* srcR = uin + (size_t)(nr >= E ? 0 : nr) * elsz;
         for (int i = tid; i < elsz; i += nthr) {
-            if (hasL) sU[i] = srcL[i];
-            if (hasR) sU[(ne + 1) * elsz + i] = srcR[i];
+            if (hasL) cp_async(sU + i, srcL + i);
+            if (hasR) cp_async(sU + (ne + 1) * elsz + i, srcR + i);
         }
         const T* srcT = uin + (size_t)e0 * elsz;
-        for (int i = tid; i < ne * elsz; i += nthr) sU[elsz + i] = srcT[i];
+        for (int i = tid; i < ne * elsz; i += nthr) cp_async(sU + elsz + i, srcT + i);
         if (nonzero(A.a)) {
             const T* srcB = ubase + (size_t)e0 * elsz;
-            for (int i = tid; i < ne * elsz; i += nthr) sB[i] = srcB[i];
+            for (int i = tid; i < ne * elsz; i += nthr) cp_async(sB + i, srcB + i);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
+    const StageConsts<T> sK = make_consts<T>(A, dt_raw);
     const T adv = sK.adv, gamma = sK.gamma;
     if (A.do_filter) finish_filter_strengths<T>(A, NP, sLam, tid, nthr, sK.adt);   // read after later barriers
 
@@ -242,7 +244,8 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
         __syncthreads();
         // ---- a9 + a10: detector and filter, one store per coefficient
         bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, 0, 1,
-                                              active, member, e0, uout, gbase, sK.det, M);
+                                              active, member, e0 + te, true,
+                                              uout + gbase + (size_t)te * elsz, sK.det, M);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool periodic = A.bc[0] == FRSG_BC_PERIODIC;
     pdl_trigger();
-    const StageConsts<T> sK = make_consts<T>(A);
+    const double dt_raw = stage_dt(A);   // issued now, used after the loads
 
     T* p = reinterpret_cast<T*>(smem_raw);
     T* sU = p; p += (size_t)(TE + 2) * elsz;
@@ -301,25 +304,26 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     T* sRed = p; p += 2 * TE * Q * NP;
     int* sFlag = reinterpret_cast<int*>(p);
 
+    // tables, then (after the wait) the state: asynchronous copies, in flight together
     const T* tab = table_block<T>(A);
     for (int i = tid; i < M * Q; i += nthr) {
-        sVz[i] = tab[A.off.VzT + i];
-        sPz[i] = tab[A.off.Pz + i];
+        cp_async(sVz + i, tab + A.off.VzT + i);
+        cp_async(sPz + i, tab + A.off.Pz + i);
     }
-    for (int i = tid; i < NP * NP; i += nthr) sD[i] = tab[A.off.D + i];
+    for (int i = tid; i < NP * NP; i += nthr) cp_async(sD + i, tab + A.off.D + i);
     for (int i = tid; i < NP; i += nthr) {
-        slm[i] = tab[A.off.lm + i];
-        slp[i] = tab[A.off.lp + i];
-        sdhL[i] = tab[A.off.dhL + i];
-        sdhR[i] = tab[A.off.dhR + i];
+        cp_async(slm + i, tab + A.off.lm + i);
+        cp_async(slp + i, tab + A.off.lp + i);
+        cp_async(sdhL + i, tab + A.off.dhL + i);
+        cp_async(sdhR + i, tab + A.off.dhR + i);
     }
     if (A.do_filter) {
         for (int i = tid; i < NP * NP; i += nthr) {
-            sVf[i] = tab[A.off.Vf + i];
-            sVfinv[i] = tab[A.off.Vfinv + i];
+            cp_async(sVf + i, tab + A.off.Vf + i);
+            cp_async(sVfinv + i, tab + A.off.Vfinv + i);
         }
-        for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
-        load_filter_table<T>(A, NP, sLam, tid, nthr);
+        for (int i = tid; i < NP; i += nthr) cp_async(sTop + i, tab + A.off.top + i);
+        for (int i = tid; i < NP * M; i += nthr) cp_async(sLam + i, tab + A.off.lam + i);
     }
     pdl_wait();
     const int nl = e0 - 1, nr = e0 + ne;
@@ -328,17 +332,19 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
         const T* srcL = uin + (size_t)(nl < 0 ? E - 1 : nl) * elsz;
         const T* srcR = uin + (size_t)(nr >= E ? 0 : nr) * elsz;
         for (int i = tid; i < elsz; i += nthr) {
-            if (hasL) sU[i] = srcL[i];
-            if (hasR) sU[(ne + 1) * elsz + i] = srcR[i];
+            if (hasL) cp_async(sU + i, srcL + i);
+            if (hasR) cp_async(sU + (ne + 1) * elsz + i, srcR + i);
         }
         const T* srcT = uin + (size_t)e0 * elsz;
-        for (int i = tid; i < ne * elsz; i += nthr) sU[elsz + i] = srcT[i];
+        for (int i = tid; i < ne * elsz; i += nthr) cp_async(sU + elsz + i, srcT + i);
         if (nonzero(A.a)) {
             const T* srcB = ubase + (size_t)e0 * elsz;
-            for (int i = tid; i < ne * elsz; i += nthr) sB[i] = srcB[i];
+            for (int i = tid; i < ne * elsz; i += nthr) cp_async(sB + i, srcB + i);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
+    const StageConsts<T> sK = make_consts<T>(A, dt_raw);
     const T adv = sK.adv, gamma = sK.gamma;
     if (A.do_filter) finish_filter_strengths<T>(A, NP, sLam, tid, nthr, sK.adt);   // read after later barriers
 
@@ -443,7 +449,8 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     if (A.do_filter) {
         __syncthreads();
         bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tj, NP,
-                                              active, true, e0, uout, gbase, sK.det, M);
+                                              active, true, e0 + te, true,
+                                              uout + gbase + (size_t)te * elsz, sK.det, M);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }

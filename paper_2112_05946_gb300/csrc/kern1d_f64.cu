@@ -1,6 +1,6 @@
 // Instantiations of the 1D stage kernels for double states (the kernel templates are in
 // kern1d.cuh; one translation unit per precision keeps the build parallel).
-#include "kern1d.cuh"
+#include "kern1d_fused.cuh"
 
 namespace frsg {
 
@@ -10,6 +10,11 @@ cudaError_t k1d_stage_f64(const frsg_config& cfg, const StageArgs& A, cudaStream
 
 cudaError_t k1d_step_f64(const frsg_config& cfg, const StageArgs* A3, unsigned* bar, int* grid, cudaStream_t st) {
     return step_np<double>(cfg, A3, bar, grid, st);
+}
+
+cudaError_t k1d_fused_f64(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok,
+                          unsigned long long token, cudaStream_t st, bool check_only) {
+    return fused_np<double>(cfg, A3, tok, token, st, check_only);
 }
 
 cudaError_t k1d_batched_f64(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,

@@ -79,7 +79,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     const int elsz = NP * M * S;
     const T* uin = static_cast<const T*>(A.uin);
     pdl_trigger();
-    const StageConsts<T> sK = make_consts<T>(A);
+    const double dt_raw = stage_dt(A);   // issued now, used after the loads
 
     T* p = reinterpret_cast<T*>(smem_raw);
     T* sU = p; p += (size_t)TE * elsz;
@@ -104,23 +104,23 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
 
     const T* tab = table_block<T>(A);
     for (int i = tid; i < M * Q; i += nthr) {
-        sVz[i] = tab[A.off.VzT + i];
-        sPz[i] = tab[A.off.Pz + i];
+        cp_async(sVz + i, tab + A.off.VzT + i);
+        cp_async(sPz + i, tab + A.off.Pz + i);
     }
-    for (int i = tid; i < N1 * N1; i += nthr) sD[i] = tab[A.off.D + i];
+    for (int i = tid; i < N1 * N1; i += nthr) cp_async(sD + i, tab + A.off.D + i);
     for (int i = tid; i < N1; i += nthr) {
-        slm[i] = tab[A.off.lm + i];
-        slp[i] = tab[A.off.lp + i];
-        sdhL[i] = tab[A.off.dhL + i];
-        sdhR[i] = tab[A.off.dhR + i];
+        cp_async(slm + i, tab + A.off.lm + i);
+        cp_async(slp + i, tab + A.off.lp + i);
+        cp_async(sdhL + i, tab + A.off.dhL + i);
+        cp_async(sdhR + i, tab + A.off.dhR + i);
     }
     if (A.do_filter) {
         for (int i = tid; i < NP * NP; i += nthr) {
-            sVf[i] = tab[A.off.Vf + i];
-            sVfinv[i] = tab[A.off.Vfinv + i];
+            cp_async(sVf + i, tab + A.off.Vf + i);
+            cp_async(sVfinv + i, tab + A.off.Vfinv + i);
         }
-        for (int i = tid; i < NP; i += nthr) sTop[i] = tab[A.off.top + i];
-        load_filter_table<T>(A, NP, sLam, tid, nthr);
+        for (int i = tid; i < NP; i += nthr) cp_async(sTop + i, tab + A.off.top + i);
+        for (int i = tid; i < NP * M; i += nthr) cp_async(sLam + i, tab + A.off.lam + i);
     }
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool xper = A.bc[0] == FRSG_BC_PERIODIC, yper = A.bc[2] == FRSG_BC_PERIODIC;
@@ -134,7 +134,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
         const int nl = ex0 - 1, nr = ex0 + ne;
         const bool hasL = nl >= 0 || xper, hasR = nr < nx || xper;
         const T* srcT = uin + (size_t)e0 * elsz;
-        for (int i = tid; i < ne * elsz; i += nthr) sU[i] = srcT[i];
+        for (int i = tid; i < ne * elsz; i += nthr) cp_async(sU + i, srcT + i);
         const int fpairs = N1 * M;
         for (int idx = tid; idx < (2 + 2 * ne) * fpairs; idx += nthr) {
             const int f = idx / fpairs, r = idx - f * fpairs;
@@ -171,7 +171,9 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             for (int q = 0; q < S; ++q) sFT[((f * N1 + line) * M + k) * S + q] = acc[q];
         }
     }
+    cp_async_wait_all();
     __syncthreads();
+    const StageConsts<T> sK = make_consts<T>(A, dt_raw);
     const T gamma = sK.gamma, adv = sK.adv;
     if (A.do_filter) finish_filter_strengths<T>(A, NP, sLam, tid, nthr, sK.adt);   // read after later barriers
 
@@ -378,7 +380,8 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     if (A.do_filter) {
         __syncthreads();
         bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tl, N1,
-                                              active, true, e0, uout, gbase, sK.det, M);
+                                              active, true, e0 + te, true,
+                                              uout + gbase + (size_t)te * elsz, sK.det, M);
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
 }

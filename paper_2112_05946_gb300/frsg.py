@@ -353,7 +353,9 @@ class Solver:
         return v.value, t.value
 
     def set_variant(self, variant):
-        """1D stage layout: 0 thread per (z-node, element), 1 thread per (z-node, point, element)."""
+        """1D layout: 0 thread per (z-node, element), 1 thread per (z-node, point, element),
+        2 one cooperative launch per SSP-RK3 step, 3 one launch per step with each tile
+        recomputing a three-element halo (2 and 3: no limiter)."""
         self._ck(self.lib.fr_sg_set_variant(self.h, int(variant)), "set_variant")
 
 

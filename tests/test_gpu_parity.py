@@ -100,7 +100,7 @@ def test_cfl_dt(name):
 
 
 @pytest.mark.parametrize("tile", [1, 3])
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_one_step_burgers_with_filter(tile, variant):
     """One SSP-RK3 step with the detector-switched exponential filter, from a state with
     a steep front so that some elements are flagged and others are not."""
@@ -178,7 +178,7 @@ def test_burgers_run_past_shock_with_replayed_decisions():
     rec = []
     ref = integrate.run(prob, u0, dt, nsteps, record=rec)
     assert np.any(np.concatenate(rec))
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         s = solver(wl)
         s.set_variant(variant)
         gpu_initial(s, wl)
@@ -289,7 +289,7 @@ def test_autotuned_choice_keeps_parity(name, precision, tol):
     prob = oracle_problem(wl)
     s = solver(wl, precision=precision)
     variant, tile = s.autotune(reps=2)
-    assert variant in (0, 1) and tile >= 1
+    assert variant in (0, 1, 2, 3) and tile >= 1
     base = [0.2] if name == "burgers" else [1.0, 0.2, 2.5]
     amp = [0.5] if name == "burgers" else [0.05, 0.05, 0.1]
     u = workloads.random_state(s.state_shape, seed=8, base=base, amp=amp)
