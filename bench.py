@@ -149,6 +149,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- our arm
 
+# DRAM bytes per launch of the benchmark's kernels, from ncu captures of the current build
+# (dram__bytes_read.sum + dram__bytes_write.sum, one launch, L2 flushed by ncu before it;
+# profiles/step1d_fused_burgers_E1024_ncu.md)
+MEASURED_TRAFFIC = {("step1d_fused_kernel", "fp32"): 175872}
+
+
 def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracle_ref):
     E, Np, M, S = workload_sizes(wl)
     dof = E * Np * M * S
@@ -224,8 +230,13 @@ def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracl
 
     ms = float(np.mean(step_ms))
     mean_stage = np.mean(np.array(stage_ms), axis=0)           # ms per stage launch
-    arrays = [2, 3, 3]                                         # state arrays read+written per stage
-    alg_bytes = [a * esz * dof for a in arrays]
+    if variant == 3:
+        # one launch per step whose stage states stay on chip: it must read u^n and write
+        # u^{n+1}, two state arrays per step
+        alg_bytes = [2 * esz * dof]
+    else:
+        arrays = [2, 3, 3]                                     # state arrays read+written per stage
+        alg_bytes = [a * esz * dof for a in arrays]
     if variant in (2, 3):
         # one launch per step: the timed step is the kernel
         achieved = sum(alg_bytes) / (ms * 1e-3) / 1e9
@@ -516,9 +527,9 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     kname = {0: "stage1d_kernel", 1: "stage1d_wide_kernel", 2: "stage1d_step_kernel",
              3: "step1d_fused_kernel"}[chosen["variant"]]
-    # DRAM bytes of one launch from the ncu capture of this kernel build (dram__bytes_read.sum +
-    # dram__bytes_write.sum; profiles/stage1d_burgers_E1024_ncu.md); null for any other layout
-    traffic = 333568 if (kname == "stage1d_wide_kernel" and chosen["precision"] == "fp32") else None
+    # DRAM bytes of one launch from the ncu capture of this kernel build; null for a layout
+    # without a capture of the current build
+    traffic = MEASURED_TRAFFIC.get((kname, chosen["precision"]))
     roofline = {"bound": "hbm", "achieved": round(chosen["achieved_gbs"], 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(chosen["achieved_gbs"] / hbm_peak, 5), "traffic": traffic,
                 "kernel": kname, "peak_source": "measured" if peaks else "fallback",

@@ -1078,7 +1078,7 @@ frsg_status fr_sg_tune_cache_load(const char* path) {
         int n = std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
                             &v[6], &v[7], &v[8], &v[9], &v[10], &v[11], &v[12]);
         if (n == EOF) break;
-        if (n != 13 || v[11] < 0 || v[11] > 2 || v[12] < 1 || v[12] > 64) {
+        if (n != 13 || v[11] < 0 || v[11] > 3 || v[12] < 1 || v[12] > 64) {
             std::fclose(f);
             return FRSG_E_INVAL;
         }
@@ -1097,7 +1097,12 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
+        // a cached choice from a file may not fit this device (the one-launch layouts need
+        // their grid resident): re-time then
+        const bool usable = it != g_tune_cache.end() &&
+                            (c.dim != 1 || tile_fits_1d(ctx, it->second.second,
+                                                        it->second.first == 2 ? 0 : it->second.first));
+        if (usable) {
             ctx->wide = it->second.first;
             ctx->TE = it->second.second;
             drop_graphs(ctx);

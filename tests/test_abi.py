@@ -65,12 +65,16 @@ def test_tune_cache_file_roundtrip(tmp_path):
     p = tmp_path / "tune.txt"
     frsg.tune_cache_save(str(p))
     assert p.read_text().startswith("frsg-tune 1")
-    p.write_text("frsg-tune 1\n1 3 8 16 1 1 1024 1 1 0 0 1 4\n")
+    p.write_text("frsg-tune 1\n1 3 8 16 1 1 1024 1 1 0 0 1 4\n1 3 8 16 1 1 1024 3 1 0 0 3 7\n")
     frsg.tune_cache_load(str(p))
     frsg.tune_cache_save(str(p))
     assert "1 3 8 16 1 1 1024 1 1 0 0 1 4" in p.read_text()
+    assert "1 3 8 16 1 1 1024 3 1 0 0 3 7" in p.read_text()
     bad = tmp_path / "bad.txt"
     bad.write_text("frsg-tune 1\n1 2 3\n")
+    with pytest.raises(frsg.FrsgError):
+        frsg.tune_cache_load(str(bad))
+    bad.write_text("frsg-tune 1\n1 3 8 16 1 1 1024 3 1 0 0 4 7\n")   # no layout 4
     with pytest.raises(frsg.FrsgError):
         frsg.tune_cache_load(str(bad))
     with pytest.raises(frsg.FrsgError):

@@ -70,11 +70,13 @@ def test_fused_step_matches_layout1_and_oracle(precision, nx, tile):
 @pytest.mark.parametrize("bc", [("outflow", "outflow"), ("reflect", "reflect"), ("dirichlet", "outflow"),
                                 ("dirichlet", "dirichlet")])
 @pytest.mark.parametrize("tile", [1, 4])
-def test_fused_step_boundaries(bc, tile):
-    """1D Euler (no limiter) with the filter at every kind of physical boundary."""
+@pytest.mark.parametrize("flux", ["llf", "hll"])
+def test_fused_step_boundaries(bc, tile, flux):
+    """1D Euler (no limiter) with the filter at every kind of physical boundary, with either
+    interface flux."""
     over = dict(nx=11, P=2, N=3, Q=6)
     wl = workloads.sod_1d(**over)
-    kw = dict(bc=bc + ("periodic", "periodic"), limiter=False, **over)
+    kw = dict(bc=bc + ("periodic", "periodic"), limiter=False, flux=flux, **over)
     prob = oracle_problem(wl, **kw)
     s0 = solver(wl, **kw)
     u = workloads.random_state(s0.state_shape, seed=3 + tile, base=[1.0, 0.3, 2.5], amp=[0.05, 0.05, 0.1])

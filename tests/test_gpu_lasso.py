@@ -45,7 +45,7 @@ def test_lasso_filter_alone_euler():
     assert rel_l2(s.get_state(), ref) < TOL64
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_lasso_burgers_run(variant):
     wl = _burgers_lasso(nx=64)
     prob = oracle_problem(wl)

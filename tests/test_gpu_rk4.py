@@ -22,7 +22,7 @@ def _oracle_rk4(prob, u, dt, nsteps, rec=None):
     return u
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("graph", [False, True])
 def test_rk4_advection(variant, graph):
     wl = workloads.advection_1d()
