@@ -53,11 +53,11 @@ __device__ __forceinline__ unsigned long long tok_read(const unsigned long long*
 
 // a0, a1, a2: the three stages' arguments (same shapes and tables; own coefficients, flags
 // and replay rows).  tok: one word per CTA; token: this launch's value (strictly increasing).
-// Blocks hold at most 1024 threads.  Scalar float builds are held to 48 registers (they
-// need no more), so that two 640-thread CTAs share an SM; the rest may use 64, the most a
-// 1024-thread block allows.
+// Blocks hold at most 1024 threads.  Scalar float builds may use 72 registers, so that one
+// 896-thread CTA (8 elements) fits an SM with the tables held in registers; the rest 64, the
+// most a 1024-thread block allows.
 template <typename T, int NP, int S, int EQ, int MC = 0, int QC = 0>
-__global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
+__global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
     step1d_fused_kernel(const __grid_constant__ StageArgs a0, const __grid_constant__ StageArgs a1,
                         const __grid_constant__ StageArgs a2, unsigned long long* tok, unsigned long long token) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -148,6 +148,22 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
     if (a0.do_filter) finish_filter_strengths<T>(a0, NP, sLam, tid, nthr, K0.adt);   // own entries; read after later barriers
 
     const T adv = K0.adv, gamma = K0.gamma, invJ = K0.invJx;
+    // small tables that every stage reuses, in registers: ell(-1), ell(+1), this thread's row of
+    // D, h'_L and h'_R at its point, and (mode count compiled in) its column of Vz.  Shared-
+    // memory load throughput bounds the phases; these are a third of a stage's loads.
+    T rlm[NP], rlp[NP], rD[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        rlm[m] = slm[m];
+        rlp[m] = slp[m];
+        rD[m] = sD[tj * NP + m];
+    }
+    const T rdhL = sdhL[tj], rdhR = sdhR[tj];
+    T rVz[MC > 0 ? MC : 1];
+    if constexpr (MC > 0) {
+#pragma unroll
+        for (int k = 0; k < MC; ++k) rVz[k] = sVz[k * Q + tq];
+    }
     // a later stage's constants: K0 with that stage's SSP coefficients (same products as
     // make_consts, without its per-thread double work)
     auto stage_consts = [&](const StageArgs& A) {
@@ -200,10 +216,18 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
             T u[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) u[s] = T(0);
-            for (int k = 0; k < M; ++k) {
-                const T v = sVz[k * Q + tq];
+            if constexpr (MC > 0) {
 #pragma unroll
-                for (int s = 0; s < S; ++s) u[s] += v * ue[k * S + s];
+                for (int k = 0; k < MC; ++k) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) u[s] += rVz[k] * ue[k * S + s];
+                }
+            } else {
+                for (int k = 0; k < M; ++k) {
+                    const T v = sVz[k * Q + tq];
+#pragma unroll
+                    for (int s = 0; s < S; ++s) u[s] += v * ue[k * S + s];
+                }
             }
 #pragma unroll
             for (int s = 0; s < S; ++s) sUn[((r * NP + tj) * S + s) * Q + tq] = u[s];
@@ -218,7 +242,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
 
         // ---- a5 + a6 + a7: traces, interface fluxes, derivative row j (nodal in z)
         if (out_valid) {
-            auto trace = [&](const T* src, const T* w, int s) {
+            auto trace = [&](const T* src, const T(&w)[NP], int s) {
                 T acc = T(0);
 #pragma unroll
                 for (int m = 0; m < NP; ++m) acc += w[m] * src[(m * S + s) * Q + tq];
@@ -229,14 +253,14 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
             T uLf[S], uRf[S], nL[S], nR[S], fDL[S], fDR[S], fIL[S], fIR[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                uLf[s] = trace(own, slm, s);
-                uRf[s] = trace(own, slp, s);
-                fDL[s] = trace(fown, slm, s);
-                fDR[s] = trace(fown, slp, s);
+                uLf[s] = trace(own, rlm, s);
+                uRf[s] = trace(own, rlp, s);
+                fDL[s] = trace(fown, rlm, s);
+                fDR[s] = trace(fown, rlp, s);
             }
             if (hasL) {
 #pragma unroll
-                for (int s = 0; s < S; ++s) nL[s] = trace(sUn + (size_t)(r - 1) * nsz, slp, s);
+                for (int s = 0; s < S; ++s) nL[s] = trace(sUn + (size_t)(r - 1) * nsz, rlp, s);
             } else if (A.bc[0] == FRSG_BC_DIRICHLET) {
                 const double* gh = A.ghost;
 #pragma unroll
@@ -250,7 +274,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
             }
             if (hasR) {
 #pragma unroll
-                for (int s = 0; s < S; ++s) nR[s] = trace(sUn + (size_t)(r + 1) * nsz, slm, s);
+                for (int s = 0; s < S; ++s) nR[s] = trace(sUn + (size_t)(r + 1) * nsz, rlm, s);
             } else if (A.bc[1] == FRSG_BC_DIRICHLET) {
                 const double* gh = A.ghost + (size_t)M * S;
 #pragma unroll
@@ -266,30 +290,32 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
             face_flux<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma, A.flux);
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                T d = (fIL[s] - fDL[s]) * sdhL[tj] + (fIR[s] - fDR[s]) * sdhR[tj];
+                T d = (fIL[s] - fDL[s]) * rdhL + (fIR[s] - fDR[s]) * rdhR;
 #pragma unroll
-                for (int m = 0; m < NP; ++m) d += sD[tj * NP + m] * fown[(m * S + s) * Q + tq];
+                for (int m = 0; m < NP; ++m) d += rD[m] * fown[(m * S + s) * Q + tq];
                 sG[(r * NP + tj) * GR + s * Q + tq] = -invJ * d;
             }
         }
         __syncthreads();
 
         // the last stage stores to global memory: first make sure that every CTA reading
-        // these elements as its halo has loaded them
-        if (st == 2) {
-            int ok = 1;
-            if (nb >= 0) {
-                const long long t0 = clock64();
-                while ((long long)(seen - token) < 0) {
-                    if (clock64() - t0 > kFusedWaitCycles) {
-                        atomicOr(a0.err, kErrTimeout);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
-                    seen = tok_read(tok + nb);
+        // these elements as its halo has loaded them.  The verdict travels with the next
+        // barrier that precedes a global store (before the projection without the filter,
+        // before the detector with it).
+        int ok = 1;
+        if (st == 2 && nb >= 0) {
+            const long long t0 = clock64();
+            while ((long long)(seen - token) < 0) {
+                if (clock64() - t0 > kFusedWaitCycles) {
+                    atomicOr(a0.err, kErrTimeout);
+                    ok = 0;
+                    break;
                 }
+                __nanosleep(64);
+                seen = tok_read(tok + nb);
             }
+        }
+        if (st == 2 && !A.do_filter) {
             if (!__syncthreads_and(ok)) return;
         }
 
@@ -303,7 +329,11 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 48 : 64)
                                              AccTerm<T>{nullptr, nullptr, T(0), T(0), T(0)});
         }
         if (A.do_filter) {
-            __syncthreads();
+            if (st == 2) {
+                if (!__syncthreads_and(ok)) return;
+            } else {
+                __syncthreads();
+            }
             T* dst = st < 2 ? sU + (size_t)r * elsz : dst_global;
             bad |= detector_filter_store<T, NP, S, true>(A, sU, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, r, tq, Q, tj, NP,
                                                    out_valid, out_valid, g_r, owned, dst, sK.det, M);
