@@ -40,8 +40,8 @@ struct frsg_ctx {
     double* d_conv = nullptr;     // FP32 contexts: double staging buffer for set/get_state
     double* d_dt = nullptr;       // step size read by the stage kernels (graphs do not depend on dt)
     unsigned* d_bar = nullptr;    // grid-barrier words of the one-launch step (count, generation)
-    unsigned long long* d_tok = nullptr;   // [E] per-tile load tokens of the halo-recomputing step
-    unsigned long long tok_seq = 0;        // token of its last launch
+    unsigned long long* d_tok = nullptr;   // [E] per-tile launch counters of the halo-recomputing step
+    int tok_te = 0;                        // tile those counters were counted with (0: none yet)
     double dt_set = -1.0;         // value last written to d_dt
     uint8_t* d_flags = nullptr;   // [4][E] (rows 0..2 SSP-RK3 stages, row 3 the last RK4 stage)
     double* d_beta = nullptr;     // [4][E]
@@ -418,7 +418,13 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
                 A3[s].TE = c->TE;
                 A3[s].wide = 1;
             }
-            return frsg::launch_fused1d(c->cfg, c->fp64, A3, c->d_tok, ++c->tok_seq, c->stream);
+            if (c->tok_te != c->TE) {
+                // the counters move in lock step only within one tiling
+                cudaError_t e = cudaMemsetAsync(c->d_tok, 0, sizeof(unsigned long long) * c->E, c->stream);
+                if (e != cudaSuccess) return e;
+                c->tok_te = c->TE;
+            }
+            return frsg::launch_fused1d(c->cfg, c->fp64, A3, c->d_tok, c->stream);
         }
         return frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
     }
@@ -494,7 +500,7 @@ bool tile_fits_1d(const frsg_ctx* c, int te, int wide) {
             A3[s].TE = te;
             A3[s].do_filter = c->cfg.filter != FRSG_FILTER_NONE ? 1 : 0;
         }
-        return frsg::launch_fused1d(c->cfg, c->fp64, A3, nullptr, 0, c->stream, true) == cudaSuccess;
+        return frsg::launch_fused1d(c->cfg, c->fp64, A3, nullptr, c->stream, true) == cudaSuccess;
     }
     const int thr = te * c->Q * (wide ? c->Np : 1);
     const size_t sm = wide ? frsg::stage1d_wide_smem_bytes(c->fp64, te, c->Np, c->M, c->Q, c->S)

@@ -137,12 +137,12 @@ int stage1d_batched_blocks_per_sm(bool fp64, int equation, size_t smem);
 cudaError_t launch_step1d(const frsg_config& cfg, bool fp64, const StageArgs* A3, unsigned* bar, int* grid,
                           cudaStream_t st);
 // One SSP-RK3 step as one launch whose CTAs recompute a three-element halo on each side
-// (no grid barrier).  tok: one zeroed word per tile; token: larger than any earlier launch's.
-// Returns cudaErrorCooperativeLaunchTooLarge when the grid cannot be resident at once and
-// cudaErrorInvalidConfiguration when a tile needs more than 1024 threads; check_only: those
-// checks alone, nothing launched.
+// (no grid barrier).  tok: one launch counter per tile, zeroed whenever the tile size changes
+// (every launch of one tiling adds one to each).  Returns cudaErrorCooperativeLaunchTooLarge
+// when the grid cannot be resident at once and cudaErrorInvalidConfiguration when a tile needs
+// more than 1024 threads; check_only: those checks alone, nothing launched.
 cudaError_t launch_fused1d(const frsg_config& cfg, bool fp64, const StageArgs* A3, unsigned long long* tok,
-                           unsigned long long token, cudaStream_t st, bool check_only = false);
+                           cudaStream_t st, bool check_only = false);
 size_t stage1d_fused_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S);
 cudaError_t launch_limit(bool fp64, const LimitArgs& A, cudaStream_t st);
 cudaError_t launch_project(bool fp64, const double* u0, void* uhat, int E, int Np, int M, int Q, int S,

@@ -8,10 +8,10 @@ cudaError_t k1d_stage_f32(const frsg_config& cfg, const StageArgs& A, cudaStream
 cudaError_t k1d_stage_f64(const frsg_config& cfg, const StageArgs& A, cudaStream_t st);
 cudaError_t k1d_step_f32(const frsg_config& cfg, const StageArgs* A3, unsigned* bar, int* grid, cudaStream_t st);
 cudaError_t k1d_step_f64(const frsg_config& cfg, const StageArgs* A3, unsigned* bar, int* grid, cudaStream_t st);
-cudaError_t k1d_fused_f32(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok,
-                          unsigned long long token, cudaStream_t st, bool check_only);
-cudaError_t k1d_fused_f64(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok,
-                          unsigned long long token, cudaStream_t st, bool check_only);
+cudaError_t k1d_fused_f32(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
+                          bool check_only);
+cudaError_t k1d_fused_f64(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
+                          bool check_only);
 cudaError_t k1d_batched_f32(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,
                             cudaStream_t st);
 cudaError_t k1d_batched_f64(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,
@@ -51,11 +51,10 @@ cudaError_t launch_step1d(const frsg_config& cfg, bool fp64, const StageArgs* A3
 }
 
 cudaError_t launch_fused1d(const frsg_config& cfg, bool fp64, const StageArgs* A3, unsigned long long* tok,
-                           unsigned long long token, cudaStream_t st, bool check_only) {
+                           cudaStream_t st, bool check_only) {
     StageArgs B3[3] = {A3[0], A3[1], A3[2]};
     for (int s = 0; s < 3; ++s) prepare_float_scalars(B3[s]);
-    return fp64 ? k1d_fused_f64(cfg, B3, tok, token, st, check_only)
-                : k1d_fused_f32(cfg, B3, tok, token, st, check_only);
+    return fp64 ? k1d_fused_f64(cfg, B3, tok, st, check_only) : k1d_fused_f32(cfg, B3, tok, st, check_only);
 }
 
 int stage1d_batched_blocks_per_sm(bool fp64, int equation, size_t smem) {

@@ -12,9 +12,9 @@ cudaError_t k1d_step_f64(const frsg_config& cfg, const StageArgs* A3, unsigned* 
     return step_np<double>(cfg, A3, bar, grid, st);
 }
 
-cudaError_t k1d_fused_f64(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok,
-                          unsigned long long token, cudaStream_t st, bool check_only) {
-    return fused_np<double>(cfg, A3, tok, token, st, check_only);
+cudaError_t k1d_fused_f64(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
+                          bool check_only) {
+    return fused_np<double>(cfg, A3, tok, st, check_only);
 }
 
 cudaError_t k1d_batched_f64(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,

@@ -13,10 +13,13 @@
 // solution point j of slot r), so the two layouts give the same numbers.
 //
 // The step's output overwrites u^n in place, and the neighbouring CTAs read u^n of this
-// CTA's elements as their halo.  So each CTA, once its loads are done, publishes the launch's
-// token in tok[b]; before storing, it waits (bounded) until every CTA whose window covers its
-// elements has published.  The wait sits after three stages of work, so it rarely spins; the
-// host runs this layout only when the whole grid is resident at once.
+// CTA's elements as their halo.  So tile b keeps a launch counter tok[b]: every launch
+// increments each tile's counter once, after that tile's loads, so the counters move in
+// lock step (the host zeroes them when the tiling changes).  A CTA reads its own count k after
+// griddepcontrol.wait; before storing, it waits (bounded) until every tile whose window covers
+// its elements has reached k + 1.  Nothing launch-specific comes from the host, so the launch
+// may be replayed from a graph.  The wait sits after three stages of work, so it rarely spins;
+// the host runs this layout only when the whole grid is resident at once.
 #pragma once
 
 #include "kern1d.cuh"
@@ -41,8 +44,14 @@ __host__ __device__ inline size_t smem1d_fused_bytes(int TE, int NP, int M, int 
     return n * sizeof(T) + W * sizeof(int) + 16;
 }
 
-__device__ __forceinline__ void tok_publish(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void tok_arrive(unsigned long long* p) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long tok_peek(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ unsigned long long tok_read(const unsigned long long* p) {
@@ -52,15 +61,16 @@ __device__ __forceinline__ unsigned long long tok_read(const unsigned long long*
 }
 
 // a0, a1, a2: the three stages' arguments (same shapes and tables; own coefficients, flags
-// and replay rows).  tok: one word per CTA; token: this launch's value (strictly increasing).
+// and replay rows).  tok: one launch counter per tile.
 // Blocks hold at most 1024 threads.  Scalar float builds may use 72 registers, so that one
 // 896-thread CTA (8 elements) fits an SM with the tables held in registers; the rest 64, the
 // most a 1024-thread block allows.
 template <typename T, int NP, int S, int EQ, int MC = 0, int QC = 0>
 __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
     step1d_fused_kernel(const __grid_constant__ StageArgs a0, const __grid_constant__ StageArgs a1,
-                        const __grid_constant__ StageArgs a2, unsigned long long* tok, unsigned long long token) {
+                        const __grid_constant__ StageArgs a2, unsigned long long* tok) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long s_target;
     constexpr int H = kFusedHalo;
     const int Q = QC ? QC : a0.Q, M = MC ? MC : a0.M, TE = a0.TE, E = a0.E;
     const int W = TE + 2 * H;   // slots (thread rows); a short last tile uses the first ne + 2H
@@ -129,6 +139,11 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         for (int i = tid; i < NP * M; i += nthr) cp_async(sLam + i, tab + a0.off.lam + i);
     }
     pdl_wait();
+    // this tile's launch count before this launch (only this tile's CTAs ever add to it, and the
+    // previous one has finished): the neighbours must reach one more before the final store.
+    // Issued ahead of the state copies and consumed after them, so that the latencies overlap.
+    unsigned long long own = 0;
+    if (tid == nthr - 1) own = tok_peek(tok + blockIdx.x);
     {
         const T* uin = static_cast<const T*>(a0.uin);   // u^n: the first stage's input and the SSP base
         for (int i = tid; i < W * elsz; i += nthr) {
@@ -141,8 +156,9 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         }
     }
     cp_async_wait_all();
+    if (tid == nthr - 1) s_target = own + 1;
     __syncthreads();
-    if (tid == nthr - 1) tok_publish(tok + blockIdx.x, token);   // this CTA's reads of u^n are done
+    if (tid == nthr - 1) tok_arrive(tok + blockIdx.x);   // this CTA's reads of u^n are done
     const StageConsts<T> K0 = make_consts<T>(a0, dt_raw);
     const T dtT = (T)dt_raw;
     if (a0.do_filter) finish_filter_strengths<T>(a0, NP, sLam, tid, nthr, K0.adt);   // own entries; read after later barriers
@@ -197,7 +213,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         else if (c >= ntiles) c = -1;
         nb = c == (int)blockIdx.x ? -1 : c;
     }
-    unsigned long long seen = token;
+    unsigned long long seen = 0;
     bool bad = false;
 
 #pragma unroll 1
@@ -206,7 +222,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         const StageConsts<T> sK = st == 0 ? K0 : stage_consts(A);
         const bool in_valid = present && r >= st && r <= Wv - 1 - st;
         const bool out_valid = present && r >= st + 1 && r <= Wv - 2 - st;   // st == 2: the owned slots
-        // the neighbours' tokens are read as stage 1 starts and checked before the last
+        // the neighbours' counters are read as stage 1 starts and checked before the last
         // stores; the readers sit in slot 0, which has no work in stages 1 and 2
         if (st == 1 && nb >= 0) seen = tok_read(tok + nb);
 
@@ -305,7 +321,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         int ok = 1;
         if (st == 2 && nb >= 0) {
             const long long t0 = clock64();
-            while ((long long)(seen - token) < 0) {
+            while ((long long)(seen - s_target) < 0) {
                 if (clock64() - t0 > kFusedWaitCycles) {
                     atomicOr(a0.err, kErrTimeout);
                     ok = 0;
@@ -345,7 +361,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
 
 // check_only: run the size and residency checks, launch nothing.
 template <typename T, int NP, int S, int EQ, int MC, int QC>
-cudaError_t fused_mq(const StageArgs* A3, unsigned long long* tok, unsigned long long token, cudaStream_t st,
+cudaError_t fused_mq(const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
                      bool check_only) {
     const int TE = A3[0].TE;
     const int W = TE + 2 * kFusedHalo;
@@ -378,40 +394,40 @@ cudaError_t fused_mq(const StageArgs* A3, unsigned long long* tok, unsigned long
     if (grid > c_resident) return cudaErrorCooperativeLaunchTooLarge;
     if (check_only) return cudaSuccess;
     dim3 block(A3[0].Q, NP, W);
-    return launch_pdl(kern, dim3(grid), block, smem, st, A3[0], A3[1], A3[2], tok, token);
+    return launch_pdl(kern, dim3(grid), block, smem, st, A3[0], A3[1], A3[2], tok);
 }
 
 template <typename T, int NP, int S, int EQ>
-cudaError_t fused_typed(const StageArgs* A3, unsigned long long* tok, unsigned long long token, cudaStream_t st,
+cudaError_t fused_typed(const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
                         bool check_only) {
     if constexpr (NP == 4 && S == 1) {
-        if (A3[0].M == 9 && A3[0].Q == 16) return fused_mq<T, NP, S, EQ, 9, 16>(A3, tok, token, st, check_only);
+        if (A3[0].M == 9 && A3[0].Q == 16) return fused_mq<T, NP, S, EQ, 9, 16>(A3, tok, st, check_only);
     }
     if constexpr (NP == 4 && S == 3) {
-        if (A3[0].M == 7 && A3[0].Q == 12) return fused_mq<T, NP, S, EQ, 7, 12>(A3, tok, token, st, check_only);
+        if (A3[0].M == 7 && A3[0].Q == 12) return fused_mq<T, NP, S, EQ, 7, 12>(A3, tok, st, check_only);
     }
-    return fused_mq<T, NP, S, EQ, 0, 0>(A3, tok, token, st, check_only);
+    return fused_mq<T, NP, S, EQ, 0, 0>(A3, tok, st, check_only);
 }
 
 template <typename T, int NP>
-cudaError_t fused_eq(int eq, const StageArgs* A3, unsigned long long* tok, unsigned long long token, cudaStream_t st,
+cudaError_t fused_eq(int eq, const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
                      bool check_only) {
     switch (eq) {
-        case FRSG_EQ_ADVECTION: return fused_typed<T, NP, 1, FRSG_EQ_ADVECTION>(A3, tok, token, st, check_only);
-        case FRSG_EQ_BURGERS: return fused_typed<T, NP, 1, FRSG_EQ_BURGERS>(A3, tok, token, st, check_only);
-        case FRSG_EQ_EULER: return fused_typed<T, NP, 3, FRSG_EQ_EULER>(A3, tok, token, st, check_only);
+        case FRSG_EQ_ADVECTION: return fused_typed<T, NP, 1, FRSG_EQ_ADVECTION>(A3, tok, st, check_only);
+        case FRSG_EQ_BURGERS: return fused_typed<T, NP, 1, FRSG_EQ_BURGERS>(A3, tok, st, check_only);
+        case FRSG_EQ_EULER: return fused_typed<T, NP, 3, FRSG_EQ_EULER>(A3, tok, st, check_only);
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename T>
-cudaError_t fused_np(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok, unsigned long long token,
-                     cudaStream_t st, bool check_only) {
+cudaError_t fused_np(const frsg_config& cfg, const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
+                     bool check_only) {
     switch (cfg.P + 1) {
-        case 2: return fused_eq<T, 2>(cfg.equation, A3, tok, token, st, check_only);
-        case 3: return fused_eq<T, 3>(cfg.equation, A3, tok, token, st, check_only);
-        case 4: return fused_eq<T, 4>(cfg.equation, A3, tok, token, st, check_only);
-        case 5: return fused_eq<T, 5>(cfg.equation, A3, tok, token, st, check_only);
+        case 2: return fused_eq<T, 2>(cfg.equation, A3, tok, st, check_only);
+        case 3: return fused_eq<T, 3>(cfg.equation, A3, tok, st, check_only);
+        case 4: return fused_eq<T, 4>(cfg.equation, A3, tok, st, check_only);
+        case 5: return fused_eq<T, 5>(cfg.equation, A3, tok, st, check_only);
     }
     return cudaErrorInvalidValue;
 }
