@@ -161,6 +161,16 @@ frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt);
  * use_graph = 1 replays the three stage launches from a captured CUDA graph. */
 frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph);
 
+/* One call from a state to a state: copy uhat_in in (as fr_sg_set_state), take nsteps steps
+ * of fr_sg_rk_step, copy the result out to uhat_out (as fr_sg_get_state).  where: FRSG_HOST
+ * (host arrays; pinned memory gives the fastest copies) or FRSG_DEVICE (device arrays), both
+ * double [E][Np][M][S]; uhat_in and uhat_out may be the same array.  A HOST call synchronises
+ * once, at the end, instead of once per copy; a DEVICE call is asynchronous.  FRSG_E_INVAL
+ * for null arrays, a bad where, dt <= 0 or nsteps < 0 (the state is then unchanged); device
+ * errors as fr_sg_rk_step. */
+frsg_status fr_sg_advance(frsg_ctx* ctx, const double* uhat_in, double* uhat_out, int where, double dt, int nsteps,
+                          int use_graph);
+
 /* Advance the context's state by nsteps steps of size dt of the classical four-stage
  * Runge-Kutta scheme (the integrator of the advection study, §5.1 setup table):
  * y1 = u + dt/2 L(u), y2 = u + dt/2 L(y1), y3 = u + dt L(y2),

@@ -869,6 +869,43 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     return FRSG_OK;
 }
 
+frsg_status fr_sg_advance(frsg_ctx* ctx, const double* uhat_in, double* uhat_out, int where, double dt, int nsteps,
+                          int use_graph) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!uhat_in || !uhat_out) return fail(ctx, FRSG_E_INVAL, "null state");
+    if (where != FRSG_HOST && where != FRSG_DEVICE) return fail(ctx, FRSG_E_INVAL, "where must be HOST or DEVICE");
+    if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
+    const size_t n = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    const bool host = where == FRSG_HOST;
+    // in: straight into the state (FP64) or through the double staging buffer (FP32)
+    if (ctx->fp64) {
+        CK(cudaMemcpyAsync(ctx->d_u, uhat_in, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    } else {
+        cudaError_t e = cudaMemcpyAsync(ctx->d_conv, uhat_in, sizeof(double) * n,
+                                        host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess) e = frsg::launch_convert(ctx->d_conv, ctx->d_u, n, true, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "advance (in)");
+        ctx->launches += 1;
+    }
+    const frsg_status st = fr_sg_rk_step(ctx, dt, nsteps, use_graph);
+    if (st != FRSG_OK) return st;
+    // out, ordered after the steps on the same stream
+    if (ctx->fp64) {
+        CK(cudaMemcpyAsync(uhat_out, ctx->d_u, sizeof(double) * n, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    } else {
+        cudaError_t e = frsg::launch_convert(ctx->d_u, ctx->d_conv, n, false, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(uhat_out, ctx->d_conv, sizeof(double) * n,
+                                host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "advance (out)");
+        ctx->launches += 1;
+    }
+    if (host) CK(cudaStreamSynchronize(ctx->stream));
+    return FRSG_OK;
+}
+
 frsg_status fr_sg_rk4_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     if (!ctx) return FRSG_E_INVAL;
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");

@@ -71,6 +71,8 @@ _SIGNATURES = [
     ("fr_sg_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_rk_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_rk4_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_advance", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int]),
     ("fr_sg_tune_cache_save", ctypes.c_int, [ctypes.c_char_p]),
     ("fr_sg_tune_cache_load", ctypes.c_int, [ctypes.c_char_p]),
     ("fr_sg_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -276,6 +278,20 @@ class Solver:
 
     def rk_step(self, dt, nsteps=1, graph=True):
         self._ck(self.lib.fr_sg_rk_step(self.h, float(dt), int(nsteps), int(bool(graph))), "rk_step")
+
+    def advance(self, u_in, u_out, dt, nsteps=1, graph=True):
+        """fr_sg_advance: state u_in -> nsteps SSP-RK3 steps -> u_out, one call.  numpy float64
+        arrays (host, synchronous) or device float64 tensors [E, Np, M, S]; may be the same."""
+        host = isinstance(u_in, np.ndarray)
+        if host != isinstance(u_out, np.ndarray):
+            raise TypeError("u_in and u_out must both be host arrays or both device tensors")
+        if host:
+            for a in (u_in, u_out):
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != tuple(self.state_shape):
+                    raise ValueError("host states must be C-contiguous float64 arrays of the state shape")
+        self._ck(self.lib.fr_sg_advance(self.h, _ptr(u_in), _ptr(u_out), HOST if host else DEVICE, float(dt),
+                                        int(nsteps), int(bool(graph))), "advance")
+        return u_out
 
     def project(self, u0, uhat):
         """fr_sg_project: device float64 tensors [E, Np, Q, S] -> [E, Np, M, S]."""

@@ -1,0 +1,65 @@
+"""fr_sg_advance: one call from a state to a state must equal fr_sg_set_state, fr_sg_rk_step
+and fr_sg_get_state (bit for bit), for host and device arrays, in place, in both precisions."""
+import numpy as np
+import pytest
+
+from paper_2112_05946_gb300 import frsg, workloads
+from tests.helpers import oracle_problem, solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _front(s, seed):
+    x = s.nodes()[0]
+    u = workloads.random_state(s.state_shape, seed=seed, base=[0.0], amp=[1e-3])
+    u[:, :, 0, 0] += np.tanh((x - 1.0) / 0.05)
+    return u
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("variant", [0, 1, 3])
+def test_advance_equals_set_step_get(precision, variant):
+    import torch
+    wl = workloads.burgers_1d(nx=40)
+    prob = oracle_problem(wl, nx=40)
+    dt = 0.1 * prob.dx / 1.2
+    ref_s = solver(wl, precision=precision)
+    ref_s.set_variant(variant)
+    u = _front(ref_s, seed=5)
+    ref_s.set_state(u)
+    ref_s.rk_step(dt, 3, graph=True)
+    ref_s.check()
+    ref = ref_s.get_state()
+
+    s = solver(wl, precision=precision)
+    s.set_variant(variant)
+    out = np.empty_like(u)
+    s.advance(u, out, dt, 3)
+    s.check()
+    np.testing.assert_array_equal(out, ref)
+    np.testing.assert_array_equal(s.get_state(), ref)    # the context holds the result too
+
+    inplace = u.copy()
+    s.advance(inplace, inplace, dt, 3)
+    np.testing.assert_array_equal(inplace, ref)
+
+    ud = torch.tensor(u, dtype=torch.float64, device="cuda")
+    od = torch.empty_like(ud)
+    s.advance(ud, od, dt, 3)
+    torch.cuda.synchronize()
+    s.check()
+    np.testing.assert_array_equal(od.cpu().numpy(), ref)
+
+
+def test_advance_rejects_bad_arguments_and_keeps_the_state():
+    wl = workloads.burgers_1d(nx=16)
+    s = solver(wl)
+    u = _front(s, seed=2)
+    s.set_state(u)
+    out = np.empty_like(u)
+    with pytest.raises(frsg.FrsgError) as ei:
+        s.advance(u + 1.0, out, -1e-3, 1)
+    assert ei.value.status == frsg.E_INVAL
+    with pytest.raises(frsg.FrsgError):
+        s.advance(u + 1.0, out, 1e-3, -1)
+    np.testing.assert_array_equal(s.get_state(), u)
