@@ -163,7 +163,8 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph);
 
 /* One call from a state to a state: copy uhat_in in (as fr_sg_set_state), take nsteps steps
  * of fr_sg_rk_step, copy the result out to uhat_out (as fr_sg_get_state).  where: FRSG_HOST
- * (host arrays; pinned memory gives the fastest copies) or FRSG_DEVICE (device arrays), both
+ * (host arrays; an FRSG_FP32 context reads and writes pinned ones in place from its
+ * conversion kernels, and copies others through a staging buffer) or FRSG_DEVICE (device arrays), both
  * double [E][Np][M][S]; uhat_in and uhat_out may be the same array.  A HOST call synchronises
  * once, at the end, instead of once per copy; a DEVICE call is asynchronous.  FRSG_E_INVAL
  * for null arrays, a bad where, dt <= 0 or nsteps < 0 (the state is then unchanged); device

@@ -877,14 +877,29 @@ frsg_status fr_sg_advance(frsg_ctx* ctx, const double* uhat_in, double* uhat_out
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
     const size_t n = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
     const bool host = where == FRSG_HOST;
+    // Pinned host arrays are mapped into the device's address space: an FP32 context's
+    // conversion kernels then read and write them in place, without a copy engine transfer
+    // through the staging buffer.  Other host memory goes through the copies.
+    auto mapped = [](const void* p) -> void* {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+    };
     // in: straight into the state (FP64) or through the double staging buffer (FP32)
     if (ctx->fp64) {
         CK(cudaMemcpyAsync(ctx->d_u, uhat_in, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                            ctx->stream));
     } else {
-        cudaError_t e = cudaMemcpyAsync(ctx->d_conv, uhat_in, sizeof(double) * n,
-                                        host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, ctx->stream);
-        if (e == cudaSuccess) e = frsg::launch_convert(ctx->d_conv, ctx->d_u, n, true, ctx->stream);
+        const void* src = host ? mapped(uhat_in) : uhat_in;
+        cudaError_t e = cudaSuccess;
+        if (!src) {
+            e = cudaMemcpyAsync(ctx->d_conv, uhat_in, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream);
+            src = ctx->d_conv;
+        }
+        if (e == cudaSuccess) e = frsg::launch_convert(src, ctx->d_u, n, true, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "advance (in)");
         ctx->launches += 1;
     }
@@ -895,10 +910,10 @@ frsg_status fr_sg_advance(frsg_ctx* ctx, const double* uhat_in, double* uhat_out
         CK(cudaMemcpyAsync(uhat_out, ctx->d_u, sizeof(double) * n, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                            ctx->stream));
     } else {
-        cudaError_t e = frsg::launch_convert(ctx->d_u, ctx->d_conv, n, false, ctx->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(uhat_out, ctx->d_conv, sizeof(double) * n,
-                                host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream);
+        void* dst = host ? mapped(uhat_out) : uhat_out;
+        cudaError_t e = frsg::launch_convert(ctx->d_u, dst ? dst : ctx->d_conv, n, false, ctx->stream);
+        if (e == cudaSuccess && !dst)
+            e = cudaMemcpyAsync(uhat_out, ctx->d_conv, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "advance (out)");
         ctx->launches += 1;
     }

@@ -43,6 +43,14 @@ def test_advance_equals_set_step_get(precision, variant):
     s.advance(inplace, inplace, dt, 3)
     np.testing.assert_array_equal(inplace, ref)
 
+    # pinned host memory (read and written in place by the FP32 conversion kernels)
+    pin_in = torch.tensor(u, dtype=torch.float64).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    s.advance(pin_in.numpy(), pin_out.numpy(), dt, 3)
+    np.testing.assert_array_equal(pin_out.numpy(), ref)
+    s.advance(pin_in.numpy(), pin_in.numpy(), dt, 3)
+    np.testing.assert_array_equal(pin_in.numpy(), ref)
+
     ud = torch.tensor(u, dtype=torch.float64, device="cuda")
     od = torch.empty_like(ud)
     s.advance(ud, od, dt, 3)
