@@ -286,11 +286,17 @@ class Solver:
         if host != isinstance(u_out, np.ndarray):
             raise TypeError("u_in and u_out must both be host arrays or both device tensors")
         if host:
+            nbytes = 8 * self.E * self.Np * self.M * self.S
             for a in (u_in, u_out):
-                if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != tuple(self.state_shape):
-                    raise ValueError("host states must be C-contiguous float64 arrays of the state shape")
-        self._ck(self.lib.fr_sg_advance(self.h, _ptr(u_in), _ptr(u_out), HOST if host else DEVICE, float(dt),
-                                        int(nsteps), int(bool(graph))), "advance")
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.nbytes != nbytes:
+                    raise ValueError("host states must be C-contiguous float64 arrays of the state's size")
+            pin, pout = u_in.ctypes.data, u_out.ctypes.data
+        else:
+            pin, pout = _ptr(u_in), _ptr(u_out)
+        st = self.lib.fr_sg_advance(self.h, pin, pout, HOST if host else DEVICE, float(dt), int(nsteps),
+                                    1 if graph else 0)
+        if st != OK:
+            self._ck(st, "advance")
         return u_out
 
     def project(self, u0, uhat):
