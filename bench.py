@@ -532,7 +532,13 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": round(chosen["achieved_gbs"], 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(chosen["achieved_gbs"] / hbm_peak, 5), "traffic": traffic,
                 "kernel": kname, "peak_source": "measured" if peaks else "fallback",
-                "alg_bytes_per_step": chosen["alg_bytes_per_step"], "stage_us": chosen["stage_us"]}
+                "alg_bytes_per_step": chosen["alg_bytes_per_step"]}
+    if chosen["variant"] in (2, 3):
+        # one launch per step: the timed launch is the step (fr_sg_stage runs single stages in
+        # another layout, so its times do not describe this kernel)
+        roofline["launch_us"] = round(chosen["ms_per_step"] * 1e3, 3)
+    else:
+        roofline["stage_us"] = chosen["stage_us"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
