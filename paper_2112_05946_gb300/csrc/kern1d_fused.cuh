@@ -5,7 +5,8 @@
 // when periodic), and runs the three stages of the step on chip.  Stage s (s = 0, 1, 2)
 // needs valid inputs on slots s .. W-1-s and leaves valid outputs on slots s+1 .. W-2-s,
 // since a residual needs the neighbours' traces (§3.3): after the third stage exactly the
-// owned slots 3 .. TE+2 are valid, and only they are stored.  The halo elements are
+// owned slots 3 .. TE+2 are valid, and only they are stored, in one coalesced sweep after the
+// third stage has finished in shared memory.  The halo elements are
 // recomputed by the neighbouring CTAs too (a stage works on TE+4, TE+2, TE elements), but the
 // stage states u1 and u2 never leave shared memory and a step is one launch.
 //
@@ -314,55 +315,50 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         }
         __syncthreads();
 
-        // the last stage stores to global memory: first make sure that every CTA reading
-        // these elements as its halo has loaded them.  The verdict travels with the next
-        // barrier that precedes a global store (before the projection without the filter,
-        // before the detector with it).
-        int ok = 1;
-        if (st == 2 && nb >= 0) {
-            const long long t0 = clock64();
-            while ((long long)(seen - s_target) < 0) {
-                if (clock64() - t0 > kFusedWaitCycles) {
-                    atomicOr(a0.err, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-                seen = tok_read(tok + nb);
-            }
-        }
-        if (st == 2 && !A.do_filter) {
-            if (!__syncthreads_and(ok)) return;
-        }
-
-        // ---- a4 + a8: projection, SSP combination (in place on the slot, or to global)
-        T* uout = static_cast<T*>(A.uout);
-        T* dst_global = out_valid && st == 2 ? uout + (size_t)g_r * elsz : nullptr;
+        // ---- a4 + a8: projection, SSP combination, in place on the slot
         if (out_valid) {
-            T* dst = (A.do_filter || st < 2) ? sU + (size_t)r * elsz : dst_global;
-            bad |= project_combine<T, NP, S>(sG + r * NP * GR, GR, sU + r * elsz, sB + r * elsz, sPz, dst, M, Q, tq,
-                                             Q, tj, NP, sK.ca, sK.cb, sK.cc, sK.use_base != 0,
-                                             AccTerm<T>{nullptr, nullptr, T(0), T(0), T(0)});
+            bad |= project_combine<T, NP, S>(sG + r * NP * GR, GR, sU + r * elsz, sB + r * elsz, sPz,
+                                             sU + (size_t)r * elsz, M, Q, tq, Q, tj, NP, sK.ca, sK.cb, sK.cc,
+                                             sK.use_base != 0, AccTerm<T>{nullptr, nullptr, T(0), T(0), T(0)});
         }
+        // ---- a9 + a10: detector and filter, in place on the slot
         if (A.do_filter) {
-            if (st == 2) {
-                if (!__syncthreads_and(ok)) return;
-            } else {
-                __syncthreads();
-            }
-            T* dst = st < 2 ? sU + (size_t)r * elsz : dst_global;
+            __syncthreads();
             bad |= detector_filter_store<T, NP, S, true>(A, sU, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, r, tq, Q, tj, NP,
-                                                   out_valid, out_valid, g_r, owned, dst, sK.det, M);
+                                                   out_valid, out_valid, g_r, owned, sU + (size_t)r * elsz, sK.det, M);
         }
         __syncthreads();
+    }
+
+    // The step ends in shared memory (the owned slots).  Before the store over u^n, make sure
+    // that every CTA reading these elements as its halo has loaded them.
+    int ok = 1;
+    if (nb >= 0) {
+        const long long t0 = clock64();
+        while ((long long)(seen - s_target) < 0) {
+            if (clock64() - t0 > kFusedWaitCycles) {
+                atomicOr(a0.err, kErrTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+            seen = tok_read(tok + nb);
+        }
+    }
+    if (!__syncthreads_and(ok)) return;
+    {
+        // one coalesced sweep: the owned slots are consecutive elements in both places
+        T* uout = static_cast<T*>(a2.uout);
+        const size_t gb = (size_t)e0 * elsz;
+        const T* src = sU + (size_t)H * elsz;
+        for (int i = tid; i < ne * elsz; i += nthr) uout[gb + i] = src[i];
     }
     if (bad) atomicOr(a0.err, kErrNonFinite);
 }
 
 // check_only: run the size and residency checks, launch nothing.
 template <typename T, int NP, int S, int EQ, int MC, int QC>
-cudaError_t fused_mq(const StageArgs* A3, unsigned long long* tok, cudaStream_t st,
-                     bool check_only) {
+cudaError_t fused_mq(const StageArgs* A3, unsigned long long* tok, cudaStream_t st, bool check_only) {
     const int TE = A3[0].TE;
     const int W = TE + 2 * kFusedHalo;
     const size_t smem = smem1d_fused_bytes<T>(TE, NP, A3[0].M, A3[0].Q, S);
