@@ -302,6 +302,7 @@ cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
     L.S = c->S;
     L.Np = c->Np;
     L.tab = c->d_tab;
+    L.tabf = c->fp64 ? nullptr : c->d_tabf;
     L.off = c->off;
     L.gamma = c->cfg.gamma;
     L.beta = beta;

@@ -98,6 +98,7 @@ struct LimitArgs {
     void* u;               // state limited in place
     int E, M, Q, S, Np;
     const double* tab;
+    const float* tabf;     // the same table block in float (FP32 contexts), or null
     TabOff off;
     double gamma;
     double* beta;          // [E] recorded scaling (beta1*beta2), or null

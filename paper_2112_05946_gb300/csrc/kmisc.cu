@@ -70,14 +70,19 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
     const size_t elsz = (size_t)NPT * M * S;
     const double* tab = A.tab;
     const double gamma = A.gamma;
+    // the screen reads its tables in T: the float copy of the block for float states (the
+    // same roundings as converting each entry, without a double conversion per use)
+    const T* tabT = sizeof(T) == 4 && A.tabf ? reinterpret_cast<const T*>(A.tabf) : reinterpret_cast<const T*>(tab);
+    const bool tab_is_T = sizeof(T) == 8 || A.tabf != nullptr;
+    auto tabv = [&](int i) -> T { return tab_is_T ? tabT[i] : (T)tab[i]; };
     T lmT[N1], lpT[N1];
     double lmD[N1], lpD[N1];
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
         lmD[j] = tab[A.off.lm + j];
         lpD[j] = tab[A.off.lp + j];
-        lmT[j] = (T)lmD[j];
-        lpT[j] = (T)lpD[j];
+        lmT[j] = tabv(A.off.lm + j);
+        lpT[j] = tabv(A.off.lp + j);
     }
 
     const bool exact = sizeof(T) == sizeof(double);
@@ -90,7 +95,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
         for (int s = 0; s < S; ++s) ub[s] = T(0);
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-            const T wj = (T)tab[A.off.w + j];
+            const T wj = tabv(A.off.w + j);
 #pragma unroll
             for (int s = 0; s < S; ++s) ub[s] += wj * ue[(size_t)j * M * S + s];
         }
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
 #pragma unroll
             for (int s = 0; s < S; ++s) v[s][j] = T(0);
         for (int k = 0; k < M; ++k) {
-            const T vz = (T)tab[A.off.VzT + k * Q + tq];
+            const T vz = tabv(A.off.VzT + k * Q + tq);
 #pragma unroll
             for (int j = 0; j < NPT; ++j)
 #pragma unroll
