@@ -152,7 +152,8 @@ class ClockSampler:
 # DRAM bytes per launch of the benchmark's kernels, from ncu captures of the current build
 # (dram__bytes_read.sum + dram__bytes_write.sum, one launch, L2 flushed by ncu before it;
 # profiles/step1d_fused_burgers_E1024_ncu.md)
-MEASURED_TRAFFIC = {("step1d_fused_kernel", "fp32"): 176896}
+# keyed by (kernel, precision, tile): the halo re-reads depend on the tile
+MEASURED_TRAFFIC = {("step1d_fused_kernel", "fp32", 7): None}
 
 
 def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracle_ref):
@@ -528,7 +529,7 @@ def run_ours(args):
              3: "step1d_fused_kernel"}[chosen["variant"]]
     # DRAM bytes of one launch from the ncu capture of this kernel build; null for a layout
     # without a capture of the current build
-    traffic = MEASURED_TRAFFIC.get((kname, chosen["precision"]))
+    traffic = MEASURED_TRAFFIC.get((kname, chosen["precision"], chosen["tile"]))
     roofline = {"bound": "hbm", "achieved": round(chosen["achieved_gbs"], 2), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(chosen["achieved_gbs"] / hbm_peak, 5), "traffic": traffic,
                 "kernel": kname, "peak_source": "measured" if peaks else "fallback",

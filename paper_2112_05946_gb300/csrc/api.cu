@@ -1199,7 +1199,7 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
     std::vector<std::pair<int, int>> cand;
     const int variants = c.dim == 1 ? (c.limiter ? 2 : 4) : 1;
     for (int w = 0; w < variants; ++w)
-        for (int te : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+        for (int te : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32}) {
             bool fits;
             if (c.dim == 1) {
                 fits = tile_fits_1d(ctx, te, w == 2 ? 0 : w);
