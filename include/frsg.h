@@ -238,12 +238,13 @@ uint64_t fr_sg_batch_launch_count(const frsg_batch* b);
 /* Tile count, persistent grid size and dynamic shared memory per CTA of the batched launch. */
 frsg_status fr_sg_batch_info(const frsg_batch* b, int* ntiles, int* grid, size_t* smem);
 
-/* Discrete adjoint of fr_sg_rk_step for 1D FRSG_FP64 contexts with the LLF flux and no
- * filter, the exponential or the L2 filter: periodic advection / Burgers, or Euler with any
- * 1D boundary kind, with or without the positivity limiter (FRSG_E_UNSUPPORTED otherwise).
- * The paper has no adjoint; it is the exact transpose of the linearised scheme of §2.1-§4.3
- * with the filter decisions of the forward run frozen, the Lax-Friedrichs dissipation
- * max(lambda_L, lambda_R) differentiated along the branch the forward values take, and the
+/* Discrete adjoint of fr_sg_rk_step for 1D FRSG_FP64 contexts with no filter, the
+ * exponential or the L2 filter: periodic advection / Burgers with the LLF flux, or Euler with
+ * the LLF or HLL flux, any 1D boundary kind, with or without the positivity limiter
+ * (FRSG_E_UNSUPPORTED otherwise).  The paper has no adjoint; it is the exact transpose of the
+ * linearised scheme of §2.1-§4.3 with the filter decisions of the forward run frozen, the
+ * Lax-Friedrichs dissipation max(lambda_L, lambda_R) and the HLL branch and signal speeds
+ * min / max differentiated along the branch the forward values take (ties shared equally), and the
  * limiter differentiated through its scalings beta_1 and beta_2 (eps held constant; the
  * minimising points are those of the forward values).
  *

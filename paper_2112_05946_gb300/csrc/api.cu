@@ -1288,11 +1288,12 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
 static frsg_status adjoint_supported(frsg_ctx* ctx) {
     const frsg_config& c = ctx->cfg;
     const bool euler = c.equation == FRSG_EQ_EULER;
-    if (c.dim != 1 || !ctx->fp64 || c.filter == FRSG_FILTER_LASSO || c.flux != FRSG_FLUX_LLF ||
-        (!euler && (c.limiter || c.bc[0] != FRSG_BC_PERIODIC)))
+    if (c.dim != 1 || !ctx->fp64 || c.filter == FRSG_FILTER_LASSO ||
+        (!euler && (c.flux != FRSG_FLUX_LLF || c.limiter || c.bc[0] != FRSG_BC_PERIODIC)))
         return fail(ctx, FRSG_E_UNSUPPORTED,
-                    "the adjoint covers 1D FRSG_FP64 contexts with the LLF flux and a linear (exponential or L2) "
-                    "filter: periodic advection/Burgers, or Euler with any 1D boundary kind and the limiter");
+                    "the adjoint covers 1D FRSG_FP64 contexts with a linear (exponential or L2) filter: periodic "
+                    "advection/Burgers with the LLF flux, or Euler with the LLF or HLL flux, any 1D boundary kind and "
+                    "the limiter");
     return FRSG_OK;
 }
 
@@ -1587,7 +1588,7 @@ frsg_status fr_sg_adjoint(frsg_ctx* ctx, const double* lambda_T, double* grad_u0
                     CK(frsg::launch_adjoint_stage_euler1d(c.P, segV + (size_t)s * nstate, y, t2, lb, ca[s], cb[s],
                                                           cb[s] * dt, s == 2 ? 1 : 0, s == 0 ? 1 : 0, ctx->d_tab,
                                                           ctx->off, ctx->E, ctx->M, ctx->Q, invJx, c.gamma, c.bc[0],
-                                                          c.bc[1], ctx->d_ghost, ctx->stream));
+                                                          c.bc[1], ctx->d_ghost, c.flux, ctx->stream));
                 } else {
                     CK(frsg::launch_adjoint_stage1d(c.P, c.equation, segV + (size_t)s * nstate, y, t2, lb, ca[s],
                                                     cb[s], cb[s] * dt, s == 2 ? 1 : 0, s == 0 ? 1 : 0, ctx->d_tab,

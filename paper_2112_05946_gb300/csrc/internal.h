@@ -163,7 +163,8 @@ cudaError_t launch_filter_transpose(int P, const double* mu, double* out, const 
 cudaError_t launch_adjoint_stage_euler1d(int P, const double* v, const double* y, double* lam_v, double* lam_base,
                                          double a, double b, double cdt, int base_init, int accumulate,
                                          const double* tab, TabOff off, int E, int M, int Q, double invJx,
-                                         double gamma, int bcL, int bcR, const double* ghost, cudaStream_t st);
+                                         double gamma, int bcL, int bcR, const double* ghost, int flux,
+                                         cudaStream_t st);
 cudaError_t launch_limiter_adjoint1d(int P, const double* y, const double* vbar, double* ybar, int E, int M, int Q,
                                      const double* tab, TabOff off, double gamma, cudaStream_t st);
 cudaError_t launch_adjoint_stage1d(int P, int equation, const double* v, const double* y, double* lam_v,

@@ -93,6 +93,67 @@ struct Euler1 {
             for (int s = 0; s < 3; ++s) gR[s] -= 0.5 * dot * gl[s];
         }
     }
+    // the Davis speeds v - c, v + c and their gradients
+    __device__ void speeds(const double (&u)[3], double* lo, double* hi, double (&glo)[3], double (&ghi)[3]) const {
+        double v, p, c;
+        prim(u, &v, &p, &c);
+        const double g1 = gamma - 1.0, rho = u[0];
+        const double k = gamma / (2.0 * c * rho);
+        const double gv[3] = {-v / rho, 1.0 / rho, 0.0};
+        const double gc[3] = {k * (0.5 * g1 * v * v - p / rho), k * (-g1 * v), k * g1};
+        *lo = v - c;
+        *hi = v + c;
+        for (int s = 0; s < 3; ++s) {
+            glo[s] = gv[s] - gc[s];
+            ghi[s] = gv[s] + gc[s];
+        }
+    }
+    // (dF/du_L)^T Fb and (dF/du_R)^T Fb of the HLL flux (§5.3-5.4 setup tables) with
+    // S_L = min(v_L - c_L, v_R - c_R), S_R = max(v_L + c_L, v_R + c_R).  The branch follows
+    // the values; a tie in the min or max shares the derivative equally between its arguments.
+    __device__ void hll_vjp(const double (&uL)[3], const double (&uR)[3], const double (&Fb)[3], double (&gL)[3],
+                            double (&gR)[3]) const {
+        double loL, hiL, loR, hiR, gloL[3], ghiL[3], gloR[3], ghiR[3];
+        speeds(uL, &loL, &hiL, gloL, ghiL);
+        speeds(uR, &loR, &hiR, gloR, ghiR);
+        const double SL = fmin(loL, loR), SR = fmax(hiL, hiR);
+        for (int s = 0; s < 3; ++s) gL[s] = gR[s] = 0.0;
+        if (SL >= 0.0) {
+            jac_t(uL, Fb, gL);
+            return;
+        }
+        if (SR <= 0.0) {
+            jac_t(uR, Fb, gR);
+            return;
+        }
+        // F = (S_R f_L - S_L f_R + S_L S_R (u_R - u_L)) / (S_R - S_L), S_L < 0 < S_R
+        const double D = SR - SL;
+        double fL[3], fR[3], F[3], jl[3], jr[3];
+        flux(uL, fL);
+        flux(uR, fR);
+        jac_t(uL, Fb, jl);
+        jac_t(uR, Fb, jr);
+        double dSL = 0.0, dSR = 0.0;   // Fb . dF/dS_L and Fb . dF/dS_R
+        for (int s = 0; s < 3; ++s) {
+            const double du = uR[s] - uL[s];
+            F[s] = (SR * fL[s] - SL * fR[s] + SL * SR * du) / D;
+            gL[s] = (SR * jl[s] - SL * SR * Fb[s]) / D;
+            gR[s] = (-SL * jr[s] + SL * SR * Fb[s]) / D;
+            dSL += Fb[s] * (F[s] - fR[s] + SR * du) / D;
+            dSR += Fb[s] * (fL[s] + SL * du - F[s]) / D;
+        }
+        const double wl = loL < loR ? 1.0 : (loL > loR ? 0.0 : 0.5);   // share of S_L owed to u_L
+        const double wh = hiL > hiR ? 1.0 : (hiL < hiR ? 0.0 : 0.5);   // share of S_R owed to u_L
+        for (int s = 0; s < 3; ++s) {
+            gL[s] += dSL * wl * gloL[s] + dSR * wh * ghiL[s];
+            gR[s] += dSL * (1.0 - wl) * gloR[s] + dSR * (1.0 - wh) * ghiR[s];
+        }
+    }
+    __device__ void face_vjp(int kind, const double (&uL)[3], const double (&uR)[3], const double (&Fb)[3],
+                             double (&gL)[3], double (&gR)[3]) const {
+        if (kind == FRSG_FLUX_HLL) hll_vjp(uL, uR, Fb, gL, gR);
+        else llf_vjp(uL, uR, Fb, gL, gR);
+    }
 };
 
 // Ghost of a boundary face from the interior trace t at z-node q, and the map of the ghost's
@@ -122,7 +183,7 @@ template <int NP>
 __global__ void __launch_bounds__(256) adjoint_stage_euler_kernel(
     const double* v, const double* y, double* lam_v, double* lam_base, double a, double b, double cdt, int base_init,
     int accumulate, const double* tab, TabOff off, int E, int M, int Q, int TE, double invJx, double gamma, int bcL,
-    int bcR, const double* ghost) {
+    int bcR, const double* ghost, int flux) {
     constexpr int S = 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tq = threadIdx.x, te = threadIdx.y;
@@ -236,7 +297,7 @@ __global__ void __launch_bounds__(256) adjoint_stage_euler_kernel(
                 ghost_state(bcL, own_l, ghost, sVz, M, Q, tq, left);
                 for (int s = 0; s < S; ++s) Fb[s] = gLo[s];
             }
-            eu.llf_vjp(left, own_l, Fb, gl, gr);
+            eu.face_vjp(flux, left, own_l, Fb, gl, gr);
             for (int s = 0; s < S; ++s) bbar[s] += gr[s];
             if (!interior) ghost_back(bcL, gl, bbar);
         }
@@ -253,7 +314,7 @@ __global__ void __launch_bounds__(256) adjoint_stage_euler_kernel(
                 ghost_state(bcR, own_r, ghost + (size_t)M * S, sVz, M, Q, tq, right);
                 for (int s = 0; s < S; ++s) Fb[s] = gRo[s];
             }
-            eu.llf_vjp(own_r, right, Fb, gl, gr);
+            eu.face_vjp(flux, own_r, right, Fb, gl, gr);
             for (int s = 0; s < S; ++s) abar[s] += gl[s];
             if (!interior) ghost_back(bcR, gr, abar);
         }
@@ -443,7 +504,7 @@ template <int NP>
 cudaError_t euler_adj_launch(const double* v, const double* y, double* lam_v, double* lam_base, double a, double b,
                              double cdt, int base_init, int accumulate, const double* tab, TabOff off, int E, int M,
                              int Q, int TE, double invJx, double gamma, int bcL, int bcR, const double* ghost,
-                             cudaStream_t st) {
+                             int flux, cudaStream_t st) {
     constexpr int S = 3;
     const size_t smem = sizeof(double) * ((size_t)2 * (TE + 2) * NP * M * S + (size_t)TE * NP * S * Q +
                                           (size_t)4 * (TE + 2) * S * Q + (size_t)2 * M * Q) + 16;
@@ -454,7 +515,7 @@ cudaError_t euler_adj_launch(const double* v, const double* y, double* lam_v, do
     }
     dim3 block(Q, TE), grid((E + TE - 1) / TE);
     k<<<grid, block, smem, st>>>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx,
-                                 gamma, bcL, bcR, ghost);
+                                 gamma, bcL, bcR, ghost, flux);
     return cudaGetLastError();
 }
 
@@ -463,13 +524,14 @@ cudaError_t euler_adj_launch(const double* v, const double* y, double* lam_v, do
 cudaError_t launch_adjoint_stage_euler1d(int P, const double* v, const double* y, double* lam_v, double* lam_base,
                                          double a, double b, double cdt, int base_init, int accumulate,
                                          const double* tab, TabOff off, int E, int M, int Q, double invJx,
-                                         double gamma, int bcL, int bcR, const double* ghost, cudaStream_t st) {
+                                         double gamma, int bcL, int bcR, const double* ghost, int flux,
+                                         cudaStream_t st) {
     const int TE = Q * 4 <= 256 ? 4 : 1;
     switch (P + 1) {
-        case 2: return euler_adj_launch<2>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, st);
-        case 3: return euler_adj_launch<3>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, st);
-        case 4: return euler_adj_launch<4>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, st);
-        case 5: return euler_adj_launch<5>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, st);
+        case 2: return euler_adj_launch<2>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, flux, st);
+        case 3: return euler_adj_launch<3>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, flux, st);
+        case 4: return euler_adj_launch<4>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, flux, st);
+        case 5: return euler_adj_launch<5>(v, y, lam_v, lam_base, a, b, cdt, base_init, accumulate, tab, off, E, M, Q, TE, invJx, gamma, bcL, bcR, ghost, flux, st);
     }
     return cudaErrorInvalidValue;
 }

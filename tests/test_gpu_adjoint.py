@@ -129,13 +129,13 @@ def test_autograd_function_gives_the_adjoint_gradient():
 
 
 def test_adjoint_rejects_unsupported_contexts():
-    """FP32 states, 2D meshes, the HLL flux, the Lasso filter and non-periodic scalar problems
-    have no adjoint."""
+    """FP32 states, 2D meshes, scalar problems with the HLL flux, the Lasso filter and
+    non-periodic scalar problems have no adjoint."""
     from paper_2112_05946_gb300 import frsg
     cases = [
         solver(workloads.sod_1d(nx=8), precision="fp32"),
         solver(workloads.shock_vortex_2d(nx=4, ny=4)),
-        solver(workloads.sod_1d(nx=8), flux="hll"),
+        solver(_burgers(nx=8), flux="hll"),
         solver(_burgers(nx=8), filter="lasso", sensor=False),
         solver(_burgers(nx=8), bc=("outflow", "outflow", "periodic", "periodic")),
     ]

@@ -1,5 +1,5 @@
 """Discrete adjoint of 1D Euler runs on the GPU (fr_sg_forward_record / fr_sg_adjoint) against
-the reverse-mode oracle (oracle.adjoint1d): the LLF flux, Dirichlet, outflow, reflecting and
+the reverse-mode oracle (oracle.adjoint1d): the LLF and HLL fluxes, Dirichlet, outflow, reflecting and
 periodic ends, the filter (decisions frozen) and the positivity limiter differentiated through
 its scalings (the stochastic-location Sod state, where the limiter acts from the first stage)."""
 import numpy as np
@@ -58,9 +58,45 @@ def test_euler_adjoint_smooth_states(bc):
     _run_case(wl, prob, u0, 3, 2)
 
 
-def test_euler_adjoint_rejects_hll():
+@pytest.mark.parametrize("bc", [("dirichlet", "dirichlet"), ("outflow", "reflect"), ("periodic", "periodic")])
+def test_euler_adjoint_hll_smooth_states(bc):
+    """The HLL flux's transpose, with subsonic faces (the HLL middle state and its signal-speed
+    derivatives) and every boundary kind."""
+    wl = workloads.sod_location_1d(nx=12, P=3, N=4, Q=8, filter="l2")
+    wl["solver"].update(flux="hll", sensor=False, bc=bc + ("periodic", "periodic"))
+    prob = oracle_problem(wl)
+    u0 = workloads.random_state((prob.E, prob.Np, prob.M, prob.S), seed=8, base=[1.0, 0.3, 2.5],
+                                amp=[0.05, 0.1, 0.1])
+    _run_case(wl, prob, u0, 3, 2)
+
+
+@pytest.mark.parametrize("vel", [2.2, -2.2])
+def test_euler_adjoint_hll_supersonic(vel):
+    """Supersonic flow: every face takes the upwind branch of HLL."""
+    wl = workloads.sod_location_1d(nx=10, P=2, N=3, Q=6, filter="l2")
+    wl["solver"].update(flux="hll", sensor=False, bc=("periodic",) * 4)
+    prob = oracle_problem(wl)
+    u0 = workloads.random_state((prob.E, prob.Np, prob.M, prob.S), seed=4, base=[1.0, vel, 4.0],
+                                amp=[0.02, 0.05, 0.05])
+    _run_case(wl, prob, u0, 2, 1)
+
+
+@pytest.mark.parametrize("nsteps,k", [(3, 2)])
+def test_euler_adjoint_hll_with_active_limiter(nsteps, k):
+    wl = workloads.sod_location_1d(nx=16, P=2, N=3, Q=5, filter="l2")
+    wl["solver"]["flux"] = "hll"
+    wl["solver"]["sensor"] = False
+    prob = oracle_problem(wl)
+    u0 = oracle_initial(prob, wl)
+    rec = []
+    capture.limit(prob, prob.tabs(), u0, record=rec)
+    assert np.sum(rec[0] < 1.0) >= 2
+    _run_case(wl, prob, u0, nsteps, k)
+
+
+def test_scalar_adjoint_rejects_hll():
     from paper_2112_05946_gb300 import frsg
-    wl = workloads.sod_location_1d(nx=8, P=2, N=3, Q=5)
-    s = solver(wl)
+    wl = workloads.burgers_1d(nx=8)
+    s = solver(wl, flux="hll")
     with pytest.raises(frsg.FrsgError):
         s.forward_record(1e-4, 2, 1)
