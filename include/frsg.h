@@ -274,12 +274,24 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out);
  * without limiter; FRSG_E_UNSUPPORTED when no tile fits: 7*Q*(P+1) > 1024, or every tile's
  * grid too large to be resident at once).  Before storing the step, a
  * CTA waits until the CTAs reading its elements as halo have loaded them (a wait longer than
- * about 2 s latches FRSG_E_TIMEOUT and the CTA stores nothing); the tile is the number of
+ * about 2 s latches FRSG_E_TIMEOUT and the CTA stores nothing, while other CTAs may have stored:
+ * the state is then partly advanced and must be reloaded); the tile is the number of
  * elements a CTA finishes, and the launch is refused (FRSG_E_CUDA from the step) when its
  * grid cannot be resident at once.  With layout 3, single stages (fr_sg_stage, fr_sg_rhs,
  * the recorded run) run layout 1.  All compute the same stage; the tile is re-chosen
  * automatically.  2D contexts accept only 0 (FRSG_E_UNSUPPORTED otherwise). */
 frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant);
+
+/* Test hook of the one-launch step (layout 3 of fr_sg_set_variant).  wait_cycles > 0 bounds the
+ * neighbour wait before the final store to that many SM clock cycles (0 restores the default of
+ * about 2 s).  hold_tile >= 0 (layout 3 only; FRSG_E_UNSUPPORTED otherwise, FRSG_E_INVAL past the
+ * last tile) adds 2^40 to that tile's launch counter, as if a CTA reading its elements as halo had
+ * never loaded them: in the next step that tile's wait cannot be met, so after wait_cycles it
+ * latches FRSG_E_TIMEOUT (reported by fr_sg_check) and stores nothing, while the other tiles store
+ * their new elements; the counters are re-zeroed before the step after.  After FRSG_E_TIMEOUT from
+ * this layout the state is therefore partly advanced: reload it before stepping on.  Drops the
+ * cached step graphs.  Synchronises. */
+frsg_status fr_sg_test_fused_wait(frsg_ctx* ctx, long long wait_cycles, int hold_tile);
 
 /* Autotuner: times graph-replayed SSP-RK3 steps (reps per candidate, default 20; CUDA
  * events on the context's stream) for every layout (1D) and tile that fits, re-times the
@@ -317,13 +329,15 @@ uint64_t fr_sg_launch_count(const frsg_ctx* ctx);
  *
  * cfg: as for fr_sg_init, with dim = 1 and precision = FRSG_FP64 (FRSG_E_UNSUPPORTED otherwise).
  * ghost_modes: host [4][M][S] gPC modes of the Dirichlet sides' ghost states (the modes that
- *   fr_sg_set_boundary_nodal computes), or NULL when no side is Dirichlet.
+ *   fr_sg_set_boundary_nodal computes), or NULL when no side is Dirichlet (FRSG_E_INVAL when a
+ *   Dirichlet side has none).
  * u_in, u_out: device double [E][Np][M][S]; u_out receives the state after nsteps steps of
  *   size dt of the same scheme as fr_sg_rk_step (limiter, residual, SSP combination, detector
  *   and filter per stage); u_in == u_out is allowed.
  * stream: a cudaStream_t.  The work is enqueued there and the call synchronises that stream
  *   before it returns, so that it can report the errors kernels latch (FRSG_E_NONFINITE,
- *   FRSG_E_POSITIVITY).
+ *   FRSG_E_POSITIVITY).  A call that fails after it has queued work (FRSG_E_CUDA) also waits
+ *   for that work before it returns.
  * The first call on a device looks up the device address of the static array, with that
  * device current; make that first call before any stream capture.  Every call shares the
  * array and leaves its contents behind: each call clears what must start at zero (the

@@ -42,6 +42,8 @@ struct frsg_ctx {
     unsigned* d_bar = nullptr;    // grid-barrier words of the one-launch step (count, generation)
     unsigned long long* d_tok = nullptr;   // [E] per-tile launch counters of the halo-recomputing step
     int tok_te = 0;                        // tile those counters were counted with (0: none yet)
+    long long fused_wait = 0;              // neighbour-wait bound of layout 3 in SM cycles (0: default)
+    bool tok_reset_next = false;           // re-zero the counters before the step after the next
     double dt_set = -1.0;         // value last written to d_dt
     uint8_t* d_flags = nullptr;   // [4][E] (rows 0..2 SSP-RK3 stages, row 3 the last RK4 stage)
     double* d_beta = nullptr;     // [4][E]
@@ -418,6 +420,7 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
             for (int s = 0; s < 3; ++s) {
                 A3[s].TE = c->TE;
                 A3[s].wide = 1;
+                A3[s].wait_cycles = c->fused_wait;
             }
             if (c->tok_te != c->TE) {
                 // the counters move in lock step only within one tiling
@@ -425,7 +428,13 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
                 if (e != cudaSuccess) return e;
                 c->tok_te = c->TE;
             }
-            return frsg::launch_fused1d(c->cfg, c->fp64, A3, c->d_tok, c->stream);
+            cudaError_t e = frsg::launch_fused1d(c->cfg, c->fp64, A3, c->d_tok, c->stream);
+            if (c->tok_reset_next) {
+                // a held counter (fr_sg_test_fused_wait) broke the lock step: re-zero next time
+                c->tok_te = 0;
+                c->tok_reset_next = false;
+            }
+            return e;
         }
         return frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
     }
@@ -1282,6 +1291,30 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant) {
                     "no tile of the halo-recomputing step fits: 7*Q*(P+1) > 1024 threads, or no grid small "
                     "enough to be resident at once");
     }
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_test_fused_wait(frsg_ctx* ctx, long long wait_cycles, int hold_tile) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (wait_cycles < 0) return fail(ctx, FRSG_E_INVAL, "wait_cycles must be >= 0");
+    if (hold_tile >= 0 && !(ctx->cfg.dim == 1 && ctx->wide == 3 && one_launch_step(ctx)))
+        return fail(ctx, FRSG_E_UNSUPPORTED, "a held tile needs the halo-recomputing step (layout 3)");
+    const int ntiles = (ctx->E + ctx->TE - 1) / ctx->TE;
+    if (hold_tile >= ntiles) return fail(ctx, FRSG_E_INVAL, "hold_tile beyond the last tile");
+    drop_graphs(ctx);
+    ctx->fused_wait = wait_cycles;
+    if (hold_tile < 0) return FRSG_OK;
+    if (ctx->tok_te != ctx->TE) {
+        CK(cudaMemsetAsync(ctx->d_tok, 0, sizeof(unsigned long long) * ctx->E, ctx->stream));
+        ctx->tok_te = ctx->TE;
+    }
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, ctx->d_tok + hold_tile, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    v += 1ull << 40;
+    CK(cudaMemcpyAsync(ctx->d_tok + hold_tile, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->tok_reset_next = true;
     return FRSG_OK;
 }
 

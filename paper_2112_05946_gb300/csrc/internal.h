@@ -69,6 +69,7 @@ struct StageArgs {
     unsigned* err;
     int TE;                // elements per block
     int wide;              // 1D: one thread per (z-node, point) instead of per z-node
+    long long wait_cycles; // bound of the one-launch step's neighbour wait in SM cycles (0: default)
     // optional second output of the same residual (the RK4 weighted sum of the L's):
     // acc_out = acc_a*acc_in + acc_b*uin + acc_c*dt*L(uin), unfiltered; null = none
     void* acc_out;

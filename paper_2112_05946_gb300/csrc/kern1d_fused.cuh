@@ -335,8 +335,9 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
     int ok = 1;
     if (nb >= 0) {
         const long long t0 = clock64();
+        const long long limit = a0.wait_cycles > 0 ? a0.wait_cycles : kFusedWaitCycles;
         while ((long long)(seen - s_target) < 0) {
-            if (clock64() - t0 > kFusedWaitCycles) {
+            if (clock64() - t0 > limit) {
                 atomicOr(a0.err, kErrTimeout);
                 ok = 0;
                 break;

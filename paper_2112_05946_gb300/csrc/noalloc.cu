@@ -28,24 +28,31 @@ constexpr int kTabCap = 4096;                // doubles; 1D tables need < 1500
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device with that device current.
+// Device address of g_noalloc_scratch and the SM count, looked up once per device with that
+// device current.
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_mu;                 // guards g_scratch_ptr and the host staging arrays below
+int g_sm_count[kMaxDevices] = {};
+std::mutex g_mu;                 // guards the per-device caches and the host staging arrays below
 double g_host_tab[kTabCap];
 double g_host_ghost[4 * frsg::kMaxM * 3];
 
-cudaError_t scratch_for_current_device(unsigned char** out) {
+cudaError_t scratch_for_current_device(unsigned char** out, int* sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     if (!g_scratch_ptr[dev]) {
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
+        g_sm_count[dev] = n > 0 ? n : 1;
         g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
     }
     *out = g_scratch_ptr[dev];
+    *sms = g_sm_count[dev];
     return cudaSuccess;
 }
 
@@ -210,6 +217,10 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
         std::fprintf(stderr, "fr_sg_rk_step_noalloc: the exponential and L2 filters only\n");
         return FRSG_E_UNSUPPORTED;
     }
+    if (!ghost_modes && (cfg->bc[0] == FRSG_BC_DIRICHLET || cfg->bc[1] == FRSG_BC_DIRICHLET)) {
+        std::fprintf(stderr, "fr_sg_rk_step_noalloc: a Dirichlet side needs ghost_modes\n");
+        return FRSG_E_INVAL;
+    }
     const int n1 = cfg->P + 1, M = cfg->N + 1, Q = cfg->Q, E = cfg->nx;
     const int S = cfg->equation == FRSG_EQ_EULER ? 3 : 1;
     const size_t nstate = (size_t)E * n1 * M * S;
@@ -233,7 +244,8 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
         return FRSG_E_INVAL;
     }
     unsigned char* base = nullptr;
-    if (scratch_for_current_device(&base) != cudaSuccess) return FRSG_E_CUDA;
+    int sms = 1;
+    if (scratch_for_current_device(&base, &sms) != cudaSuccess) return FRSG_E_CUDA;
     unsigned* d_err = reinterpret_cast<unsigned*>(base + o_err);
     double* d_dt = reinterpret_cast<double*>(base + o_dt);
     double* d_ghost = reinterpret_cast<double*>(base + o_ghost);
@@ -250,9 +262,15 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, g_host_tab, sizeof(double) * ntab, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && u_out != u_in)
         e = cudaMemcpyAsync(u_out, u_in, sizeof(double) * nstate, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return FRSG_E_CUDA;
+    // From here on work may be queued on st: every exit waits for it, so that the lock is
+    // released only once no kernel of this call still uses the shared scratch.
+    auto finish = [&](frsg_status status) {
+        cudaStreamSynchronize(st);
+        return status;
+    };
+    if (e != cudaSuccess) return finish(FRSG_E_CUDA);
 
-    int te = E / (2 * 152);
+    int te = E / (2 * sms);
     if (te < 1) te = 1;
     if (te > 512 / Q) te = 512 / Q;
     while (te > 1 && stage1d_smem_bytes(true, te, n1, M, Q, S) > 200 * 1024) --te;
@@ -306,7 +324,7 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
                 L.err = d_err;
                 L.dim = 1;
                 L.TE = 256 / Q > 0 ? 256 / Q : 1;
-                if (launch_limit(true, L, st) != cudaSuccess) return FRSG_E_CUDA;
+                if (launch_limit(true, L, st) != cudaSuccess) return finish(FRSG_E_CUDA);
             }
             A.uin = bin[s];
             A.ubase = u_out;
@@ -314,11 +332,12 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
             A.a = ca[s];
             A.b = cb[s];
             A.c = cb[s];
-            if (launch_stage1d(*cfg, true, A, st) != cudaSuccess) return FRSG_E_CUDA;
+            if (launch_stage1d(*cfg, true, A, st) != cudaSuccess) return finish(FRSG_E_CUDA);
         }
     }
     unsigned err = 0;
-    if (cudaMemcpyAsync(&err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FRSG_E_CUDA;
+    if (cudaMemcpyAsync(&err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return finish(FRSG_E_CUDA);
     if (cudaStreamSynchronize(st) != cudaSuccess) return FRSG_E_CUDA;
     if (err & kErrPositivity) return FRSG_E_POSITIVITY;
     if (err & kErrNonFinite) return FRSG_E_NONFINITE;

@@ -88,6 +88,7 @@ _SIGNATURES = [
     ("fr_sg_launch_count", ctypes.c_uint64, [ctypes.c_void_p]),
     ("fr_sg_set_tile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("fr_sg_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_test_fused_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
     ("fr_sg_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     ("fr_sg_forward_record", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
@@ -171,14 +172,38 @@ def tune_cache_load(path):
         raise FrsgError(st, f"fr_sg_tune_cache_load({path}) failed")
 
 
+def check_noalloc_args(u_in, u_out, ghost_modes, cfg):
+    """Argument checks of rk_step_noalloc, made before the library is called: both states are
+    contiguous CUDA float64 tensors of E*Np*M*S values for the configuration, and the ghost
+    modes (when given) have shape (4, M, S).  The kernels index the states by the
+    configuration's sizes, so a smaller or mistyped tensor would be read and written out of
+    bounds.  Raises FrsgError(E_INVAL) and returns the ghost modes as a contiguous array."""
+    P, N = cfg.get("P", 2), cfg.get("N", 4)
+    equation = cfg.get("equation", "advection")
+    S = 3 if equation == "euler" else 1
+    want = int(cfg.get("nx", 32)) * (P + 1) * (N + 1) * S
+    for name, t in (("u_in", u_in), ("u_out", u_out)):
+        if str(getattr(t, "dtype", None)) != "torch.float64":
+            raise FrsgError(E_INVAL, f"rk_step_noalloc: {name} must be a torch.float64 tensor")
+        if not getattr(t, "is_cuda", False):
+            raise FrsgError(E_INVAL, f"rk_step_noalloc: {name} must be on a CUDA device")
+        if not t.is_contiguous() or t.numel() != want:
+            raise FrsgError(E_INVAL, f"rk_step_noalloc: {name} must be contiguous with {want} values "
+                                     f"(nx*(P+1)*(N+1)*S), got {t.numel()}")
+    if ghost_modes is None:
+        return None
+    g = np.ascontiguousarray(ghost_modes, dtype=np.float64)
+    if g.shape != (4, N + 1, S):
+        raise FrsgError(E_INVAL, f"rk_step_noalloc: ghost_modes must have shape (4, {N + 1}, {S}), got {g.shape}")
+    return g
+
+
 def rk_step_noalloc(u_in, u_out, dt, nsteps=1, ghost_modes=None, stream=None, **cfg):
     """fr_sg_rk_step_noalloc: nsteps SSP-RK3 steps of a 1D FP64 problem for callers that may
     not allocate device memory; u_in, u_out are device float64 tensors [E, Np, M, S]."""
+    g = check_noalloc_args(u_in, u_out, ghost_modes, cfg)
     lib = load_library()
     c = make_config(**cfg)
-    g = None
-    if ghost_modes is not None:
-        g = np.ascontiguousarray(ghost_modes, dtype=np.float64)
     st = lib.fr_sg_rk_step_noalloc(ctypes.byref(c), _ptr(g), _ptr(u_in), _ptr(u_out), float(dt), int(nsteps),
                                    ctypes.c_void_p(stream or 0))
     if st != OK:
@@ -373,6 +398,11 @@ class Solver:
         v, t = ctypes.c_int(), ctypes.c_int()
         self._ck(self.lib.fr_sg_autotune(self.h, int(reps), ctypes.byref(v), ctypes.byref(t)), "autotune")
         return v.value, t.value
+
+    def test_fused_wait(self, wait_cycles=0, hold_tile=-1):
+        """fr_sg_test_fused_wait: bound the one-launch step's neighbour wait, and optionally hold
+        one tile's launch counter so that its next wait runs out."""
+        self._ck(self.lib.fr_sg_test_fused_wait(self.h, int(wait_cycles), int(hold_tile)), "test_fused_wait")
 
     def set_variant(self, variant):
         """1D layout: 0 thread per (z-node, element), 1 thread per (z-node, point, element),

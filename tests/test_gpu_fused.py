@@ -185,3 +185,39 @@ def test_fused_step_replays_from_a_captured_graph():
     ref.rk_step(dt, 10, graph=True)
     ref.check()
     assert rel_l2(s.get_state(), ref.get_state()) < SAME["fp64"]
+
+
+def test_fused_wait_runs_out_when_a_tile_is_held():
+    """The neighbour wait before the final store is bounded: hold one tile's launch counter so
+    that its target cannot be reached, with a short bound, and the step reports FRSG_E_TIMEOUT;
+    the held tile stores nothing (its elements keep u^n) while every other tile stores the same
+    new elements as an ordinary step.  The following step re-zeroes the counters and runs."""
+    wl = workloads.burgers_1d(nx=256)
+    s = solver(wl)
+    s.set_variant(3)
+    te = s.set_tile(4)
+    u = _front_state(s, seed=5)
+    dt = 0.1 * (2.0 / 256) / 1.2
+    # reference: an ordinary step of the same layout
+    s.set_state(u)
+    s.rk_step(dt, 1, graph=False)
+    s.check()
+    ref = s.get_state()
+    hold = 9                                 # elements 36 .. 39
+    s.set_state(u)
+    s.test_fused_wait(wait_cycles=2_000_000, hold_tile=hold)   # about 1 ms
+    s.rk_step(dt, 1, graph=False)
+    with pytest.raises(frsg.FrsgError) as ei:
+        s.check()
+    assert ei.value.status == frsg.E_TIMEOUT
+    got = s.get_state()
+    mine = np.zeros(256, dtype=bool)
+    mine[hold * te:(hold + 1) * te] = True
+    np.testing.assert_array_equal(got[mine], u[mine])
+    np.testing.assert_array_equal(got[~mine], ref[~mine])
+    # the counters are re-zeroed and the next step completes
+    s.test_fused_wait(0, -1)
+    s.set_state(u)
+    s.rk_step(dt, 1, graph=False)
+    s.check()
+    np.testing.assert_array_equal(s.get_state(), ref)

@@ -26,11 +26,21 @@ def _ghost_modes(wl, M, S, Q):
     return out
 
 
-@pytest.mark.parametrize("name,nx,nsteps", [("burgers", 1024, 5), ("sod", 512, 3), ("advection", 32, 10)])
+def _workload(name, nx):
+    if name == "advection":
+        return workloads.advection_1d()
+    if name == "sod_location_l2":
+        # HLL flux, L2 filter behind the detector, limiter, Dirichlet ends
+        return workloads.sod_location_1d(nx=nx, filter="l2")
+    return workloads.ALL[name](nx=nx)
+
+
+@pytest.mark.parametrize("name,nx,nsteps", [("burgers", 1024, 5), ("sod", 512, 3), ("advection", 32, 10),
+                                             ("sod_location_l2", 100, 3)])
 def test_noalloc_matches_context_path_on_two_calls(name, nx, nsteps):
     import torch
     from paper_2112_05946_gb300 import frsg
-    wl = workloads.ALL[name]() if name == "advection" else workloads.ALL[name](nx=nx)
+    wl = _workload(name, nx)
     s = solver(wl)
     gpu_initial(s, wl)
     u0 = torch.tensor(s.get_state(), dtype=torch.float64, device="cuda")
@@ -62,4 +72,15 @@ def test_noalloc_rejects_oversized_problem():
     u = torch.zeros((65536, 4, 9, 1), dtype=torch.float64, device="cuda")
     with pytest.raises(frsg.FrsgError) as ei:
         frsg.rk_step_noalloc(u, u, 1e-4, 1, **cfg)
+    assert ei.value.status == frsg.E_INVAL
+
+
+def test_noalloc_rejects_dirichlet_without_ghost_modes():
+    import torch
+    from paper_2112_05946_gb300 import frsg
+    wl = workloads.sod_1d(nx=64)
+    cfg = dict(wl["solver"])
+    u = torch.zeros((64, 4, 7, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(frsg.FrsgError) as ei:
+        frsg.rk_step_noalloc(u, u, 1e-4, 1, ghost_modes=None, **cfg)
     assert ei.value.status == frsg.E_INVAL
