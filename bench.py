@@ -1,25 +1,33 @@
 #!/usr/bin/env python
 """Throughput of the FR-SG stage on GB300: DOF-stage updates per second.
 
-A "step" is one SSP-RK3 time step (three fused stage launches: z-evaluation, flux,
-Galerkin projection, FR derivative with LLF + Radau correction, SSP combination,
-detector and filter) of the stochastic Burgers workload: 1024 elements, P = 3,
-N = 8, Q = 16 (36,864 DOF), exponential filter switched by the detector, CFL 0.1.
-DOF = elements x solution points x gPC modes x variables; one step is 3 DOF-stages
-per DOF.  Both the plain FP64 form and the FP32 form are measured; the line reports
-the faster form whose error against the FP64 oracle meets its stated bound.
+Headline workload: the stochastic 2D shock-vortex interaction (§5.4 family), 256 x 128
+quads, tensor-product FR with P = 3 (16 points per element), gPC degree N = 4 with Q = 8
+z-nodes, four conserved variables: 10,485,760 DOF.  L2 filter behind the detector and the
+positivity limiter on every stage input.  A "step" is one SSP-RK3 step: per stage the
+limiter launch and the stage kernel (z-evaluation, flux, projection, FR derivative with the
+interface flux and Radau correction, SSP combination, detector and filter), replayed from a
+CUDA graph.  DOF = elements x points x gPC modes x variables; a step is 3 DOF-stages per DOF.
 
-Timing: W untimed steps, then K steps each bracketed by CUDA events on the solver's
-stream, with a 256 MiB memset between timed steps to flush the 129 MB L2 (the state
-is 0.3 MB, so every timed step starts from HBM).  Max over ranks under torchrun
-(N > 1 runs independent replicas: "weak" scaling, no collective on the data path).
+Both the plain FP64 form and the FP32 form are timed, and each is compared with the FP64
+oracle after one step from the initial state (on windows of the mesh that the oracle
+reproduces exactly).  The line reports the faster form whose error meets its stated bound,
+with the other beside it.
 
---impl reference times the FP64 CPU oracle (numpy, one core) on the same workload.
+Timing: W untimed steps, then K steps each bracketed by CUDA events on the solver's stream,
+with a 256 MiB memset between timed steps that flushes the 129 MB L2.  The stage kernels are
+timed alone with events recorded between the limiter and the stage kernel.  Max over ranks
+under torchrun (N > 1 runs independent replicas: "weak" scaling, no collective on the data
+path).  The oracle runs in spawned worker processes while the GPU is timed.
+
+--impl reference times the FP64 CPU oracle on a 32 x 16-element patch of the same problem.
 """
 import argparse
+import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -36,22 +44,30 @@ from paper_2112_05946_gb300 import workloads  # noqa: E402
 
 METRIC = "DOF-stage updates/s"
 UNIT = "DOF-stage/s"
-ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5}     # relative L2 vs the FP64 oracle after the accuracy run
-ACC_STEPS = 50
+HEADLINE = "shock_vortex"
+# relative L2 against the FP64 oracle (the FP32 bound of the 1D shock workloads covers the
+# limiter's FP32 target, 1e-5 of the element mean above eps)
+ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5}
+ERR_BOUND_SHOCK_FP32 = 1e-3
+# oracle windows of the 256 x 128 mesh: inflow boundary and vortex, shock face at the bottom
+# wall, outflow corner at the top wall
+WINDOWS = [(0, 48, 40, 88), (56, 72, 0, 24), (232, 256, 104, 128)]
+PATCH = dict(nx=32, ny=16)          # the oracle's bounded sample of the headline problem
+CFL_2D = 0.05
 
 
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="burgers", choices=sorted(workloads.ALL))
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="single-thread oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the Sod, 2D, batched and adjoint lines")
-    ap.add_argument("--only", default=None, choices=["burgers", "sod", "shock_vortex", "batch", "adjoint"],
-                    help="measure one extra workload alone and print its line (for profiling runs)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads' lines")
+    ap.add_argument("--only", default=None,
+                    choices=["shock_vortex", "advection", "burgers", "sod", "batch", "adjoint", "peak"],
+                    help="measure one workload alone and print its result (profiling runs)")
     return ap.parse_args(argv)
 
 
@@ -90,11 +106,65 @@ def dist_env():
 def workload_sizes(wl):
     s = wl["solver"]
     n1 = s["P"] + 1
-    E = s["nx"] * (s.get("ny", 1) if s.get("dim", 1) == 2 else 1)
-    Np = n1 ** s.get("dim", 1)
+    dim = s.get("dim", 1)
+    E = s["nx"] * (s.get("ny", 1) if dim == 2 else 1)
+    Np = n1 ** dim
     M = s["N"] + 1
-    S = 1 if s["equation"] != "euler" else (3 if s.get("dim", 1) == 1 else 4)
+    S = 1 if s["equation"] != "euler" else (3 if dim == 1 else 4)
     return E, Np, M, S
+
+
+def flops_per_dof_stage(wl):
+    """Algorithmic flops per DOF-stage of the modal scheme (one model for every workload):
+    z-evaluation 2Q, projection 2Q, face evaluation and projection 2 d 2 2Q / (P+1),
+    derivative 2 (P+1) d, correction 4 d, flux c_f Q / M, combination 5, with c_f the flops of
+    one flux evaluation per variable and point (advection 1, Burgers 2, Euler 20/3 in 1D,
+    10 per direction pair in 2D)."""
+    s = wl["solver"]
+    d = s.get("dim", 1)
+    n1, Q, M = s["P"] + 1, s["Q"], s["N"] + 1
+    cf = {"advection": 1.0, "burgers": 2.0}.get(s["equation"], 20.0 / 3.0 if d == 1 else 10.0)
+    return 2 * Q + 2 * Q + 2 * d * 2 * 2 * Q / n1 + 2 * n1 * d + 4 * d + cf * Q / M + 5
+
+
+def src_hash(*names):
+    """Hash of the kernel sources a figure was measured on."""
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2112_05946_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+KERNEL_SOURCES = {"stage2d_kernel": ("kern2d.cu", "epilogue.cuh", "physics.cuh", "internal.h", "pdl.cuh"),
+                  "limit_kernel": ("kmisc.cu", "limiter.cuh", "internal.h")}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from an ncu capture,
+# keyed by kernel, precision and tile, with the hash of the sources it was captured on: a
+# figure whose sources have changed since is not reported.
+MEASURED_TRAFFIC = {}
+
+
+def measured_traffic(kernel, precision, tile):
+    rec = MEASURED_TRAFFIC.get((kernel, precision, tile))
+    if not rec:
+        return None, "no ncu capture of this kernel, precision and tile"
+    nbytes, h = rec
+    if h != src_hash(*KERNEL_SOURCES[kernel]):
+        return None, "the kernel's sources changed since the ncu capture"
+    return nbytes, f"ncu capture of this build (sources {h}), one launch"
+
+
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
 
 
 # ---------------------------------------------------------------- clocks
@@ -147,197 +217,367 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- our arm
+# ---------------------------------------------------------------- oracle jobs (worker processes)
+#
+# Workloads hold functions, so jobs name them: (factory name, keyword arguments, solver
+# overrides).  Each worker rebuilds the workload and runs the plain oracle.
 
-# DRAM bytes per launch of the benchmark's kernels, from ncu captures of the current build
-# (dram__bytes_read.sum + dram__bytes_write.sum, one launch, L2 flushed by ncu before it;
-# profiles/step1d_fused_burgers_E1024_ncu.md)
-# keyed by (kernel, precision, tile): the halo re-reads depend on the tile
-MEASURED_TRAFFIC = {("step1d_fused_kernel", "fp32", 7): 177408}
+def _spec_workload(spec):
+    name, kw, over = spec
+    wl = getattr(workloads, name)(**kw)
+    wl["solver"].update(over)
+    return wl
 
 
-def measure_form(torch, frsg, wl, precision, steps, warmup, stream, flush, oracle_ref):
+def _oracle_problem(wl):
+    import oracle
+    from oracle import tables
+    prob = oracle.Problem(**wl["solver"])
+    if "boundary" in wl:
+        g = tables.gpc_tables(prob.N, prob.Q)
+        prob.dirichlet = {side: g["Pz"] @ workloads.boundary_values(fn, g["z"])
+                          for side, fn in wl["boundary"].items()}
+    return prob
+
+
+def job_windows(spec, cfl, nsteps):
+    """Oracle windows of a 2D workload after nsteps steps from the projected initial state;
+    the step size from the oracle's CFL condition on that state."""
+    from oracle import integrate, windows
+    wl = _spec_workload(spec)
+    prob = _oracle_problem(wl)
+    u0 = integrate.project_initial(prob, wl["ic"])
+    dt = integrate.cfl_dt(prob, prob.tabs(), u0, cfl)
+    out = []
+    for box in WINDOWS:
+        full, got = windows.run_window(prob, u0, box, dt, nsteps)
+        out.append((full, got))
+    return dt, out
+
+
+def job_run_1d(spec, cfl, nsteps, integrator="ssp3", limit_first=False):
+    """The oracle's state after nsteps steps of a 1D workload from the projected initial state.
+    cfl: a number (dt from the oracle's CFL condition on the initial state) or None (dt from
+    the workload's fixed wave speed lam0)."""
+    from oracle import capture, integrate
+    wl = _spec_workload(spec)
+    prob = _oracle_problem(wl)
+    tabs = prob.tabs()
+    u = integrate.project_initial(prob, wl["ic"])
+    if cfl is None:
+        dt = wl["cfl"] * prob.dx / wl["lam0"]
+    else:
+        v = capture.limit(prob, tabs, u) if limit_first else u
+        dt = integrate.cfl_dt(prob, tabs, v, cfl)
+    step = integrate.rk4_step if integrator == "rk4" else integrate.ssp_rk3_step
+    for _ in range(nsteps):
+        u = step(prob, tabs, u, dt)
+    return dt, u
+
+
+def job_patch_steps(nsteps, seconds=0.0):
+    """Time the oracle on the 32 x 16 patch of the headline problem: nsteps SSP-RK3 steps, or as
+    many as fit in `seconds` (at least two).  Returns (steps, wall seconds, DOF)."""
+    from oracle import integrate
+    wl = workloads.shock_vortex_2d(**PATCH)
+    prob = _oracle_problem(wl)
+    tabs = prob.tabs()
+    u = integrate.project_initial(prob, wl["ic"])
+    dt = integrate.cfl_dt(prob, tabs, u, CFL_2D)
     E, Np, M, S = workload_sizes(wl)
-    dof = E * Np * M * S
+    n = 0
+    t0 = time.perf_counter()
+    while (n < nsteps) if seconds <= 0 else (time.perf_counter() - t0 < seconds or n < 2):
+        u = integrate.ssp_rk3_step(prob, tabs, u, dt)
+        n += 1
+    return n, time.perf_counter() - t0, E * Np * M * S
+
+
+def _pool(n):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    return cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn"))
+
+
+def cpu_baseline(seconds):
+    """The oracle on a 32 x 16-element patch of the headline problem (same P, N, Q, variables,
+    limiter and filter): one thread for `seconds`, then one process per host core running the
+    same sample side by side.  Reported value: the all-core aggregate."""
+    n1, t1, dof = job_patch_steps(0, seconds)
+    single = dof * 3 * n1 / t1
+    cores = os.cpu_count() or 1
+    steps = max(2, int(round(n1 * 0.5)))
+    t0 = time.perf_counter()
+    with _pool(cores) as ex:
+        res = list(ex.map(job_patch_steps, [steps] * cores))
+    wall = time.perf_counter() - t0
+    total = sum(dof * 3 * r[0] for r in res)
+    return dict(value=total / wall, unit=UNIT, cores=cores, kind="oracle",
+                sample=(f"numpy FP64 oracle on a 32x16-element patch of the shock_vortex problem (P=3, N=4, Q=8, "
+                        f"S=4, limiter, L2 filter; {dof} DOF): {cores} processes x {steps} SSP-RK3 steps side by "
+                        f"side, {wall:.1f} s wall; single thread: {n1} steps in {t1:.1f} s"),
+                single_thread={"value": single, "cores": 1, "steps": n1, "seconds": t1},
+                host=host_info())
+
+
+# ---------------------------------------------------------------- our arm: GPU measurements
+
+def rel_l2(a, b):
+    den = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b) / (den if den > 0 else 1.0))
+
+
+def coef_err(a, b):
+    """Largest coefficient error relative to the largest |value| of its variable."""
+    scale = np.max(np.abs(b), axis=tuple(range(b.ndim - 1)))
+    scale = np.where(scale > 0, scale, 1.0)
+    return float(np.max(np.abs(a - b) / scale))
+
+
+def new_solver(frsg, wl, stream, precision):
     s = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
-    variant, tile = s.autotune()
-    x, z = s.nodes()
-    u0 = workloads.nodal_values(wl["ic"], x, z)
-    dx = (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"]
-    dt = wl["cfl"] * dx / wl["lam0"]
-    esz = 8 if precision == "fp64" else 4
+    nodes = s.nodes()
+    if "boundary" in wl:
+        for side, fn in wl["boundary"].items():
+            s.set_boundary_nodal(side, workloads.boundary_values(fn, nodes[-1]))
+    return s
 
-    # accuracy run against the FP64 oracle
-    s.set_initial_nodal(u0)
-    s.rk_step(dt, ACC_STEPS, graph=True)
-    s.check()
-    got = s.get_state()
-    err = float(np.linalg.norm(got - oracle_ref) / np.linalg.norm(oracle_ref))
 
-    # throughput: per-step events with an L2 flush between steps
-    s.set_initial_nodal(u0)
+def set_initial(s, wl):
+    nodes = s.nodes()
+    if len(nodes) == 2:
+        s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[1]))
+    else:
+        s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[2], nodes[1]))
+
+
+def time_steps(torch, s, stream, flush, dt, steps, warmup, rk4=False, refresh=None):
+    """Per-step CUDA events over `steps` graph-replayed steps after `warmup`, L2 flushed before
+    each; refresh(i) may return a new dt (outside the events).  Returns (ms list, launches)."""
+    adv = s.rk4_step if rk4 else s.rk_step
     with torch.cuda.stream(stream):
-        s.rk_step(dt, warmup, graph=True)
+        adv(dt, warmup, graph=True)
         stream.synchronize()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         l0 = s.launch_count()
         torch.cuda.nvtx.range_push("timed")            # profilers can select the timed launches
         for i in range(steps):
+            if refresh is not None:
+                dt = refresh(i, dt)
             flush.zero_()
             starts[i].record(stream)
-            s.rk_step(dt, 1, graph=True)
+            adv(dt, 1, graph=True)
             ends[i].record(stream)
         torch.cuda.nvtx.range_pop()
         stream.synchronize()
-        launches = s.launch_count() - l0
-        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], s.launch_count() - l0, dt
 
-        # kernel durations: the three stage launches timed one by one (same flush)
-        kst = min(steps, 200)
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kst)]
-        for i in range(kst):
-            flush.zero_()
-            evs[i][0].record(stream)
+
+def time_kernels(torch, s, stream, flush, dt, reps):
+    """Stage by stage (fr_sg_stage, same launches as a step), L2 flushed before each stage:
+    events before the limiter, between it and the stage kernel, after the stage kernel.
+    Returns mean ms per stage of (limiter, stage kernel), each a list of three."""
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(3)] for _ in range(reps)]
+    with torch.cuda.stream(stream):
+        for row in evs:                  # torch creates the CUDA event at its first record
+            for trio in row:
+                for e in trio:
+                    e.record(stream)
+        for i in range(reps):
             for st in range(3):
+                e = evs[i][st]
+                s.set_timing_events(*e)
+                flush.zero_()
                 s.stage(st, dt)
-                evs[i][st + 1].record(stream)
         stream.synchronize()
-        stage_ms = [[evs[i][st].elapsed_time(evs[i][st + 1]) for st in range(3)] for i in range(kst)]
+    s.set_timing_events(None, None, None)
+    lim = np.array([[evs[i][st][0].elapsed_time(evs[i][st][1]) for st in range(3)] for i in range(reps)])
+    ker = np.array([[evs[i][st][1].elapsed_time(evs[i][st][2]) for st in range(3)] for i in range(reps)])
+    return lim.mean(axis=0).tolist(), ker.mean(axis=0).tolist()
 
-        # steady state: back-to-back graph replays, state resident in L2 (context only)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        s.rk_step(dt, steps, graph=True)
-        ev1.record(stream)
-        stream.synchronize()
-        steady_ms = ev0.elapsed_time(ev1) / steps
-    s.check()
 
-    # end to end through the public API with host buffers: pinned host state in, step, state out
-    h_in = torch.empty((E, Np, M, S), dtype=torch.float64, pin_memory=True)
-    h_in.copy_(torch.from_numpy(got))
-    h_out = torch.empty_like(h_in)
-    e2e_steps = min(steps, 200)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    hi, ho = h_in.numpy(), h_out.numpy()
-    for _ in range(e2e_steps):
-        s.advance(hi, ho, dt, 1)             # state in, one step, state out: one call, one sync
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    s.close()
-
-    ms = float(np.mean(step_ms))
-    mean_stage = np.mean(np.array(stage_ms), axis=0)           # ms per stage launch
-    if variant == 3:
-        # one launch per step whose stage states stay on chip: it must read u^n and write
-        # u^{n+1}, two state arrays per step
-        alg_bytes = [2 * esz * dof]
+def roofline(kernel, precision, tile, ms_per_launch, dof, wl, peaks):
+    """Roofline of one stage-kernel launch: algorithmic bytes 24 (FP64) / 12 (FP32) per
+    DOF-stage (read the stage input and u^n, write the output) against the measured HBM copy
+    bandwidth, and algorithmic flops against the measured FMA throughput of the form's
+    precision.  `bound` names the tighter of the two."""
+    esz = 8 if precision == "fp64" else 4
+    alg_bytes = 3 * esz * dof
+    alg_flops = flops_per_dof_stage(wl) * dof
+    sec = ms_per_launch * 1e-3
+    hbm = peaks["hbm_gbs"]
+    fma = peaks["fp64_tflops" if precision == "fp64" else "fp32_tflops"]
+    t_hbm = alg_bytes / (hbm * 1e9)
+    t_alu = alg_flops / (fma * 1e12) if fma else 0.0
+    traffic, tsrc = measured_traffic(kernel, precision, tile)
+    gbs = alg_bytes / sec / 1e9
+    tfl = alg_flops / sec / 1e12
+    out = {"kernel": kernel, "launch_us": round(ms_per_launch * 1e3, 3), "alg_bytes_per_launch": alg_bytes,
+           "alg_flops_per_launch": alg_flops, "traffic": traffic, "traffic_source": tsrc,
+           "hbm": {"achieved": round(gbs, 2), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 5),
+                   "peak_source": peaks["hbm_source"]},
+           "alu": {"achieved": round(tfl, 4), "peak": fma, "unit": "TFLOP/s",
+                   "frac": round(tfl / fma, 5) if fma else None,
+                   "peak_source": peaks["fma_source"]}}
+    if t_alu > t_hbm:
+        out.update(bound="alu", achieved=out["alu"]["achieved"], peak=fma, unit="TFLOP/s", frac=out["alu"]["frac"])
     else:
-        arrays = [2, 3, 3]                                     # state arrays read+written per stage
-        alg_bytes = [a * esz * dof for a in arrays]
-    if variant in (2, 3):
-        # one launch per step: the timed step is the kernel
-        achieved = sum(alg_bytes) / (ms * 1e-3) / 1e9
-    else:
-        achieved = sum(alg_bytes) / (sum(mean_stage) * 1e-3) / 1e9  # GB/s over the stage kernels
-    return dict(
-        precision=precision, value=dof * 3 / (ms * 1e-3), ms_per_step=ms, err_vs_oracle=err,
-        err_bound=ERR_BOUND[precision], dof=dof, launches=launches, steady_ms=steady_ms,
-        stage_us=[float(v * 1e3) for v in mean_stage], achieved_gbs=achieved,
-        alg_bytes_per_step=sum(alg_bytes), e2e_value=dof * 3 / e2e_s, e2e_ms=e2e_s * 1e3,
-        h2d=dof * 8, d2h=dof * 8, variant=variant, tile=tile,
-    )
+        out.update(bound="hbm", achieved=out["hbm"]["achieved"], peak=hbm, unit="GB/s", frac=out["hbm"]["frac"])
+    return out
 
 
-def measure_extra(torch, frsg, wl, precision, steps, warmup, stream, flush, integrator="ssp3"):
-    """Throughput of another workload (FP64 or FP32 form): per-step events with the L2
-    flush between steps, dt from the CFL condition refreshed every 20 steps outside the timed
-    events, plus the stage-kernel duration (limiter launches, if any, timed with their
-    stage).  integrator "rk4" times classical RK4 steps (four stages; per-stage time = step
-    time / 4)."""
-    rk4 = integrator == "rk4"
-    nst = 4 if rk4 else 3
-    lim = bool(wl["solver"].get("limiter"))
+def measure_headline(torch, frsg, precision, args, stream, flush, peaks, oracle_dt, oracle_windows):
+    """The headline workload in one precision: throughput, kernel times, end to end, error."""
+    wl = workloads.shock_vortex_2d()
     E, Np, M, S = workload_sizes(wl)
     dof = E * Np * M * S
-    esz = 8 if precision == "fp64" else 4
-    s = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
-    s.autotune()
-    nodes = s.nodes()
-    if "boundary" in wl:
-        for side, fn in wl["boundary"].items():
-            s.set_boundary_nodal(side, workloads.boundary_values(fn, nodes[-1]))
-    if len(nodes) == 2:
-        s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[1]))
-    else:
-        s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[2], nodes[1]))
-    # half the CFL number of the correctness runs, refreshed every 20 steps outside the timed
-    # events: the Euler wave speeds grow after t = 0.  With the limiter on, the state is
-    # limited before each refresh (a projection discontinuous in z, or a filtered stage
-    # output, can leave inadmissible z-node states that the next stage would limit anyway).
-    cfl = 0.5 * wl["cfl"]
+    s = new_solver(frsg, wl, stream, precision)
+    variant, tile = s.autotune()
+    set_initial(s, wl)
 
-    def refresh_dt():
-        if lim:
+    def refresh(i, dt):
+        # the Euler wave speeds grow after t = 0: a new dt every 20 steps, outside the events
+        if i % 20 == 0:
             s.limit()
-        return s.cfl_dt(cfl)
-    dt = refresh_dt()
-    advance = s.rk4_step if rk4 else s.rk_step
+            return s.cfl_dt(CFL_2D)
+        return dt
+
+    dt = s.cfl_dt(CFL_2D)
+    step_ms, launches, dt = time_steps(torch, s, stream, flush, dt, args.steps, args.warmup, refresh=refresh)
+    lim_ms, ker_ms = time_kernels(torch, s, stream, flush, dt, max(3, min(args.steps, 10)))
     with torch.cuda.stream(stream):
-        advance(dt, warmup, graph=True)
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        for i in range(steps):
-            if i % 20 == 0:
-                dt = refresh_dt()
-            flush.zero_()
-            starts[i].record(stream)
-            advance(dt, 1, graph=True)
-            ends[i].record(stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.rk_step(dt, args.steps, graph=True)
+        ev1.record(stream)
         stream.synchronize()
-        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-        kst = 0 if rk4 else min(steps, 50)
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kst)]
-        for i in range(kst):
-            flush.zero_()
-            evs[i][0].record(stream)
-            for st in range(3):
-                s.stage(st, dt)
-                evs[i][st + 1].record(stream)
+    steady_ms = ev0.elapsed_time(ev1) / args.steps
+    s.check()
+
+    # end to end through fr_sg_advance with pinned host buffers: state in, one step, state out
+    h_in = torch.empty((E, Np, M, S), dtype=torch.float64, pin_memory=True)
+    s.get_state(h_in.numpy())
+    h_out = torch.empty_like(h_in)
+    hi, ho = h_in.numpy(), h_out.numpy()
+    n_e2e = max(3, min(args.steps, 10))
+    s.advance(hi, ho, dt, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        s.advance(hi, ho, dt, 1)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+
+    # accuracy: one step from the projected initial state with the oracle's step size
+    set_initial(s, wl)
+    s.rk_step(oracle_dt, 1, graph=False)
+    s.check()
+    got = s.get_state()
+    s.close()
+    errs = [(rel_l2(got[full], ref), coef_err(got[full], ref)) for full, ref in oracle_windows]
+    ms = float(np.mean(step_ms))
+    kernel_ms = float(np.mean(ker_ms))
+    return dict(precision=precision, value=dof * 3 / (ms * 1e-3), ms_per_step=ms, steady_ms_per_step=steady_ms,
+                dof=dof, launches=launches, variant=variant, tile=tile,
+                limiter_us=[v * 1e3 for v in lim_ms], stage_kernel_us=[v * 1e3 for v in ker_ms],
+                err_vs_oracle=max(e[0] for e in errs), coef_err_vs_oracle=max(e[1] for e in errs),
+                err_bound=ERR_BOUND[precision],
+                err_sample=("one step from the projected initial state; oracle on windows "
+                            f"{WINDOWS} of the mesh, {sum(len(f) for f, _ in oracle_windows)} elements compared"),
+                e2e_value=dof * 3 / e2e_s, e2e_ms=e2e_s * 1e3, h2d=dof * 8, d2h=dof * 8,
+                roofline=roofline("stage2d_kernel", precision, tile, kernel_ms, dof, wl, peaks))
+
+
+def measure_1d(torch, frsg, wl, precision, steps, warmup, stream, flush, peaks, ref, integrator="ssp3",
+               fixed_dt=None, cfl=None, limit_first=False):
+    """Another 1D workload: throughput (dt fixed, or from the CFL condition refreshed every 20
+    steps outside the events), stage-kernel times, and the error against the oracle's state
+    `ref` = (dt, state) after the same steps from the initial state."""
+    rk4 = integrator == "rk4"
+    E, Np, M, S = workload_sizes(wl)
+    dof = E * Np * M * S
+    s = new_solver(frsg, wl, stream, precision)
+    variant, tile = s.autotune()
+    lim = bool(wl["solver"].get("limiter"))
+    # accuracy first, from the projected initial state, with the oracle's step size
+    ref_dt, ref_u, nref = ref
+    set_initial(s, wl)
+    (s.rk4_step if rk4 else s.rk_step)(ref_dt, nref, graph=True)
+    s.check()
+    got = s.get_state()
+    err, cerr = rel_l2(got, ref_u), coef_err(got, ref_u)
+    set_initial(s, wl)
+
+    def refresh(i, dt):
+        if fixed_dt is None and i % 20 == 0:
+            if lim:
+                s.limit()
+            return s.cfl_dt(cfl)
+        return dt
+
+    if fixed_dt is None:
+        if lim or limit_first:
+            s.limit()
+        dt = s.cfl_dt(cfl)
+    else:
+        dt = fixed_dt
+    step_ms, launches, dt = time_steps(torch, s, stream, flush, dt, steps, warmup, rk4=rk4, refresh=refresh)
+    with torch.cuda.stream(stream):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        (s.rk4_step if rk4 else s.rk_step)(dt, steps, graph=True)
+        ev1.record(stream)
         stream.synchronize()
+    steady_ms = ev0.elapsed_time(ev1) / steps
+    out = dict(value=dof * (4 if rk4 else 3) / (float(np.mean(step_ms)) * 1e-3), ms_per_step=float(np.mean(step_ms)),
+               us_per_step=float(np.mean(step_ms)) * 1e3, steady_us_per_step=steady_ms * 1e3, dof=dof,
+               launches_per_step=launches / steps, variant=variant, tile=tile, err_vs_oracle=err,
+               coef_err_vs_oracle=cerr, err_steps=nref, integrator=integrator, limiter=lim,
+               filter=wl["solver"].get("filter"), flux=wl["solver"].get("flux", "llf"))
+    if not rk4 and variant not in (2, 3):
+        lim_ms, ker_ms = time_kernels(torch, s, stream, flush, dt, max(3, min(steps, 20)))
+        out["limiter_us"] = [v * 1e3 for v in lim_ms]
+        out["stage_kernel_us"] = [v * 1e3 for v in ker_ms]
+        kname = "stage1d_kernel" if variant == 0 else "stage1d_wide_kernel"
+        r = roofline(kname, precision, tile, float(np.mean(ker_ms)), dof, wl, peaks)
+        out["roofline"] = {k: r[k] for k in ("kernel", "bound", "frac", "launch_us")}
+        out["roofline"]["hbm_frac"] = r["hbm"]["frac"]
+        out["roofline"]["alu_frac"] = r["alu"]["frac"]
+    else:
+        # one launch per step: the step is the kernel
+        kname = {2: "stage1d_step_kernel", 3: "step1d_fused_kernel"}.get(variant, "stage kernels")
+        r = roofline(kname, precision, tile, out["ms_per_step"] / (4 if rk4 else 3), dof, wl, peaks)
+        out["roofline"] = {"kernel": kname, "per_stage_us": r["launch_us"], "hbm_frac": r["hbm"]["frac"],
+                           "alu_frac": r["alu"]["frac"]}
     s.check()
     s.close()
-    ms = float(np.mean(step_ms))
-    if rk4:
-        stage = np.full(4, ms / 4)
-        alg = (3 + 5 + 5 + 3) * esz * dof      # arrays per stage: y, u, sum of residuals
-    else:
-        stage = np.mean(np.array([[evs[i][k].elapsed_time(evs[i][k + 1]) for k in range(3)]
-                                  for i in range(kst)]), axis=0)
-        alg = (2 + 3 + 3) * esz * dof
-    return dict(value=dof * nst / (ms * 1e-3), ms_per_step=ms, dof=dof, stage_us=[float(v * 1e3) for v in stage],
-                achieved_gbs=alg / (float(np.sum(stage)) * 1e-3) / 1e9, limiter=lim, integrator=integrator,
-                filter=wl["solver"].get("filter"), flux=wl["solver"].get("flux", "llf"))
+    return out
 
 
-def measure_batch(torch, frsg, precision, steps, warmup, stream, flush):
+def measure_batch(torch, frsg, precision, steps, warmup, stream, flush, refs):
     """The batched workload: 256 seeded Burgers problems of uneven size and order, advanced
-    together by one persistent launch per stage (graph-replayed), L2 flushed between steps."""
+    together by one persistent launch per stage (graph-replayed), L2 flushed between steps;
+    error of the first members against the oracle after the same steps."""
     wls = workloads.burgers_batch()
     solvers = []
     dof = 0
     for wl in wls:
         sv = frsg.Solver(stream=stream.cuda_stream, precision=precision, **wl["solver"])
-        x, z = sv.nodes()
-        sv.set_initial_nodal(workloads.nodal_values(wl["ic"], x, z))
+        set_initial(sv, wl)
         solvers.append(sv)
         E, Np, M, S = workload_sizes(wl)
         dof += E * Np * M * S
     dts = np.array([wl["cfl"] * (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"] / wl["lam0"]
                     for wl in wls])
     b = frsg.Batch(solvers, stream=stream.cuda_stream)
+    errs = []
+    nref = refs[0][2] if refs else 0
+    if refs:
+        b.rk_step(dts, nref)
+        torch.cuda.synchronize()
+        for i, (_, ref_u, _) in enumerate(refs):
+            solvers[i].check()
+            errs.append(rel_l2(solvers[i].get_state(), ref_u))
     with torch.cuda.stream(stream):
         b.rk_step(dts, warmup)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -358,109 +598,100 @@ def measure_batch(torch, frsg, precision, steps, warmup, stream, flush):
     for sv in solvers:
         sv.close()
     esz = 8 if precision == "fp64" else 4
-    alg = (2 + 3 + 3) * esz * dof
-    return dict(value=dof * 3 / (ms * 1e-3), ms_per_step=ms, dof=dof, members=len(wls), launches_per_step=launches / steps,
-                step_gbs=alg / (ms * 1e-3) / 1e9, **info)
+    return dict(value=dof * 3 / (ms * 1e-3), ms_per_step=ms, dof=dof, members=len(wls),
+                launches_per_step=launches / steps, stage_hbm_frac_vs_step=3 * 3 * esz * dof / (ms * 1e-3) / 1e9,
+                err_vs_oracle=max(errs) if errs else None, err_sample=f"members 0..{len(refs) - 1}, {nref} steps",
+                **{k: (int(v) if isinstance(v, (int, np.integer)) else v) for k, v in info.items()})
 
 
 def measure_adjoint(torch, frsg, stream, nsteps=64, k=16):
-    """Time of fr_sg_adjoint over the time of fr_sg_forward_record for the same run
-    (Burgers, 1024 elements, FP64, checkpoints every k steps)."""
+    """fr_sg_adjoint against the plain graph-replayed forward run of the same steps, and against
+    fr_sg_forward_record (Burgers, 1024 elements, FP64, checkpoints every k steps)."""
     wl = workloads.burgers_1d()
     sv = frsg.Solver(stream=stream.cuda_stream, **wl["solver"])
-    x, z = sv.nodes()
-    sv.set_initial_nodal(workloads.nodal_values(wl["ic"], x, z))
+    set_initial(sv, wl)
     u0 = torch.empty(sv.state_shape, dtype=torch.float64, device="cuda")
     sv.get_state(u0)
     dt = wl["cfl"] * (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"] / wl["lam0"]
     lam = torch.zeros_like(u0)
     g = torch.empty_like(u0)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    fw, bw = [], []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    plain, fw, bw = [], [], []
     with torch.cuda.stream(stream):
         for rep in range(4):
             sv.set_state(u0)
-            sv.forward_record(dt, nsteps, k)
+            sv.rk_step(dt, nsteps, graph=True)
+            sv.set_state(u0)
             lam.zero_()
             lam[:, :, 0, 0] = 1.0
             stream.synchronize()
             ev[0].record(stream)
-            sv.forward_record(dt, nsteps, k)
+            sv.rk_step(dt, nsteps, graph=True)
             ev[1].record(stream)
-            sv.adjoint(lam, g)
+            sv.set_state(u0)
             ev[2].record(stream)
+            sv.forward_record(dt, nsteps, k)
+            ev[3].record(stream)
+            sv.adjoint(lam, g)
+            ev[4].record(stream)
             stream.synchronize()
             if rep > 0:
-                fw.append(ev[0].elapsed_time(ev[1]))
-                bw.append(ev[1].elapsed_time(ev[2]))
+                plain.append(ev[0].elapsed_time(ev[1]))
+                fw.append(ev[2].elapsed_time(ev[3]))
+                bw.append(ev[3].elapsed_time(ev[4]))
     sv.check()
     sv.close()
-    f, a = float(np.median(fw)), float(np.median(bw))
-    return dict(workload=wl["name"], steps=nsteps, checkpoint_every=k, forward_ms=f, adjoint_ms=a, ratio=a / f)
+    p, f, a = float(np.median(plain)), float(np.median(fw)), float(np.median(bw))
+    return dict(workload=wl["name"], steps=nsteps, checkpoint_every=k, forward_ms=p, recording_forward_ms=f,
+                adjoint_ms=a, ratio=a / p, ratio_vs_recording_forward=a / f)
 
 
-def cpu_baseline(wl, seconds):
-    import oracle
-    from oracle import integrate, tables
-    kw = dict(wl["solver"])
-    prob = oracle.Problem(**kw)
-    tabs = prob.tabs()
-    u = integrate.project_initial(prob, wl["ic"])
-    dt = wl["cfl"] * prob.dx / wl["lam0"]
-    E, Np, M, S = workload_sizes(wl)
-    dof = E * Np * M * S
-    n = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds or n < 2:
-        u = integrate.ssp_rk3_step(prob, tabs, u, dt)
-        n += 1
-    t = time.perf_counter() - t0
-    del tables
-    return dict(value=dof * 3 * n / t, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{n} SSP-RK3 steps of the full {wl['name']} workload from t=0 "
-                       f"(numpy FP64 oracle, single thread), {t:.1f} s")
-
-
-def oracle_reference(wl, nsteps):
-    import oracle
-    from oracle import integrate
-    prob = oracle.Problem(**wl["solver"])
-    u = integrate.project_initial(prob, wl["ic"])
-    dt = wl["cfl"] * prob.dx / wl["lam0"]
-    return integrate.run(prob, u, dt, nsteps)
-
-
-def run_only(args):
-    """One extra measurement alone, both forms where they apply (profiling aid)."""
-    import torch
-    from paper_2112_05946_gb300 import build as _b
-    from paper_2112_05946_gb300 import frsg
-    _b.build()
-    frsg.load_library()
-    tune_file = load_tune_cache(frsg)
-    stream = torch.cuda.Stream()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    if args.only == "burgers":
-        wl = workloads.burgers_1d()
-        ref = oracle_reference(wl, ACC_STEPS)
-        out = measure_form(torch, frsg, wl, "fp32", args.steps, args.warmup, stream, flush, ref)
-    elif args.only == "batch":
-        out = {p: measure_batch(torch, frsg, p, args.steps, args.warmup, stream, flush) for p in ("fp64", "fp32")}
-    elif args.only == "adjoint":
-        out = measure_adjoint(torch, frsg, stream)
+def measure_peaks():
+    """Roofline denominators: the measured HBM copy bandwidth (MEASURED_PEAKS.json, else
+    the fallback figure) and this repository's FMA microbenchmark (libfrsg_peak.so)."""
+    from paper_2112_05946_gb300 import peak
+    out = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as f:
+            d = json.load(f)
+        out["hbm_gbs"], out["hbm_source"] = d["hbm_gbs"], "measured (MEASURED_PEAKS.json: copy bandwidth)"
     else:
-        wl = workloads.ALL[args.only]()
-        out = {p: measure_extra(torch, frsg, wl, p, args.steps, args.warmup, stream, flush) for p in ("fp64", "fp32")}
-    print(json.dumps({"only": args.only, "result": out}))
-    if tune_file:
-        frsg.tune_cache_save(tune_file)
+        out["hbm_gbs"], out["hbm_source"] = 6800.0, "fallback (6.8 TB/s)"
+    out["fp64_tflops"] = peak.fma_tflops(True)
+    out["fp32_tflops"] = peak.fma_tflops(False)
+    out["fma_source"] = "measured (libfrsg_peak.so: frsg_peak_fma, dense FMA chains, best of 5)"
+    return out
+
+
+OTHER_1D = {
+    # name: (spec, precision-independent oracle steps, dt rule)
+    "advection_E32_P2_N4_Q8": (("advection_1d", {}, {}), 320, "fixed"),
+    "burgers_E1024_P3_N8_Q16": (("burgers_1d", {}, {}), 50, "fixed"),
+    "sod_E4096_P3_N6_Q12": (("sod_1d", {}, {}), 2, "cfl"),
+    "burgers_E1024_P3_N8_Q16_lasso": (("burgers_1d", {}, {"filter": "lasso", "sensor": False}), 20, "fixed"),
+    "burgers_E1024_P3_N8_Q16_rk4": (("burgers_1d", {}, {}), 20, "fixed"),
+    "sod_location_E4096_P2_N9_Q17_lasso": (("sod_location_1d", {"nx": 4096}, {}), 2, "cfl"),
+}
 
 
 def run_ours(args):
     import torch
-    if args.only:
-        return run_only(args)
     rank, world, local = dist_env()
+    pool = None
+    futs = {}
+    batch_n = 4
+    if rank == 0:
+        # oracle references in spawned workers, started before the first GPU call
+        pool = _pool(min(os.cpu_count() or 1, 12))
+        futs["headline"] = pool.submit(job_windows, ("shock_vortex_2d", {}, {}), CFL_2D, 1)
+        if not args.no_extra:
+            for name, (spec, n, rule) in OTHER_1D.items():
+                integ = "rk4" if name.endswith("_rk4") else "ssp3"
+                cfl = None if rule == "fixed" else 0.05
+                futs[name] = pool.submit(job_run_1d, spec, cfl, n, integ, name.startswith("sod_location"))
+            for i in range(batch_n):
+                futs[f"batch{i}"] = pool.submit(job_run_1d, ("burgers_batch_member", {"i": i}, {}), None, 10)
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -473,8 +704,7 @@ def run_ours(args):
         torch.distributed.barrier()
     frsg.load_library()
     tune_file = load_tune_cache(frsg)
-    wl = workloads.ALL[args.workload]()
-    ref = oracle_reference(wl, ACC_STEPS)
+    peaks = measure_peaks()
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sampler = ClockSampler(local)
@@ -482,33 +712,31 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    forms = {}
-    for prec in ("fp64", "fp32"):
-        forms[prec] = measure_form(torch, frsg, wl, prec, args.steps, args.warmup, stream, flush, ref)
-    extra = {}
-    batch = {}
-    adj = None
-    if not args.no_extra:
-        bsteps = max(3, min(args.steps, 50))
-        batch = {prec: measure_batch(torch, frsg, prec, bsteps, 3, stream, flush) for prec in ("fp64", "fp32")}
+    if rank == 0:
+        oracle_dt, oracle_win = futs["headline"].result()
+    else:
+        oracle_dt, oracle_win = job_windows(("shock_vortex_2d", {}, {}), CFL_2D, 1)
+    forms = {p: measure_headline(torch, frsg, p, args, stream, flush, peaks, oracle_dt, oracle_win)
+             for p in ("fp64", "fp32")}
+    extra, batch, adj = {}, {}, None
+    if not args.no_extra and rank == 0:
+        xsteps = max(3, min(args.steps, 50))
+        for name, (spec, n, rule) in OTHER_1D.items():
+            wl = _spec_workload(spec)
+            dt_ref, u_ref = futs[name].result()
+            integ = "rk4" if name.endswith("_rk4") else "ssp3"
+            fixed = dt_ref if rule == "fixed" else None
+            extra[name] = {p: measure_1d(torch, frsg, wl, p, xsteps, 3, stream, flush, peaks, (dt_ref, u_ref, n),
+                                         integrator=integ, fixed_dt=fixed, cfl=0.05,
+                                         limit_first=name.startswith("sod_location"))
+                           for p in ("fp64", "fp32")}
+            if name.startswith("sod") or name.endswith("_lasso"):
+                for p in ("fp32",):
+                    extra[name][p]["err_bound"] = ERR_BOUND_SHOCK_FP32
+        brefs = [futs[f"batch{i}"].result() + (10,) for i in range(batch_n)]
+        batch = {p: measure_batch(torch, frsg, p, max(3, min(args.steps, 20)), 3, stream, flush, brefs)
+                 for p in ("fp64", "fp32")}
         adj = measure_adjoint(torch, frsg, stream)
-        xsteps = max(3, min(args.steps, 100))
-        for name in ("sod", "shock_vortex"):
-            ewl = workloads.ALL[name]()
-            extra[ewl["name"]] = {prec: measure_extra(torch, frsg, ewl, prec, xsteps, 3, stream, flush)
-                                  for prec in ("fp64", "fp32")}
-        # the headline workload with the Lasso filter (every element), and with classical RK4
-        lwl = workloads.burgers_1d()
-        lwl["solver"].update(filter="lasso", sensor=False)
-        extra[lwl["name"] + "_lasso"] = {prec: measure_extra(torch, frsg, lwl, prec, xsteps, 3, stream, flush)
-                                         for prec in ("fp64", "fp32")}
-        rwl = workloads.burgers_1d()
-        extra[rwl["name"] + "_rk4"] = {prec: measure_extra(torch, frsg, rwl, prec, xsteps, 3, stream, flush, "rk4")
-                                       for prec in ("fp64", "fp32")}
-        # the paper's second Sod case (stochastic shock location, HLL, Lasso) at 4096 elements
-        hwl = workloads.sod_location_1d(nx=4096)
-        extra[hwl["name"]] = {prec: measure_extra(torch, frsg, hwl, prec, xsteps, 3, stream, flush)
-                              for prec in ("fp64", "fp32")}
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -519,63 +747,43 @@ def run_ours(args):
     ms = max_over_ranks(torch, chosen["ms_per_step"], world, "cuda")
     value = whole_job_value(world, chosen["dof"], 3, ms)
 
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        with open(pk) as f:
-            peaks = json.load(f)
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    kname = {0: "stage1d_kernel", 1: "stage1d_wide_kernel", 2: "stage1d_step_kernel",
-             3: "step1d_fused_kernel"}[chosen["variant"]]
-    # DRAM bytes of one launch from the ncu capture of this kernel build; null for a layout
-    # without a capture of the current build
-    traffic = MEASURED_TRAFFIC.get((kname, chosen["precision"], chosen["tile"]))
-    roofline = {"bound": "hbm", "achieved": round(chosen["achieved_gbs"], 2), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(chosen["achieved_gbs"] / hbm_peak, 5), "traffic": traffic,
-                "kernel": kname, "peak_source": "measured" if peaks else "fallback",
-                "alg_bytes_per_step": chosen["alg_bytes_per_step"]}
-    if chosen["variant"] in (2, 3):
-        # one launch per step: the timed launch is the step (fr_sg_stage runs single stages in
-        # another layout, so its times do not describe this kernel)
-        roofline["launch_us"] = round(chosen["ms_per_step"] * 1e3, 3)
-    else:
-        roofline["stage_us"] = chosen["stage_us"]
-
     cpu = None
+    if pool is not None:
+        pool.shutdown(wait=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, args.cpu_seconds)
+        cpu = cpu_baseline(args.cpu_seconds)
 
+    wl = workloads.shock_vortex_2d()
     E, Np, M, S = workload_sizes(wl)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if chosen["precision"] == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "elements": E, "P": wl["solver"]["P"], "N": wl["solver"]["N"],
-                   "Q": wl["solver"]["Q"], "S": S, "dof": E * Np * M * S, "filter": "exp+detector",
-                   "l2": "256 MiB memset between timed steps (state 0.3 MB < L2)",
+                   "Q": wl["solver"]["Q"], "S": S, "dof": E * Np * M * S, "filter": "l2+detector",
+                   "limiter": True, "l2": "256 MiB memset between timed steps",
                    "parallelism": f"replicas x{world}"},
         "chosen": chosen["precision"],
+        "err_vs_oracle": chosen["err_vs_oracle"],
         "forms": {k: {"value": v["value"], "ms_per_step": v["ms_per_step"], "rel_l2_vs_oracle": v["err_vs_oracle"],
-                      "err_bound": v["err_bound"], "steady_ms_per_step": v["steady_ms"],
-                      "stage_us": v["stage_us"], "variant": v["variant"], "tile": v["tile"]}
+                      "coef_err_vs_oracle": v["coef_err_vs_oracle"], "err_bound": v["err_bound"],
+                      "err_sample": v["err_sample"], "steady_ms_per_step": v["steady_ms_per_step"],
+                      "limiter_us": v["limiter_us"], "stage_kernel_us": v["stage_kernel_us"],
+                      "tile": v["tile"], "e2e_value": v["e2e_value"],
+                      "roofline": {kk: v["roofline"][kk] for kk in ("kernel", "bound", "frac", "launch_us")}
+                      | {"hbm_frac": v["roofline"]["hbm"]["frac"], "alu_frac": v["roofline"]["alu"]["frac"]}}
                   for k, v in forms.items()},
-        "roofline": roofline,
+        "roofline": chosen["roofline"],
+        "peaks": peaks,
         "cpu_baseline": cpu,
         "e2e": {"value": chosen["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": chosen["h2d"],
-                "d2h_bytes_per_step": chosen["d2h"], "ms_per_step": chosen["e2e_ms"]},
+                "d2h_bytes_per_step": chosen["d2h"], "ms_per_step": chosen["e2e_ms"],
+                "path": "fr_sg_advance, pinned host FP64 state in, one step, state out, one sync"},
         "gpu_launches": chosen["launches"],
         "clocks": clocks,
-        "batched": {"workload": "burgers_batch0: 256 problems, E 64-2048, P 1-4, N 2-10, Q 2N",
-                    **{p: {k2: (float(v2) if isinstance(v2, (int, float)) else v2) for k2, v2 in f.items()}
-                       for p, f in batch.items()}},
+        "batched": {"workload": "burgers_batch0: 256 problems, E 64-2048, P 1-4, N 2-10, Q 2N", **batch},
         "adjoint": adj,
-        "other_workloads": {
-            k: {p: {"value": f["value"], "ms_per_step": f["ms_per_step"], "dof": f["dof"], "stage_us": f["stage_us"],
-                    "stage_gbs": f["achieved_gbs"], "stage_hbm_frac": f["achieved_gbs"] / hbm_peak,
-                    "limiter": f["limiter"], "integrator": f["integrator"], "filter": f["filter"],
-                    "flux": f["flux"]}
-                for p, f in v.items()}
-            for k, v in extra.items()},
+        "other_workloads": extra,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -585,35 +793,68 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_only(args):
+    """One workload alone, both forms (profiling aid): no oracle, no extra lines."""
+    import torch
+    from paper_2112_05946_gb300 import build as _b
+    from paper_2112_05946_gb300 import frsg
+    _b.build()
+    frsg.load_library()
+    tune_file = load_tune_cache(frsg)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if args.only == "peak":
+        from paper_2112_05946_gb300 import peak
+        out = {"fp64_tflops": peak.fma_tflops(True), "fp32_tflops": peak.fma_tflops(False)}
+    elif args.only == "batch":
+        out = {p: measure_batch(torch, frsg, p, args.steps, args.warmup, stream, flush, []) for p in ("fp64", "fp32")}
+    elif args.only == "adjoint":
+        out = measure_adjoint(torch, frsg, stream)
+    else:
+        wl = workloads.ALL[args.only]()
+        out = {}
+        for p in ("fp64", "fp32"):
+            s = new_solver(frsg, wl, stream, p)
+            variant, tile = s.autotune()
+            set_initial(s, wl)
+            if wl["solver"].get("limiter"):
+                s.limit()
+            dt = s.cfl_dt(CFL_2D if wl["solver"].get("dim", 1) == 2 else 0.05) if wl["lam0"] is None else (
+                wl["cfl"] * (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"] / wl["lam0"])
+            ms, launches, _ = time_steps(torch, s, stream, flush, dt, args.steps, args.warmup)
+            s.check()
+            s.close()
+            out[p] = {"ms_per_step": float(np.mean(ms)), "variant": variant, "tile": tile,
+                      "launches_per_step": launches / args.steps}
+    print(json.dumps({"only": args.only, "result": out}))
+    if tune_file:
+        frsg.tune_cache_save(tune_file)
+
+
 def run_reference(args):
+    """The FP64 oracle, as it stands, on the host cores: each step one SSP-RK3 step of a
+    32 x 16-element patch of the headline problem (the whole mesh takes the oracle minutes per
+    step); rank 0 only."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    from oracle import integrate
-    wl = workloads.ALL[args.workload]()
-    prob = oracle.Problem(**wl["solver"])
-    tabs = prob.tabs()
-    u = integrate.project_initial(prob, wl["ic"])
-    dt = wl["cfl"] * prob.dx / wl["lam0"]
+    job_patch_steps(args.warmup)
+    n, t, dof = job_patch_steps(args.steps)
+    value = dof * 3 * n / t
+    wl = workloads.shock_vortex_2d()
     E, Np, M, S = workload_sizes(wl)
-    dof = E * Np * M * S
-    for _ in range(args.warmup):
-        u = integrate.ssp_rk3_step(prob, tabs, u, dt)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        u = integrate.ssp_rk3_step(prob, tabs, u, dt)
-    t = time.perf_counter() - t0
-    value = dof * 3 * args.steps / t
+    sample = (f"numpy FP64 oracle, single thread: {n} SSP-RK3 steps of a 32x16-element patch of the shock_vortex "
+              f"problem ({dof} DOF, same P, N, Q, variables, limiter and filter) after {args.warmup} warm-up steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / n * (E * Np * M * S / dof),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "elements": E, "P": wl["solver"]["P"], "N": wl["solver"]["N"],
-                   "Q": wl["solver"]["Q"], "S": S, "dof": dof},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} timed SSP-RK3 steps of the full {wl['name']} workload "
-                                   f"after {args.warmup} warm-up steps (numpy FP64 oracle, single thread)"},
+                   "Q": wl["solver"]["Q"], "S": S, "dof": E * Np * M * S, "filter": "l2+detector",
+                   "limiter": True, "l2": "256 MiB memset between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -623,6 +864,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args)
 

@@ -190,6 +190,14 @@ frsg_status fr_sg_rk4_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph);
  * fr_sg_rk_step(ctx, dt, 1, 0); separate calls let a caller time or interleave stages. */
 frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt);
 
+/* Events (cudaEvent_t, created by the caller) that fr_sg_stage records on the context's
+ * stream: before_limiter before the limiter launch (§4.3), before_stage between it and the
+ * stage kernel, after_stage after the stage kernel, so that a caller can time each kernel of
+ * a stage with the same launches as fr_sg_rk_step (replayed decisions are not consumed while
+ * events are set).  Any may be NULL; all NULL (the default) records nothing.  The events are
+ * borrowed until they are replaced. */
+frsg_status fr_sg_set_timing_events(frsg_ctx* ctx, void* before_limiter, void* before_stage, void* after_stage);
+
 /* Detector + filter (§4.1-4.2) on the current state with step size dt. */
 frsg_status fr_sg_filter(frsg_ctx* ctx, double dt);
 

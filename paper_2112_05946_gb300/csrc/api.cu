@@ -66,6 +66,8 @@ struct frsg_ctx {
     double* d_seg = nullptr;      // [3 * k][state]: stage inputs of one segment
     double* d_work = nullptr;     // [4][state]: final state, lambda, stage cotangents
     int graph_kernels = 0;
+    // caller's events recorded around the kernels of fr_sg_stage (fr_sg_set_timing_events)
+    cudaEvent_t ev_lim = nullptr, ev_stage = nullptr, ev_end = nullptr;
 };
 
 namespace {
@@ -986,7 +988,27 @@ frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt) {
     if (stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt))
         return fail(ctx, FRSG_E_INVAL, "need stage in 0..2 and dt > 0");
     CK(set_dt(ctx, dt));
-    CK(issue_stage(ctx, stage, dt, true));
+    if (!ctx->ev_lim && !ctx->ev_stage && !ctx->ev_end) {
+        CK(issue_stage(ctx, stage, dt, true));
+        return FRSG_OK;
+    }
+    // the same launches as issue_stage, with the caller's events between them
+    if (ctx->ev_lim) CK(cudaEventRecord(ctx->ev_lim, ctx->stream));
+    if (ctx->cfg.limiter) {
+        void* bufs_in[3] = {ctx->d_u, ctx->d_u1, ctx->d_u2};
+        CK(launch_limiter(ctx, bufs_in[stage], ctx->d_beta + (size_t)stage * ctx->E));
+    }
+    if (ctx->ev_stage) CK(cudaEventRecord(ctx->ev_stage, ctx->stream));
+    CK(issue_stage_ex(ctx, stage, dt, ctx->d_flags + (size_t)stage * ctx->E, nullptr, false));
+    if (ctx->ev_end) CK(cudaEventRecord(ctx->ev_end, ctx->stream));
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_set_timing_events(frsg_ctx* ctx, void* before_limiter, void* before_stage, void* after_stage) {
+    if (!ctx) return FRSG_E_INVAL;
+    ctx->ev_lim = static_cast<cudaEvent_t>(before_limiter);
+    ctx->ev_stage = static_cast<cudaEvent_t>(before_stage);
+    ctx->ev_end = static_cast<cudaEvent_t>(after_stage);
     return FRSG_OK;
 }
 

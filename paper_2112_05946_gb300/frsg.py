@@ -89,6 +89,7 @@ _SIGNATURES = [
     ("fr_sg_set_tile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("fr_sg_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_test_fused_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
+    ("fr_sg_set_timing_events", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("fr_sg_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     ("fr_sg_forward_record", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
@@ -335,6 +336,14 @@ class Solver:
     def rk4_step(self, dt, nsteps=1, graph=True):
         """Classical RK4 steps (the advection study's integrator)."""
         self._ck(self.lib.fr_sg_rk4_step(self.h, float(dt), int(nsteps), int(bool(graph))), "rk4_step")
+
+    def set_timing_events(self, before_limiter=None, before_stage=None, after_stage=None):
+        """fr_sg_set_timing_events: torch.cuda.Event objects (or None) that stage() records
+        around its limiter and stage-kernel launches."""
+        def h(ev):
+            return ctypes.c_void_p(ev.cuda_event if ev is not None else 0)
+        self._ck(self.lib.fr_sg_set_timing_events(self.h, h(before_limiter), h(before_stage), h(after_stage)),
+                 "set_timing_events")
 
     def stage(self, stage, dt):
         self._ck(self.lib.fr_sg_stage(self.h, int(stage), float(dt)), "stage")

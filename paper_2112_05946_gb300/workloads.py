@@ -216,6 +216,11 @@ def burgers_batch(n=256, seed=0, e_range=(64, 2048), cfl=0.05):
     return out
 
 
+def burgers_batch_member(i, seed=0):
+    """Instance i of burgers_batch(seed=seed) alone (each instance has its own seeded stream)."""
+    return burgers_batch(n=i + 1, seed=seed)[i]
+
+
 ALL = {"advection": advection_1d, "burgers": burgers_1d, "sod": sod_1d, "shock_vortex": shock_vortex_2d}
 
 

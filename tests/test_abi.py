@@ -79,3 +79,16 @@ def test_tune_cache_file_roundtrip(tmp_path):
         frsg.tune_cache_load(str(bad))
     with pytest.raises(frsg.FrsgError):
         frsg.tune_cache_load(str(tmp_path / "missing.txt"))
+
+
+def test_peak_library_exports_its_header():
+    """libfrsg_peak.so (the FMA microbenchmark) exports what include/frsg_peak.h declares."""
+    from paper_2112_05946_gb300 import build
+    build.build()
+    txt = open(os.path.join(ROOT, "include", "frsg_peak.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = sorted(set(re.findall(r"\b(frsg_[a-z0-9_]+)\s*\(", txt)))
+    assert names == ["frsg_peak_fma"]
+    lib = ctypes.CDLL(build.PEAK_OUT)
+    for n in names:
+        assert hasattr(lib, n), n

@@ -1,0 +1,130 @@
+"""The 2D shock-vortex workload at its full size (256 x 128 quads, P = 3, N = 4, Q = 8, four
+variables: 10,485,760 DOF) against the oracle, at the tile the autotuner picks and through the
+graph-replayed step the benchmark times.
+
+The oracle cannot step the whole mesh in a test's time, so it runs on windows of it
+(oracle/windows.py): after one step, an element's state depends only on elements within three
+face-to-face moves, so a window reproduces the full-mesh result on its elements three or more
+rows from every side that cuts through the mesh.  The windows cover the inflow boundary and
+the vortex, the shock face meeting the bottom wall, and the outflow corner at the top wall.
+Inputs: the projected initial state, and that state with seeded high-mode noise and planted
+negative densities, so that the detector, the filter and the limiter act.  FP64 is held to
+1e-12 (relative L2 per window, and per coefficient against each variable's largest value)
+with the filter decisions equal; the FP32 form to its stated bounds.  A 20-step FP32 run on
+a 48 x 24 mesh of the same problem is compared with the whole-mesh oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import integrate, windows
+from paper_2112_05946_gb300 import workloads
+from tests.helpers import gpu_initial, oracle_initial, oracle_problem, rel_l2, solver
+
+pytestmark = pytest.mark.gpu
+
+WINDOWS = [(0, 48, 40, 88), (56, 72, 0, 24), (232, 256, 104, 128)]
+# relative L2 per window after one step, and per coefficient relative to the variable's largest
+# |value|.  The FP32 limiter aims 1e-5 of the element mean above eps (so that the rounded state
+# stays admissible), where the FP64 oracle aims at eps itself: limited elements of the FP32 form
+# differ from the oracle by about 1e-5 of their deviation from the mean.
+TOL = {("fp64", "ic"): 1e-12, ("fp64", "perturbed"): 1e-12, ("fp32", "ic"): 1e-6, ("fp32", "perturbed"): 1e-5}
+COEF = {("fp64", "ic"): 1e-12, ("fp64", "perturbed"): 1e-12, ("fp32", "ic"): 2e-6, ("fp32", "perturbed"): 5e-5}
+TOL_FP32_20 = 2e-5                           # FP32, 20 steps, 48 x 24 mesh, relative L2
+
+
+def _perturb(prob, u, seed=7):
+    """Seeded noise in the higher modes of a band of elements (the detector flags some) and a
+    negative density at one corner point of some elements, with the density moved to the
+    opposite corner (same quadrature weight) so that the element mean is unchanged."""
+    rng = np.random.default_rng(seed)
+    v = u.copy()
+    U = v.reshape(prob.ny, prob.nx, prob.Np, prob.M, prob.S)
+    U[30:100, :, :, 1:, :] += 0.01 * rng.standard_normal(U[30:100, :, :, 1:, :].shape)
+    U[30:100, :, 5:, 0, :] *= 1.0 + 0.05 * rng.standard_normal(U[30:100, :, 5:, 0, :].shape)
+    picks = [(ey, ex) for ey in range(44, 84, 7) for ex in range(2, 44, 9)]
+    picks += [(ey, ex) for ey in range(1, 20, 6) for ex in range(60, 68, 3)]
+    picks += [(ey, ex) for ey in range(108, 128, 6) for ex in range(236, 256, 6)]
+    last = prob.Np - 1
+    for ey, ex in picks:
+        rho0 = U[ey, ex, 0, 0, 0]
+        U[ey, ex, 0, 0, 0] = -0.05
+        U[ey, ex, last, 0, 0] += rho0 + 0.05
+    return v, picks
+
+
+@pytest.fixture(scope="module")
+def full_case():
+    wl = workloads.shock_vortex_2d()
+    prob = oracle_problem(wl)
+    tabs = prob.tabs()
+    u0 = oracle_initial(prob, wl)
+    dt = integrate.cfl_dt(prob, tabs, u0, 0.05)
+    up, picks = _perturb(prob, u0)
+    refs = {}
+    for name, u in (("ic", u0), ("perturbed", up)):
+        out = []
+        for box in WINDOWS:
+            rec = []
+            full, got = windows.run_window(prob, u, box, dt, 1, record=rec)
+            out.append((full, got, np.stack(rec)))
+        refs[name] = out
+    return dict(wl=wl, prob=prob, u0=u0, up=up, dt=dt, refs=refs, picks=picks)
+
+
+def _run_gpu(case, precision, start):
+    s = solver(case["wl"], precision=precision)
+    variant, tile = s.autotune()
+    if start == "ic":
+        gpu_initial(s, case["wl"])
+    else:
+        s.set_state(case["up"])
+    s.rk_step(case["dt"], 1, graph=True)
+    s.check()
+    flags, beta = s.decisions()
+    got = s.get_state()
+    s.close()
+    return got, flags, beta, tile
+
+
+def _compare(case, precision, start, got, flags):
+    for (full, ref, rec), box in zip(case["refs"][start], WINDOWS):
+        g = got[full]
+        assert rel_l2(g, ref) < TOL[precision, start], (box, rel_l2(g, ref))
+        scale = np.max(np.abs(ref), axis=(0, 1, 2))           # per variable
+        worst = np.max(np.abs(g - ref) / scale)
+        assert worst < COEF[precision, start], (box, worst)
+        if precision == "fp64":
+            np.testing.assert_array_equal(flags[:, full], rec, err_msg=str(box))
+        else:
+            assert np.mean(flags[:, full] != rec) < 0.01, box
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("start", ["ic", "perturbed"])
+def test_full_size_step_matches_oracle_windows(full_case, precision, start):
+    got, flags, beta, tile = _run_gpu(full_case, precision, start)
+    assert tile >= 1
+    _compare(full_case, precision, start, got, flags)
+    if start == "perturbed":
+        # the limiter scaled every planted defect in the first stage, and the detector flagged
+        # elements inside the windows
+        for ey, ex in full_case["picks"]:
+            assert beta[0, ey * 256 + ex] < 1.0
+        assert any(rec.any() for _, _, rec in full_case["refs"]["perturbed"])
+
+
+def test_fp32_twenty_steps_against_whole_mesh_oracle():
+    wl = workloads.shock_vortex_2d(nx=48, ny=24)
+    prob = oracle_problem(wl)
+    tabs = prob.tabs()
+    u0 = oracle_initial(prob, wl)
+    dt = integrate.cfl_dt(prob, tabs, u0, 0.05)
+    ref = integrate.run(prob, u0, dt, 20)
+    s = solver(wl, precision="fp32")
+    s.autotune()
+    gpu_initial(s, wl)
+    s.rk_step(dt, 20, graph=True)
+    s.check()
+    got = s.get_state()
+    err = rel_l2(got, ref)
+    assert err < TOL_FP32_20, err
