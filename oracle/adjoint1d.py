@@ -122,8 +122,10 @@ def _pressure_root(prob, ubar, us, eps):
     c = g1 * (ubar[..., 2] * ubar[..., 0] - 0.5 * ubar[..., 1] ** 2) - eps * ubar[..., 0]
     disc = torch.clamp(b * b - 4.0 * a * c, min=0.0)
     sq = torch.sqrt(disc)
-    r1 = (-b - sq) / (2.0 * a)
-    r2 = (-b + sq) / (2.0 * a)
+    # the roots as q/a and c/q, q = -(b + sign(b) sqrt(disc))/2: no cancellation when a is small
+    q = -0.5 * (b + torch.copysign(sq, b))
+    r1 = q / a
+    r2 = torch.where(q != 0.0, c / q, r1)
     lin = -c / b
     in1 = (r1 >= 0.0) & (r1 <= 1.0)
     in2 = (r2 >= 0.0) & (r2 <= 1.0)

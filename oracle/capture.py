@@ -222,7 +222,10 @@ def pressure_root(prob, ubar, ustar, eps):
 
     rho(beta) p(beta)/(gamma-1) = rho E - |m|^2/2 is quadratic in beta along the segment;
     the equation becomes a beta^2 + b beta + c = 0 with c = rho_bar (p_bar - eps) >= 0
-    and a negative value at beta = 1, so exactly one root lies in [0, 1).
+    and a negative value at beta = 1, so exactly one root lies in [0, 1).  The two roots are
+    q/a and c/q with q = -(b + sign(b) sqrt(b^2 - 4ac))/2, which never subtracts two nearly
+    equal numbers: when only the density differs along the segment, a is a rounding-sized
+    number and the textbook (-b +- sqrt(b^2 - 4ac))/(2a) loses the root.
     """
     g1 = prob.gamma - 1.0
     d = ustar - ubar
@@ -240,7 +243,8 @@ def pressure_root(prob, ubar, ustar, eps):
     disc = b * b - 4.0 * a * c
     disc = max(disc, 0.0)
     sq = np.sqrt(disc)
-    roots = [(-b - sq) / (2.0 * a), (-b + sq) / (2.0 * a)]
+    q = -0.5 * (b + np.copysign(sq, b))
+    roots = [q / a, c / q if q != 0.0 else q / a]
     cand = [r for r in roots if 0.0 <= r <= 1.0]
     if not cand:
         # numerically at the interval end

@@ -203,3 +203,31 @@ def test_moments_match_quadrature_of_expansion():
     v_ref = np.einsum("q,ejqs->ejs", w, (vals - m_ref[:, :, None, :]) ** 2)
     np.testing.assert_allclose(mean, m_ref, atol=1e-13)
     np.testing.assert_allclose(var, v_ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_pressure_root_nearly_linear_case_matches_bisection(dim):
+    """The segment from the mean to a point whose density alone differs (momentum and energy
+    equal to the mean's up to rounding) makes the quadratic of Eq. 51 nearly linear: its
+    leading coefficient is a rounding-sized number.  The root in [0, 1] must still be the
+    exact one (bisection of p(beta) = eps), not the cancellation of two nearly equal terms."""
+    S = 3 if dim == 1 else 4
+    prob = oracle.Problem(dim=dim, nx=2, ny=1, P=2, N=2, Q=4, equation="euler", limiter=True)
+    rng = np.random.default_rng(17)
+    for _ in range(40):
+        rho_b = 1.0 + rng.random()
+        m = rng.standard_normal(S - 2) * 1.5
+        E = 0.5 * np.dot(m, m) / rho_b + (0.5 + rng.random()) / (prob.gamma - 1.0)
+        ubar = np.concatenate([[rho_b], m, [E]])
+        ustar = ubar.copy()
+        ustar[0] = 1e-8 + 1e-3 * rng.random()                 # the limited density at the point
+        ustar[-1] *= 1.0 + 1e-16 * rng.standard_normal()      # rounding left in the energy
+        eps = 1e-8
+        if not scheme.pressure(ustar, prob.gamma, dim) < eps:
+            continue
+
+        def g(b):
+            return scheme.pressure(ubar + b * (ustar - ubar), prob.gamma, dim) - eps
+
+        ref = brentq(g, 0.0, 1.0, xtol=1e-16, rtol=1e-15)
+        np.testing.assert_allclose(capture.pressure_root(prob, ubar, ustar, eps), ref, rtol=1e-12)
