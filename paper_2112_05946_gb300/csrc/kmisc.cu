@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "bulk.cuh"
+#include "epilogue.cuh"
 #include "limiter.cuh"
 #include "pdl.cuh"
 #include "physics.cuh"
@@ -14,231 +16,416 @@ namespace {
 template <typename T>
 __device__ inline double ld(const T* p, size_t i) { return (double)p[i]; }
 
-// Visit the state at each of the limiter's points, given the solution-point values v[s][j]:
-// the solution points themselves, then the flux points on the faces, each interpolated along
-// its line of points (1D: r = -1, +1; 2D: r = -1 and r = +1 for every s_b, s = -1 and s = +1
-// for every r_a) with n1 multiply-adds per face point and variable.
-template <typename T, int N1, int DIM, int S, typename F>
-__device__ inline void for_each_limiter_point(const T (&v)[S][DIM == 1 ? N1 : N1 * N1], const T* lm, const T* lp,
-                                              F&& visit) {
-    constexpr int NPT = DIM == 1 ? N1 : N1 * N1;
+// The element's Euler state is admissible at a point when rho > 0 and p > 0 there (§4.3).
+// In float the screen divides with the fast reciprocal: its margins (1e-4 of the mean) are far
+// above that rounding, and a non-finite value makes the element a candidate for the exact pass.
+template <typename T, int S>
+__device__ __forceinline__ T pressure_t(const T (&w)[S], T g1) {
+    T m2 = T(0);
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-        T val[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) val[s] = v[s][j];
-        visit(val);
-    }
-    constexpr int NLINE = DIM == 1 ? 1 : N1;
-#pragma unroll
-    for (int face = 0; face < 2 * DIM; ++face) {
-        const T* w = (face & 1) ? lp : lm;
-#pragma unroll
-        for (int i = 0; i < NLINE; ++i) {
-            T val[S];
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                T acc = T(0);
-#pragma unroll
-                for (int l = 0; l < N1; ++l) {
-                    const int j = DIM == 1 ? l : (face < 2 ? i * N1 + l : l * N1 + i);
-                    acc += w[l] * v[s][j];
-                }
-                val[s] = acc;
-            }
-            visit(val);
-        }
-    }
+    for (int d = 1; d < S - 1; ++d) m2 += w[d] * w[d];
+    if constexpr (sizeof(T) == 4) return g1 * (w[S - 1] - __fdividef(0.5f * m2, w[0]));
+    else return g1 * (w[S - 1] - T(0.5) * m2 / w[0]);
 }
 
-// Block (Q, TE): thread (q, te) owns z-node q of element te.  Screening pass in the state's
-// precision T over all elements; the exact FP64 test and the limiting (§4.3, Eqs. 48-52) for
-// elements the screen cannot clear.  For T = double the screen is the exact test.
+// Minimum of a value over the element's nel consecutive threads (thread lt of the element).
+// When nel is a power of two of at most 32 and the block is whole warps, the element's threads
+// are a lane-aligned part of one warp: a butterfly of shuffles leaves the minimum in every one
+// of them, with no block barrier.  Otherwise partial minima of groups of up to 32 go through
+// shared memory (two block barriers) and the result is valid in thread lt == 0.
+template <typename V>
+__device__ inline V element_min(V v, int te, int lt, int nel, bool pow2, V* sRed) {
+    if (pow2) {
+        const int width = nel < 32 ? nel : 32;
+        for (int o = width >> 1; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (nel <= 32) return v;
+        if ((lt & 31) == 0) sRed[te * nel + lt / 32] = v;
+        __syncthreads();
+        if (lt == 0)
+            for (int i = 1; i < nel / 32; ++i) v = fmin(v, sRed[te * nel + i]);
+        __syncthreads();
+        return v;
+    }
+    sRed[te * nel + lt] = v;
+    __syncthreads();
+    if (lt == 0)
+        for (int i = 1; i < nel; ++i) v = fmin(v, sRed[te * nel + i]);
+    __syncthreads();
+    return v;
+}
+
+constexpr int kLimStages = 3;   // tiles in flight per CTA of the limiter
+
+// Shared-memory layout of limit_kernel: kLimStages barriers and tiles, then the scratch of one
+// tile's screen and exact pass, then Vz.
+struct LimLayout {
+    size_t tile, row, red, el, eps, flag, vz, total;
+};
+__host__ __device__ inline LimLayout lim_layout(int TE, int N1, int dim, int M, int Q, int S, int tsz) {
+    const int NPT = dim == 2 ? N1 * N1 : N1, nel = Q * (dim == 2 ? N1 : 1);
+    auto a16 = [](size_t n) { return (n + 15) & ~(size_t)15; };
+    LimLayout L;
+    size_t o = 16 * kLimStages;                        // barriers
+    L.tile = o;
+    o += kLimStages * a16((size_t)TE * NPT * M * S * tsz);
+    L.row = o;
+    o += dim == 2 ? a16((size_t)TE * NPT * Q * S * tsz) : 0;
+    L.red = o;
+    o += (size_t)TE * nel * sizeof(double);
+    L.el = o;
+    o += (size_t)TE * 8 * sizeof(double);
+    L.eps = o;
+    o += (size_t)TE * 2 * sizeof(double);
+    L.flag = o;
+    o += (size_t)TE * sizeof(int);
+    L.vz = a16(o);
+    L.total = L.vz + (size_t)M * Q * tsz;
+    return L;
+}
+
+// Positivity limiter (§4.3, Eqs. 48-52), persistent: CTA b takes tiles b, b + grid, ... of TE
+// elements each.  Block (Q, NL, TE): thread (q, l, te) owns z-node q of line l of element te; in
+// 2D a line is row b = l of the element's points for the solution points and the x-faces
+// (r = -1, +1 along the row), and column a = l for the y-faces (s = -1, +1), so the element's
+// Q * N1 threads cover the solution points and all four faces once; in 1D (NL = 1) a thread
+// covers the element's points and both faces.  Tiles arrive by bulk copies, kLimStages ahead:
+// the CTA screens one tile while the copy engine fetches the next ones.
+// Screen in the state's precision T over every element; for T = float with a margin of 1e-4
+// of the mean density and energy above eps, far above float rounding, so that a cleared element
+// is admissible and untriggered in exact arithmetic.  Elements the screen cannot clear get the
+// exact test and the limiting in FP64: mean, eps = min(1e-8, rho_bar, p_bar), beta_1 for the
+// density (Eq. 50), beta_2 = the smallest root of p(ubar + beta (u* - ubar)) = eps over the
+// points (Eq. 51), and the modal scaling uhat <- ubar e_0 + beta (uhat - ubar e_0) written back.
 template <typename T, int N1, int DIM, int S>
-__global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A) {
-    constexpr int NPT = DIM == 1 ? N1 : N1 * N1;
-    extern __shared__ double lsm[];
+__global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntiles) {
+    constexpr int NL = DIM == 2 ? N1 : 1;
+    constexpr int NPT = DIM == 2 ? N1 * N1 : N1;
     const int Q = A.Q, M = A.M, TE = A.TE;
-    const int tq = threadIdx.x, te = threadIdx.y;
-    const int e = blockIdx.x * TE + te;
-    const bool active = e < A.E;
+    const int tq = threadIdx.x, tl = threadIdx.y, te = threadIdx.z;
+    const int nel = Q * NL;                         // threads per element
+    const int lt = tl * Q + tq;                     // thread within its element
+    const int tid = te * nel + lt, nthr = nel * TE;
+    const bool pow2 = (nel & (nel - 1)) == 0 && (nthr & 31) == 0;
+    const bool in_warp = pow2 && nel <= 32;         // an element's threads share one warp
+    const int elsz = NPT * M * S;
     pdl_trigger();
-    double* red = lsm;                                    // [TE][Q][2]
-    double* el = red + (size_t)TE * Q * 2;                // [TE][4]: rho_min, p_min, beta1, beta2
-    int* cand = reinterpret_cast<int*>(el + (size_t)TE * 4);   // [TE]
-    T* u = static_cast<T*>(A.u);
-    const size_t elsz = (size_t)NPT * M * S;
+
+    extern __shared__ __align__(16) unsigned char lsm[];
+    const LimLayout L = lim_layout(TE, N1, DIM, M, Q, S, (int)sizeof(T));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(lsm);   // [kLimStages], 16 bytes apart
+    const size_t tstride = (((size_t)TE * elsz * sizeof(T)) + 15) & ~(size_t)15;
+    T* sRow = reinterpret_cast<T*>(lsm + L.row);        // 2D: [TE][b][a][q][s] row values of the screen
+    double* sRed = reinterpret_cast<double*>(lsm + L.red);   // [TE][nel] partial minima
+    double* sEl = reinterpret_cast<double*>(lsm + L.el);     // [TE][8]: ubar[0..S-1], -, -, beta1, beta2
+    double* sEps = reinterpret_cast<double*>(lsm + L.eps);   // [TE][2]: density / pressure targets
+    int* sFlag = reinterpret_cast<int*>(lsm + L.flag);       // [TE]: 1 candidate, 2 admissible, 4 limited
+    T* sVz = reinterpret_cast<T*>(lsm + L.vz);               // [M][Q]
+
     const double* tab = A.tab;
     const double gamma = A.gamma;
-    // the screen reads its tables in T: the float copy of the block for float states (the
-    // same roundings as converting each entry, without a double conversion per use)
     const T* tabT = sizeof(T) == 4 && A.tabf ? reinterpret_cast<const T*>(A.tabf) : reinterpret_cast<const T*>(tab);
     const bool tab_is_T = sizeof(T) == 8 || A.tabf != nullptr;
     auto tabv = [&](int i) -> T { return tab_is_T ? tabT[i] : (T)tab[i]; };
-    T lmT[N1], lpT[N1];
+    T lmT[N1], lpT[N1], wT[NPT];
     double lmD[N1], lpD[N1];
 #pragma unroll
     for (int j = 0; j < N1; ++j) {
-        lmD[j] = tab[A.off.lm + j];
-        lpD[j] = tab[A.off.lp + j];
         lmT[j] = tabv(A.off.lm + j);
         lpT[j] = tabv(A.off.lp + j);
+        lmD[j] = tab[A.off.lm + j];
+        lpD[j] = tab[A.off.lp + j];
     }
-
-    const bool exact = sizeof(T) == sizeof(double);
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) wT[j] = tabv(A.off.w + j);
+    for (int i = tid; i < M * Q; i += nthr) sVz[i] = tabv(A.off.VzT + i);
+    T* u = static_cast<T*>(A.u);
+    // one bulk copy per tile when every tile starts on a 16-byte boundary
+    const bool bulk = ((size_t)elsz * sizeof(T)) % 16 == 0 && (reinterpret_cast<uintptr_t>(u) & 15) == 0;
+    auto tile_smem = [&](int i) { return reinterpret_cast<T*>(lsm + L.tile + (size_t)(i % kLimStages) * tstride); };
+    auto issue = [&](int i, int tile) {   // thread 0: fetch tile into stage i % kLimStages
+        const int e0 = tile * TE, ne = min(TE, A.E - e0);
+        const unsigned bytes = (unsigned)((size_t)ne * elsz * sizeof(T));
+        mbar_arrive_expect_tx(bar + 2 * (i % kLimStages), bytes);
+        bulk_load(tile_smem(i), u + (size_t)e0 * elsz, bytes, bar + 2 * (i % kLimStages));
+    };
+    if (bulk && tid == 0) {
+        for (int st = 0; st < kLimStages; ++st) mbar_init(bar + 2 * st, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
     pdl_wait();
-    if (active) {
-        const T* ue = u + (size_t)e * elsz;
-        // screen in T: element mean, nodal values at the solution points, every limiter point
-        T ub[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) ub[s] = T(0);
-#pragma unroll
-        for (int j = 0; j < NPT; ++j) {
-            const T wj = tabv(A.off.w + j);
-#pragma unroll
-            for (int s = 0; s < S; ++s) ub[s] += wj * ue[(size_t)j * M * S + s];
-        }
-        T v[S][NPT];
-#pragma unroll
-        for (int j = 0; j < NPT; ++j)
-#pragma unroll
-            for (int s = 0; s < S; ++s) v[s][j] = T(0);
-        for (int k = 0; k < M; ++k) {
-            const T vz = tabv(A.off.VzT + k * Q + tq);
-#pragma unroll
-            for (int j = 0; j < NPT; ++j)
-#pragma unroll
-                for (int s = 0; s < S; ++s) v[s][j] += vz * ue[((size_t)j * M + k) * S + s];
-        }
-        T rmin = T(1e30), pmin = T(1e30);
-        const T g1 = (T)(gamma - 1.0);
-        for_each_limiter_point<T, N1, DIM, S>(v, lmT, lpT, [&](const T (&w)[S]) {
-            T m2 = T(0);
-#pragma unroll
-            for (int d = 1; d < S - 1; ++d) m2 += w[d] * w[d];
-            rmin = fmin(rmin, w[0]);
-            pmin = fmin(pmin, g1 * (w[S - 1] - T(0.5) * m2 / w[0]));
-        });
-        // thresholds: exact for double states; for float states eps <= 1e-8 plus a margin far
-        // above float rounding (1e-4 of the mean density / energy), so that a cleared element
-        // is certainly admissible and untriggered in exact arithmetic
-        T m2 = T(0);
-#pragma unroll
-        for (int d = 1; d < S - 1; ++d) m2 += ub[d] * ub[d];
-        const T pb = g1 * (ub[S - 1] - T(0.5) * m2 / ub[0]);
-        bool c;
-        if (exact) {
-            const T eps_e = fmin(T(1e-8), fmin(ub[0], pb));
-            c = !(ub[0] > T(0) && pb > T(0)) || rmin < eps_e || pmin < eps_e;
+    if (bulk && tid == 0)
+        for (int st = 0; st < kLimStages; ++st)
+            if ((int)blockIdx.x + st * (int)gridDim.x < ntiles) issue(st, blockIdx.x + st * gridDim.x);
+    const T g1 = (T)(gamma - 1.0);
+    const bool exact = sizeof(T) == sizeof(double);
+
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int e0 = tile * TE;
+        const int ne = min(TE, A.E - e0);
+        const int e = e0 + te;
+        const bool active = te < ne;
+        T* sU = tile_smem(i);
+        if (bulk) {
+            const bool ok = mbar_wait(bar + 2 * (i % kLimStages), (unsigned)((i / kLimStages) & 1), kBulkWaitCycles);
+            if (!__syncthreads_and(ok)) {
+                // give up: latch the error, then wait (bounded) for every copy still in flight
+                // into this CTA's memory before leaving
+                if (tid == 0) {
+                    atomicOr(A.err, kErrTimeout);
+                    for (int j = i; j < i + kLimStages && (int)blockIdx.x + j * (int)gridDim.x < ntiles; ++j)
+                        mbar_wait(bar + 2 * (j % kLimStages), (unsigned)((j / kLimStages) & 1), kBulkWaitCycles);
+                }
+                __syncthreads();
+                return;
+            }
         } else {
-            const T mr = T(1e-4) * fabs(ub[0]), me = T(1e-4) * fabs(ub[S - 1]);
-            c = !(ub[0] > mr && pb > me) || rmin < T(1e-8) + mr || pmin < T(1e-8) + me;
+            const T* src = u + (size_t)e0 * elsz;
+            for (size_t o = tid; o < (size_t)ne * elsz; o += nthr) sU[o] = src[o];
+            __syncthreads();
         }
-        c = c || !(rmin == rmin) || !(pmin == pmin);
-        red[(te * Q + tq) * 2 + 0] = c ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    if (active && tq == 0) {
-        int any = 0;
-        for (int i = 0; i < Q; ++i) any |= red[(te * Q + i) * 2 + 0] != 0.0;
-        cand[te] = any;
-    }
-    __syncthreads();
-    const bool is_cand = active && cand[te];
-    // exact pass in double for candidate elements: mean, admissibility, minima, beta
-    double vd[S][NPT];
-    double ubar[S];
-    double rho_bar = 1.0, eps = 0.0;
-    double eps_r = 0.0, eps_p = 0.0;   // density / pressure targets (eps, raised for float states)
-    bool admissible = true;
-    if (is_cand) {
-        const T* ue = u + (size_t)e * elsz;
-#pragma unroll
-        for (int s = 0; s < S; ++s) ubar[s] = 0.0;
-#pragma unroll
-        for (int j = 0; j < NPT; ++j) {
-            const double wj = tab[A.off.w + j];
-#pragma unroll
-            for (int s = 0; s < S; ++s) ubar[s] += wj * ld(ue, (size_t)j * M * S + s);
-        }
-        rho_bar = ubar[0];
-        const double p_bar = pressure_d<S>(ubar, gamma);
-        admissible = rho_bar > 0.0 && p_bar > 0.0;
-        eps = fmin(1e-8, fmin(rho_bar, p_bar));
-        eps_r = eps_p = eps;
-        if (!exact) {
-            // a float state is rounded after limiting: aim 1e-5 of the mean density / energy
-            // above eps so that the rounded coefficients keep rho, p > 0 at every point
-            eps_r = fmin(eps + 1e-5 * rho_bar, 0.5 * rho_bar);
-            eps_p = fmin(eps + 1e-5 * fabs(ubar[S - 1]), 0.5 * p_bar);
-        }
-#pragma unroll
-        for (int j = 0; j < NPT; ++j)
-#pragma unroll
-            for (int s = 0; s < S; ++s) vd[s][j] = 0.0;
-        for (int k = 0; k < M; ++k) {
-            const double vz = tab[A.off.VzT + k * Q + tq];
-#pragma unroll
-            for (int j = 0; j < NPT; ++j)
-#pragma unroll
-                for (int s = 0; s < S; ++s) vd[s][j] += vz * ld(ue, ((size_t)j * M + k) * S + s);
-        }
-        double rmin = 1e300, pmin = 1e300;
-        for_each_limiter_point<double, N1, DIM, S>(vd, lmD, lpD, [&](const double (&w)[S]) {
+
+        // ---- screen in T
+        T rmin = T(1e30), pmin = T(1e30);
+        auto visit = [&](const T (&w)[S]) {
             rmin = fmin(rmin, w[0]);
-            pmin = fmin(pmin, pressure_d<S>(w, gamma));
-        });
-        red[(te * Q + tq) * 2 + 0] = rmin;
-        red[(te * Q + tq) * 2 + 1] = pmin;
-    }
-    __syncthreads();
-    if (is_cand && tq == 0) {
-        double a = 1e300, b = 1e300;
-        for (int i = 0; i < Q; ++i) {
-            a = fmin(a, red[(te * Q + i) * 2 + 0]);
-            b = fmin(b, red[(te * Q + i) * 2 + 1]);
-        }
-        el[te * 4 + 0] = a;
-        el[te * 4 + 1] = b;
-        double beta1 = 1.0;
-        if (rho_bar - a > 0.0) beta1 = fmin((rho_bar - eps_r) / (rho_bar - a), 1.0);
-        el[te * 4 + 2] = beta1;
-        if (!admissible) atomicOr(A.err, kErrPositivity);
-        if (!(a == a) || !(b == b)) atomicOr(A.err, kErrNonFinite);
-    }
-    __syncthreads();
-    const bool trig = is_cand && admissible && (el[te * 4 + 0] < eps_r || el[te * 4 + 1] < eps_p);
-    if (trig) {
-        const double beta1 = el[te * 4 + 2];
-        double bmin = 1.0;
-        for_each_limiter_point<double, N1, DIM, S>(vd, lmD, lpD, [&](const double (&w)[S]) {
-            double us[S];
+            pmin = fmin(pmin, pressure_t<T, S>(w, g1));
+        };
+        const T* ue = sU + (size_t)te * elsz;
+        if (active) {
+            const int row = DIM == 2 ? tl : 0;
+            T v[N1][S];
 #pragma unroll
-            for (int d = 0; d < S; ++d) us[d] = w[d];
-            us[0] = beta1 * (us[0] - rho_bar) + rho_bar;
-            if (pressure_d<S>(us, gamma) < eps_p) bmin = fmin(bmin, pressure_root<S>(ubar, us, eps_p, gamma));
-        });
-        red[(te * Q + tq) * 2 + 0] = bmin;
-    }
-    __syncthreads();
-    if (trig && tq == 0) {
-        double b2 = 1.0;
-        for (int i = 0; i < Q; ++i) b2 = fmin(b2, red[(te * Q + i) * 2 + 0]);
-        el[te * 4 + 3] = b2;
-    }
-    __syncthreads();
-    if (active && A.beta && tq == 0) A.beta[e] = trig ? el[te * 4 + 2] * el[te * 4 + 3] : 1.0;
-    if (trig) {
-        // uhat <- ubar e_0 + scale (uhat - ubar e_0); density scaled by beta2*beta1, the rest by beta2
-        const double beta1 = el[te * 4 + 2], beta2 = el[te * 4 + 3];
-        T* ue = u + (size_t)e * elsz;
-        for (size_t o = tq; o < elsz; o += Q) {
-            const int s = (int)(o % S), k = (int)((o / S) % M);
-            const double sc = s == 0 ? beta2 * beta1 : beta2;
-            const double mean = k == 0 ? ubar[s] : 0.0;
-            ue[o] = (T)(mean + sc * (ld(ue, o) - mean));
+            for (int a = 0; a < N1; ++a)
+#pragma unroll
+                for (int s = 0; s < S; ++s) v[a][s] = T(0);
+            for (int k = 0; k < M; ++k) {
+                const T vz = sVz[k * Q + tq];
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    T x[S];
+                    ldv<T, S>(ue + ((row * N1 + a) * M + k) * S, x);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) v[a][s] += vz * x[s];
+                }
+            }
+            T fL[S], fR[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                T l = T(0), r = T(0);
+#pragma unroll
+                for (int a = 0; a < N1; ++a) {
+                    l += lmT[a] * v[a][s];
+                    r += lpT[a] * v[a][s];
+                }
+                fL[s] = l;
+                fR[s] = r;
+            }
+#pragma unroll
+            for (int a = 0; a < N1; ++a) visit(v[a]);
+            visit(fL);
+            visit(fR);
+            if constexpr (DIM == 2) {
+#pragma unroll
+                for (int a = 0; a < N1; ++a)
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+                        sRow[(((size_t)te * NPT + row * N1 + a) * Q + tq) * S + s] = v[a][s];
+            }
         }
+        if constexpr (DIM == 2) {
+            if (in_warp) __syncwarp();
+            else __syncthreads();
+            if (active) {
+                const int a = tl;   // column
+                T fB[S], fT[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    T l = T(0), r = T(0);
+#pragma unroll
+                    for (int b = 0; b < N1; ++b) {
+                        const T x = sRow[(((size_t)te * NPT + b * N1 + a) * Q + tq) * S + s];
+                        l += lmT[b] * x;
+                        r += lpT[b] * x;
+                    }
+                    fB[s] = l;
+                    fT[s] = r;
+                }
+                visit(fB);
+                visit(fT);
+            }
+        }
+        // the element mean over r (and s) and z: sum_j (w_j / 2^d) uhat_{j,0} (Phi_0 = 1); the
+        // screen's reductions and decision stay in T (double arithmetic is slow on this part)
+        T* sElT = reinterpret_cast<T*>(sEl);
+        T mean_s = T(0);
+        if (active && lt < S) {
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) mean_s += wT[j] * ue[(size_t)j * M * S + lt];
+            if (!in_warp) sElT[te * 8 + lt] = mean_s;
+        }
+        T* sRedT = reinterpret_cast<T*>(sRed);
+        const T rm = element_min<T>(rmin, te, lt, nel, pow2, sRedT);
+        const T pm = element_min<T>(pmin, te, lt, nel, pow2, sRedT);
+        T ub[S];
+        if (in_warp) {
+            // the element's lanes start at lane (lane - lt): gather the mean from its first S lanes
+            const int base = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) % 32 - lt;
+#pragma unroll
+            for (int s = 0; s < S; ++s) ub[s] = __shfl_sync(0xffffffffu, mean_s, base + s);
+        }
+        if (active && lt == 0) {
+            if (!in_warp) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) ub[s] = sElT[te * 8 + s];
+            }
+            const T pb = pressure_t<T, S>(ub, g1);
+            bool c;
+            if (exact) {
+                const T eps_e = fmin(T(1e-8), fmin(ub[0], pb));
+                c = !(ub[0] > T(0) && pb > T(0)) || rm < eps_e || pm < eps_e;
+            } else {
+                const T mr = T(1e-4) * fabs(ub[0]), me = T(1e-4) * fabs(ub[S - 1]);
+                c = !(ub[0] > mr && pb > me) || rm < T(1e-8) + mr || pm < T(1e-8) + me;
+            }
+            c = c || !(rm == rm) || !(pm == pm) || !(pb == pb);
+            sFlag[te] = c ? 1 : 0;
+        }
+        // one barrier publishes the decisions and tells whether any element needs the exact pass
+        const bool any = __syncthreads_or(active && lt == 0 && sFlag[te] != 0);
+        const bool is_cand = any && active && sFlag[te] != 0;
+        if (any) {
+            // ---- exact pass in FP64 for the candidates
+            // this thread's line values in double (2D: row b = tl, or column a = tl)
+            auto line_values = [&](bool column, double (&vd)[N1][S]) {
+#pragma unroll
+                for (int a = 0; a < N1; ++a)
+#pragma unroll
+                    for (int s = 0; s < S; ++s) vd[a][s] = 0.0;
+                for (int k = 0; k < M; ++k) {
+                    const double vz = tab[A.off.VzT + k * Q + tq];
+#pragma unroll
+                    for (int a = 0; a < N1; ++a) {
+                        const int j = DIM == 1 ? a : (column ? a * N1 + tl : tl * N1 + a);
+#pragma unroll
+                        for (int s = 0; s < S; ++s) vd[a][s] += vz * (double)ue[((size_t)j * M + k) * S + s];
+                    }
+                }
+            };
+            // every point of this thread in double: the line's solution points and its two
+            // faces; in 2D also the column's two faces
+            auto visit_points = [&](auto&& f) {
+                double vd[N1][S];
+                line_values(false, vd);
+                double fL[S], fR[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    double l = 0.0, r = 0.0;
+#pragma unroll
+                    for (int a = 0; a < N1; ++a) {
+                        l += lmD[a] * vd[a][s];
+                        r += lpD[a] * vd[a][s];
+                    }
+                    fL[s] = l;
+                    fR[s] = r;
+                }
+#pragma unroll
+                for (int a = 0; a < N1; ++a) f(vd[a]);
+                f(fL);
+                f(fR);
+                if constexpr (DIM == 2) {
+                    line_values(true, vd);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        double l = 0.0, r = 0.0;
+#pragma unroll
+                        for (int b = 0; b < N1; ++b) {
+                            l += lmD[b] * vd[b][s];
+                            r += lpD[b] * vd[b][s];
+                        }
+                        fL[s] = l;
+                        fR[s] = r;
+                    }
+                    f(fL);
+                    f(fR);
+                }
+            };
+            if (is_cand && lt < S) {
+                double acc = 0.0;
+                for (int j = 0; j < NPT; ++j) acc += tab[A.off.w + j] * (double)ue[(size_t)j * M * S + lt];
+                sEl[te * 8 + lt] = acc;
+            }
+            __syncthreads();
+            double ubar[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) ubar[s] = is_cand ? sEl[te * 8 + s] : 1.0;
+            double dr = 1e300, dp = 1e300;
+            if (is_cand) {
+                visit_points([&](const double (&w)[S]) {
+                    dr = fmin(dr, w[0]);
+                    dp = fmin(dp, pressure_d<S>(w, gamma));
+                });
+            }
+            dr = element_min<double>(dr, te, lt, nel, pow2, sRed);
+            dp = element_min<double>(dp, te, lt, nel, pow2, sRed);
+            if (is_cand && lt == 0) {
+                const double rho_bar = ubar[0], p_bar = pressure_d<S>(ubar, gamma);
+                const bool admissible = rho_bar > 0.0 && p_bar > 0.0;
+                const double eps = fmin(1e-8, fmin(rho_bar, p_bar));
+                double eps_r = eps, eps_p = eps;
+                if (!exact) {
+                    // a float state is rounded after limiting: aim 1e-5 of the mean density /
+                    // energy above eps so that the rounded coefficients keep rho, p > 0
+                    eps_r = fmin(eps + 1e-5 * rho_bar, 0.5 * rho_bar);
+                    eps_p = fmin(eps + 1e-5 * fabs(ubar[S - 1]), 0.5 * p_bar);
+                }
+                double beta1 = 1.0;
+                if (rho_bar - dr > 0.0) beta1 = fmin((rho_bar - eps_r) / (rho_bar - dr), 1.0);
+                const bool trig = admissible && (dr < eps_r || dp < eps_p);
+                sEl[te * 8 + 6] = beta1;
+                sEps[te * 2 + 0] = eps_r;
+                sEps[te * 2 + 1] = eps_p;
+                sFlag[te] = 1 | (admissible ? 2 : 0) | (trig ? 4 : 0);
+                if (!admissible) atomicOr(A.err, kErrPositivity);
+                if (!(dr == dr) || !(dp == dp)) atomicOr(A.err, kErrNonFinite);
+            }
+            __syncthreads();
+            const bool trig = is_cand && (sFlag[te] & 4) != 0;
+            double bmin = 1.0;
+            if (trig) {
+                const double beta1 = sEl[te * 8 + 6], eps_p = sEps[te * 2 + 1], rho_bar = ubar[0];
+                visit_points([&](const double (&w)[S]) {
+                    double us[S];
+#pragma unroll
+                    for (int d = 0; d < S; ++d) us[d] = w[d];
+                    us[0] = beta1 * (us[0] - rho_bar) + rho_bar;
+                    if (pressure_d<S>(us, gamma) < eps_p) bmin = fmin(bmin, pressure_root<S>(ubar, us, eps_p, gamma));
+                });
+            }
+            bmin = element_min<double>(bmin, te, lt, nel, pow2, sRed);
+            if (trig && lt == 0) sEl[te * 8 + 7] = bmin;
+            __syncthreads();
+            if (active && lt == 0 && A.beta) A.beta[e] = trig ? sEl[te * 8 + 6] * sEl[te * 8 + 7] : 1.0;
+            if (trig) {
+                // uhat <- ubar e_0 + scale (uhat - ubar e_0); density scaled by beta2*beta1, the rest
+                // by beta2
+                const double beta1 = sEl[te * 8 + 6], beta2 = sEl[te * 8 + 7];
+                T* ug = u + (size_t)e * elsz;
+                for (int oo = lt; oo < elsz; oo += nel) {
+                    const int s = oo % S, k = (oo / S) % M;
+                    const double sc = s == 0 ? beta2 * beta1 : beta2;
+                    const double mean = k == 0 ? ubar[s] : 0.0;
+                    ug[oo] = (T)(mean + sc * ((double)ue[oo] - mean));
+                }
+            }
+            __syncthreads();   // every thread is done with this stage's tile
+        } else if (active && lt == 0 && A.beta) {
+            A.beta[e] = 1.0;
+        }
+        // the tile's stage is free: the barrier above, or the one of the decisions when no
+        // element needed the exact pass (nothing reads the tile after it then)
+        if (bulk && tid == 0 && tile + kLimStages * (int)gridDim.x < ntiles) issue(i + kLimStages, tile + kLimStages * gridDim.x);
     }
 }
 
@@ -324,13 +511,43 @@ int grid_for(size_t n, int threads) {
     return (int)g;
 }
 
+// Tile: as many elements as fit 256 threads (Q z-nodes x lines per element), at most 100 KB of
+// shared memory per CTA; persistent grid: the CTAs resident at once, at most one per tile.
 template <typename T, int N1, int DIM, int S>
-cudaError_t limit_typed(const LimitArgs& A, cudaStream_t st) {
-    const size_t smem = sizeof(double) * ((size_t)A.TE * A.Q * 2 + (size_t)A.TE * 4) + sizeof(int) * A.TE + 16;
+cudaError_t limit_typed(const LimitArgs& Ain, cudaStream_t st) {
+    LimitArgs A = Ain;
+    const int nel = A.Q * (DIM == 2 ? N1 : 1);
+    int TE = 256 / nel;
+    if (TE < 1) TE = 1;
+    while (TE > 1 && lim_layout(TE, N1, DIM, A.M, A.Q, S, (int)sizeof(T)).total > 100 * 1024) --TE;
+    A.TE = TE;
+    const size_t smem = lim_layout(TE, N1, DIM, A.M, A.Q, S, (int)sizeof(T)).total;
     auto kern = limit_kernel<T, N1, DIM, S>;
-    dim3 block(A.Q, A.TE);
-    dim3 grid((A.E + A.TE - 1) / A.TE);
-    return launch_pdl(kern, grid, block, smem, st, A);
+    const int threads = nel * TE;
+    // occupancy query cached per instantiation, device and launch shape (a stage launches this)
+    thread_local int c_dev = -1, c_threads = -1, c_grid = 0;
+    thread_local size_t c_smem = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev != c_dev || threads != c_threads || smem != c_smem) {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        c_dev = dev;
+        c_threads = threads;
+        c_smem = smem;
+        c_grid = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    const int ntiles = (A.E + TE - 1) / TE;
+    const int grid = ntiles < c_grid ? ntiles : c_grid;
+    dim3 block(A.Q, DIM == 2 ? N1 : 1, TE);
+    return launch_pdl(kern, dim3(grid), block, smem, st, A, ntiles);
 }
 
 template <typename T>
