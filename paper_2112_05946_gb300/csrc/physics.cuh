@@ -9,6 +9,22 @@
 
 namespace frsg {
 
+// 1/x and sqrt(x) of the flux evaluations.  Double: the IEEE operations.  Float (the FP32 form):
+// the hardware approximations (rcp.approx, sqrt.approx; a few ulp), whose error is far below the
+// FP32 form's stated bounds against the FP64 oracle; sqrt(+0) = +0 and 1/0 = inf as in IEEE.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double root(double x) { return sqrt(x); }
+__device__ __forceinline__ float root(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Physical flux along direction DIR (0 = x, 1 = y) of equation EQ with S variables.
 template <typename T, int EQ, int S, int DIM, int DIR>
 __device__ __forceinline__ void phys_flux(const T (&u)[S], T (&f)[S], T adv, T gamma) {
@@ -18,14 +34,15 @@ __device__ __forceinline__ void phys_flux(const T (&u)[S], T (&f)[S], T adv, T g
         f[0] = T(0.5) * u[0] * u[0];
     } else if constexpr (DIM == 1) {
         const T rho = u[0], m = u[1], E = u[2];
-        const T v = m / rho;
+        const T v = m * recip(rho);
         const T p = (gamma - T(1)) * (E - T(0.5) * m * v);
         f[0] = m;
         f[1] = m * v + p;
         f[2] = (E + p) * v;
     } else {
         const T rho = u[0], mx = u[1], my = u[2], E = u[3];
-        const T vx = mx / rho, vy = my / rho;
+        const T ir = recip(rho);
+        const T vx = mx * ir, vy = my * ir;
         const T p = (gamma - T(1)) * (E - T(0.5) * (mx * vx + my * vy));
         const T vn = DIR == 0 ? vx : vy;
         f[0] = rho * vn;
@@ -44,21 +61,23 @@ __device__ __forceinline__ T wave_speed(const T (&u)[S], T adv, T gamma) {
         return fabs(u[0]);
     } else if constexpr (DIM == 1) {
         const T rho = u[0], m = u[1], E = u[2];
-        const T v = m / rho;
+        const T ir = recip(rho);
+        const T v = m * ir;
         const T p = (gamma - T(1)) * (E - T(0.5) * m * v);
-        return fabs(v) + sqrt(gamma * p / rho);
+        return fabs(v) + root(gamma * p * ir);
     } else {
         const T rho = u[0], mx = u[1], my = u[2], E = u[3];
-        const T vx = mx / rho, vy = my / rho;
+        const T ir = recip(rho);
+        const T vx = mx * ir, vy = my * ir;
         const T p = (gamma - T(1)) * (E - T(0.5) * (mx * vx + my * vy));
-        return fabs(DIR == 0 ? vx : vy) + sqrt(gamma * p / rho);
+        return fabs(DIR == 0 ? vx : vy) + root(gamma * p * ir);
     }
 }
 
 // Euler flux along DIR and the spectral radius |v_n| + c from one reciprocal of rho.
 template <typename T, int S, int DIM, int DIR>
 __device__ __forceinline__ T euler_flux_speed(const T (&u)[S], T (&f)[S], T gamma) {
-    const T ir = T(1) / u[0];
+    const T ir = recip(u[0]);
     T m2 = T(0);
 #pragma unroll
     for (int d = 1; d < S - 1; ++d) m2 += u[d] * u[d];
@@ -68,7 +87,7 @@ __device__ __forceinline__ T euler_flux_speed(const T (&u)[S], T (&f)[S], T gamm
     for (int s = 0; s < S; ++s) f[s] = u[s] * vn;
     f[1 + DIR] += p;
     f[S - 1] += p * vn;
-    return fabs(vn) + sqrt(gamma * p * ir);
+    return fabs(vn) + root(gamma * p * ir);
 }
 
 // f^I = (f(uL) + f(uR))/2 - alpha (uR - uL)/2, alpha = max(lambda(uL), lambda(uR)).
@@ -94,7 +113,7 @@ __device__ __forceinline__ void llf(const T (&uL)[S], const T (&uR)[S], T (&fI)[
 // Euler flux along DIR with the normal velocity and sound speed of the state.
 template <typename T, int S, int DIR>
 __device__ __forceinline__ void euler_flux_vc(const T (&u)[S], T (&f)[S], T gamma, T* vn, T* c) {
-    const T ir = T(1) / u[0];
+    const T ir = recip(u[0]);
     T m2 = T(0);
 #pragma unroll
     for (int d = 1; d < S - 1; ++d) m2 += u[d] * u[d];
@@ -104,7 +123,7 @@ __device__ __forceinline__ void euler_flux_vc(const T (&u)[S], T (&f)[S], T gamm
     for (int s = 0; s < S; ++s) f[s] = u[s] * *vn;
     f[1 + DIR] += p;
     f[S - 1] += p * *vn;
-    *c = sqrt(gamma * p * ir);
+    *c = root(gamma * p * ir);
 }
 
 // HLL with the Davis signal speeds: F_L if S_L >= 0, F_R if S_R <= 0, else
