@@ -22,10 +22,10 @@
  *    the last error is kept in the context (fr_sg_last_error).  Errors found by kernels
  *    (non-finite values, inadmissible element means) are latched in a device word and
  *    reported by the next call that synchronises (fr_sg_check, or any call with host output).
- *  - Precision: FRSG_FP64 keeps the state in double; FRSG_FP32 keeps it in float and
- *    computes the residual in float, with the limiter, the time-step reduction and the
- *    moments in double.  Calls that take "void*" state use the context's precision;
- *    calls that take "double*" always use double.
+ *  - Precision: FRSG_FP64 keeps the state in double; FRSG_FP32 and FRSG_FP32_TC keep it in
+ *    float and compute the residual in float, with the limiter's exact test, the time-step
+ *    reduction and the moments in double.  Calls that take "void*" state use the context's
+ *    precision (float for both float forms); calls that take "double*" always use double.
  */
 #ifndef FRSG_H
 #define FRSG_H
@@ -56,7 +56,12 @@ enum { FRSG_FILTER_NONE = 0, FRSG_FILTER_EXP = 1, FRSG_FILTER_L2 = 2, FRSG_FILTE
 /* Interface flux: local Lax-Friedrichs, or HLL with the Davis signal speeds
  * S_L = min(lambda_min(u_L), lambda_min(u_R)), S_R = max(lambda_max(u_L), lambda_max(u_R)). */
 enum { FRSG_FLUX_LLF = 0, FRSG_FLUX_HLL = 1 };
-enum { FRSG_FP64 = 0, FRSG_FP32 = 1 };
+/* Precision forms.  FRSG_FP32_TC: the FP32 form with the Galerkin projection of the residual
+ * (§2.1, Eq. 6 with the quadrature of Eq. 5) on the tensor cores (tcgen05 MMA, tf32 operands
+ * split into a tf32 part and a float remainder, three products accumulated in FP32: float
+ * accuracy); 2D elements with P = 3, Q = 8 and at most 8 gPC modes (FRSG_E_INVAL otherwise),
+ * tiles of 4 or 8 elements. */
+enum { FRSG_FP64 = 0, FRSG_FP32 = 1, FRSG_FP32_TC = 2 };
 enum { FRSG_HOST = 0, FRSG_DEVICE = 1 };
 
 /* Problem description.  Plain old data; struct_size must be sizeof(frsg_config). */
@@ -80,7 +85,7 @@ typedef struct {
     double f_eps1, f_eps2;    /* L2 filter damping of the last physical / random mode (§4.1.2, Eq. 39) */
     double s0, kappa;         /* detector parameters (§4.2, Eq. 47), log10 scale */
     int32_t limiter;          /* 1: positivity-preserving limiter on every stage input (§4.3) */
-    int32_t precision;        /* FRSG_FP64 or FRSG_FP32 */
+    int32_t precision;        /* FRSG_FP64, FRSG_FP32 or FRSG_FP32_TC */
     int32_t flux;             /* FRSG_FLUX_LLF (§3.3) or FRSG_FLUX_HLL (Euler setup tables of §5.3-5.4),
                                  evaluated pointwise at every z-node of every face */
 } frsg_config;

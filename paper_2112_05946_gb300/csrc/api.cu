@@ -19,7 +19,7 @@
 namespace frsg {
 size_t stage1d_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S);
 size_t stage1d_wide_smem_bytes(bool fp64, int TE, int NP, int M, int Q, int S);
-size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S);
+size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S, bool tc);
 }  // namespace frsg
 
 struct frsg_ctx {
@@ -110,7 +110,9 @@ std::string validate(const frsg_config& c) {
     if (c.equation < FRSG_EQ_ADVECTION || c.equation > FRSG_EQ_EULER) return "unknown equation";
     if (c.filter < FRSG_FILTER_NONE || c.filter > FRSG_FILTER_LASSO) return "unknown filter";
     if (c.filter == FRSG_FILTER_LASSO && c.dim != 1) return "the Lasso filter is implemented for 1D elements";
-    if (c.precision != FRSG_FP64 && c.precision != FRSG_FP32) return "unknown precision";
+    if (c.precision != FRSG_FP64 && c.precision != FRSG_FP32 && c.precision != FRSG_FP32_TC) return "unknown precision";
+    if (c.precision == FRSG_FP32_TC && !(c.dim == 2 && c.P == 3 && c.Q == 8 && c.N + 1 <= 8))
+        return "the FP32_TC form is built for 2D elements with P = 3, Q = 8 and at most 8 gPC modes";
     if (c.limiter && c.equation != FRSG_EQ_EULER) return "the positivity limiter is defined for Euler only";
     if (c.dim == 2 && c.equation != FRSG_EQ_EULER) return "2D supports the Euler equations only";
     for (int i = 0; i < (c.dim == 1 ? 2 : 4); ++i)
@@ -536,11 +538,20 @@ int choose_tile_1d(const frsg_ctx* c) {
     return te;
 }
 
+bool tc_form(const frsg_ctx* c) { return c->cfg.precision == FRSG_FP32_TC; }
+
+// A 2D tile fits: threads (at most 512), shared memory, and for the FP32_TC form whole MMA tiles
+// read back by all four TMEM lane quarters (4 or 8 elements).
+bool tile_fits_2d(const frsg_ctx* c, int te, size_t smem_cap) {
+    if (te < 1 || te * c->Q * c->n1 > 512) return false;
+    if (tc_form(c) && te != 4 && te != 8) return false;
+    return frsg::stage2d_smem_bytes(c->fp64, te, c->n1, c->M, c->Q, c->S, tc_form(c)) <= smem_cap;
+}
+
 int choose_tile_2d(const frsg_ctx* c) {
+    if (tc_form(c)) return tile_fits_2d(c, 8, 100 * 1024) && c->E / 8 >= 2 * 152 ? 8 : 4;
     int te = 1;
-    while (te < 8 && frsg::stage2d_smem_bytes(c->fp64, te * 2, c->n1, c->M, c->Q, c->S) <= 100 * 1024 &&
-           te * 2 * c->Q * c->n1 <= 512 && c->E / (te * 2) >= 2 * 152)
-        te *= 2;
+    while (te < 8 && tile_fits_2d(c, te * 2, 100 * 1024) && c->E / (te * 2) >= 2 * 152) te *= 2;
     return te;
 }
 
@@ -626,7 +637,7 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     ctx->TE = cfg->dim == 1 ? choose_tile_1d(ctx) : 1;
     ctx->TE_lim = std::max(1, 256 / ctx->Q);   // limit_kernel is built for at most 256 threads
     if (cfg->dim == 2) {
-        if (frsg::stage2d_smem_bytes(ctx->fp64, 1, ctx->n1, ctx->M, ctx->Q, ctx->S) > 200 * 1024) {
+        if (!tile_fits_2d(ctx, tc_form(ctx) ? 4 : 1, 200 * 1024)) {
             fr_sg_destroy(ctx);
             return FRSG_E_INVAL;
         }
@@ -1235,8 +1246,7 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
             if (c.dim == 1) {
                 fits = tile_fits_1d(ctx, te, w == 2 ? 0 : w);
             } else {
-                fits = te * ctx->Q * ctx->n1 <= 512 &&
-                       frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) <= 200 * 1024;
+                fits = tile_fits_2d(ctx, te, 200 * 1024);
             }
             if (fits && te <= ctx->E) cand.push_back({c.dim == 1 ? w : 0, te});
         }
@@ -1675,9 +1685,9 @@ frsg_status fr_sg_set_tile(frsg_ctx* ctx, int te, int* te_out) {
         if (!tile_fits_1d(ctx, te, ctx->wide == 2 ? 0 : ctx->wide))
             return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
     } else {
-        if (te * ctx->Q * ctx->n1 > 512 ||
-            frsg::stage2d_smem_bytes(ctx->fp64, te, ctx->n1, ctx->M, ctx->Q, ctx->S) > 220 * 1024)
-            return fail(ctx, FRSG_E_INVAL, "tile too large for one CTA");
+        if (!tile_fits_2d(ctx, te, 220 * 1024))
+            return fail(ctx, FRSG_E_INVAL, tc_form(ctx) ? "the FP32_TC form takes tiles of 4 or 8 elements"
+                                                        : "tile too large for one CTA");
     }
     if (want != ctx->TE) drop_graphs(ctx);
     ctx->TE = want;

@@ -15,23 +15,44 @@
 //   a4  projection of the nodal residual onto the modes (§2.1, Eq. 6)
 //   a8  SSP combination; a9 detector on density with the tensor modal basis
 //       Psi_ma(r) Psi_mb(s) Phi_k(z) (§4.2); a10 filter of flagged elements (§4.1, Eq. 34)
+//
+// TC (the FP32_TC form): the projection a4 runs on the tensor cores.  The nodal residual is
+// a matrix G [rows (te, j, s)] x [K = Q z-nodes]; the projection is G Pz^T, with Pz the
+// [mode k] x [z-node q] projection table (§2.1, Eq. 6 with the quadrature of Eq. 5).  The
+// sweeps write G straight into the K-major layout of the MMA operand (core matrices of 8 rows
+// x 16 bytes, padded strides so that the sweeps' stores hit distinct banks), split into a
+// tf32 part and the float remainder; one thread issues, per 128-row tile (two elements),
+// three kind::tf32 MMAs Ghi Pzhi + Ghi Pzlo + Glo Pzhi (the 3xTF32 product, float accuracy)
+// into a TMEM accumulator of 16 columns; each warp then reads its lane quarter of the tiles
+// and forms the SSP combination.
 #include <cuda_runtime.h>
 
 #include "epilogue.cuh"
 #include "internal.h"
 #include "physics.cuh"
+#include "tc.cuh"
 
 namespace frsg {
 namespace {
 
+// TC operand layouts: G [TE*Np*S rows] x [Q = 8], K-major, LBO 144 and SBO 272 bytes (one
+// 16-byte pad per core matrix and per 8-row group, so that the sweeps' stores of one warp fall
+// in distinct banks); Pz^T padded to 16 rows of modes, LBO 128, SBO 256.
+constexpr unsigned kTcLboA = 144, kTcSboA = 272, kTcLboB = 128, kTcSboB = 256;
+constexpr int kTcN = 16;                   // MMA N: the modes, padded
+__host__ __device__ inline size_t tc_a_bytes(int TE, int Np, int S) { return (size_t)TE * Np * S / 8 * kTcSboA; }
+
 template <typename T>
-__host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int S) {
+__host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int S, bool tc) {
     const int Np = n1 * n1;
     size_t n = 0;
     n += (size_t)TE * Np * M * S;           // U: the tile (later the new state)
     n += (size_t)(2 + 2 * TE) * n1 * M * S; // modal face traces of the neighbours (x-halo, below, above)
     n += (size_t)TE * Np * S * Q;           // Un (nodal values)
-    n += ((size_t)TE * Np * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;   // G (nodal residual, rows padded; later modal coefficients)
+    if (tc)                                 // G as the MMA operand, tf32 part and remainder; Pz^T likewise
+        n += (2 * tc_a_bytes(TE, Np, S) + 2 * (size_t)kTcN * 8 * sizeof(float)) / sizeof(T);
+    else                                    // G (nodal residual, rows padded; later modal coefficients)
+        n += ((size_t)TE * Np * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;
     n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][q][s]
     n += 2 * (size_t)M * Q;                 // Vz, Pz
     n += (size_t)n1 * n1 + 4 * n1;          // D, lm, lp, dhL, dhR
@@ -41,8 +62,9 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
 }
 
 template <typename T>
-size_t smem2d_bytes_t(int TE, int n1, int M, int Q, int S) {
-    return smem2d_elems<T>(TE, n1, M, Q, S) * sizeof(T) + (size_t)TE * sizeof(int) + 16;
+size_t smem2d_bytes_t(int TE, int n1, int M, int Q, int S, bool tc) {
+    // the flags, then (TC) the MMA barrier and the TMEM address
+    return smem2d_elems<T>(TE, n1, M, Q, S, tc) * sizeof(T) + (size_t)TE * sizeof(int) + 16 + (tc ? 32 : 0);
 }
 
 // A neighbour's trace at z-node q from its modal face trace ft [k][s] (one line of a face):
@@ -63,8 +85,10 @@ __device__ inline void face_eval(const T* ft, int M, const T* Vzq_stride, int Q,
 // MC, QC: the mode and z-node counts when fixed at compile time (0: taken from A).
 // Blocks hold at most 512 threads.  Float builds are held to 80 registers: with about 35 KB of
 // shared memory per 4-element CTA that lets six CTAs share an SM (at 86 registers, five).
-template <typename T, int N1, int S, int MC = 0, int QC = 0>
+template <typename T, int N1, int S, int MC = 0, int QC = 0, bool TC = false>
 __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const StageArgs A) {
+    static_assert(!TC || (sizeof(T) == 4 && N1 == 4 && S == 4 && QC == 8 && MC > 0 && MC <= 8),
+                  "the tensor-core projection is built for float, P = 3, four variables, Q = 8, M <= 8");
     constexpr int NP = N1 * N1;
     constexpr int EQ = FRSG_EQ_EULER;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -86,7 +110,17 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     T* sFT = p; p += (size_t)(2 + 2 * TE) * N1 * M * S;   // [face][line][k][s]
     T* sUn = p; p += (size_t)TE * NP * S * Q;            // [te][point][q][s]
     const int GR = S * Q + (sizeof(T) == 4 ? 1 : 0);   // row stride of the nodal residual (float: padded)
-    T* sG = p; p += ((size_t)TE * NP * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;
+    T* sG = p;                                         // CUDA-core projection: [te][point][GR]
+    unsigned char* sAh = reinterpret_cast<unsigned char*>(p);   // TC: G, tf32 part / float remainder
+    unsigned char* sAl = sAh + tc_a_bytes(TE, NP, S);
+    float* sBh = reinterpret_cast<float*>(sAl + tc_a_bytes(TE, NP, S));   // TC: Pz^T, tf32 part / remainder
+    float* sBl = sBh + kTcN * 8;
+    if constexpr (TC) p += (2 * tc_a_bytes(TE, NP, S) + 2 * (size_t)kTcN * 8 * sizeof(float)) / sizeof(T);
+    else p += ((size_t)TE * NP * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;
+    // element (row, q) of the G operand: row = (te * NP + j) * S + s
+    auto g_at = [&](unsigned char* base, int row, int q) -> float* {
+        return reinterpret_cast<float*>(base + kmajor_offset(row, q, kTcLboA, kTcSboA));
+    };
     T* sTx = p; p += (size_t)(TE + 2) * 2 * N1 * S * Q;  // [row][side][line][q][s]
     T* sVz = p; p += M * Q;
     T* sPz = p; p += M * Q;
@@ -101,6 +135,11 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     T* sTop = p; p += NP;
     T* sRed = p; p += 2 * TE * N1 * Q;
     int* sFlag = reinterpret_cast<int*>(p);
+    // TC: the MMA completion barrier (16-byte aligned after the flags) and the TMEM address
+    uint64_t* sBar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(sFlag + TE) + 15) & ~(uintptr_t)15);
+    uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 2);
+    const int warp = tid >> 5, lane = tid & 31;
+    const uint32_t kTmemCols = TE <= 4 ? 32 : 64;   // TE/2 tiles x 16 columns (a power of two >= 32)
 
     const T* tab = table_block<T>(A);
     for (int i = tid; i < M * Q; i += nthr) {
@@ -176,6 +215,29 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     const StageConsts<T> sK = make_consts<T>(A, dt_raw);
     const T gamma = sK.gamma, adv = sK.adv;
     if (A.do_filter) finish_filter_strengths<T>(A, NP, sLam, tid, nthr, sK.adt);   // read after later barriers
+    uint32_t tmem = 0;
+    if constexpr (TC) {
+        // Pz^T as the B operand (rows: modes, padded with zeros to 16; K: the 8 z-nodes),
+        // tf32 part and remainder; the completion barrier of the MMAs; the TMEM accumulator
+        for (int i = tid; i < kTcN * 8; i += nthr) {
+            const int n = i >> 3, q = i & 7;
+            const float pz = n < M ? (float)sPz[n * Q + q] : 0.f;
+            const float hi = tf32_round(pz);
+            const unsigned o = kmajor_offset(n, q, kTcLboB, kTcSboB) / 4;
+            sBh[o] = hi;
+            sBl[o] = pz - hi;
+        }
+        fence_async_shared();
+        if (tid == 0) {
+            mbar_init(sBar, 1);
+            mbar_init_fence();
+        }
+        if (warp == 0) tmem_alloc(sTmem, kTmemCols);
+        tc_fence_before_sync();
+        __syncthreads();
+        tc_fence_after_sync();
+        tmem = *sTmem;
+    }
 
     const bool active = te < ne;
     const int ex = ex0 + te;
@@ -314,7 +376,8 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
                 T d = (fIL[s] - fDL[s]) * sdhL[a] + (fIR[s] - fDR[s]) * sdhR[a];
 #pragma unroll
                 for (int m = 0; m < N1; ++m) d += sD[a * N1 + m] * f[m][s];
-                sG[(te * NP + b * N1 + a) * GR + s * Q + tq] = -invJ * d;
+                if constexpr (TC) *g_at(sAh, (te * NP + b * N1 + a) * S + s, tq) = -invJ * d;
+                else sG[(te * NP + b * N1 + a) * GR + s * Q + tq] = -invJ * d;
             }
     }
     __syncthreads();
@@ -358,9 +421,19 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
                 T d = (gIB[s] - gDB[s]) * sdhL[b] + (gIT[s] - gDT[s]) * sdhR[b];
 #pragma unroll
                 for (int m = 0; m < N1; ++m) d += sD[b * N1 + m] * g[m][s];
-                sG[(te * NP + b * N1 + a) * GR + s * Q + tq] -= invJ * d;
+                if constexpr (TC) {
+                    // the final residual, split into its tf32 part and the float remainder
+                    const int row = (te * NP + b * N1 + a) * S + s;
+                    const float gv = *g_at(sAh, row, tq) - invJ * d;
+                    const float hi = tf32_round(gv);
+                    *g_at(sAh, row, tq) = hi;
+                    *g_at(sAl, row, tq) = gv - hi;
+                } else {
+                    sG[(te * NP + b * N1 + a) * GR + s * Q + tq] -= invJ * d;
+                }
             }
     }
+    if constexpr (TC) fence_async_shared();   // the operand stores, to the tensor cores
     __syncthreads();
 
     // ---- projection + SSP combination
@@ -369,7 +442,70 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     T* sTile = sU;
     const size_t gbase = (size_t)e0 * elsz;
     bool bad = false;
-    if (active) {
+    if constexpr (TC) {
+        // one thread issues the three MMAs of every 128-row tile (elements 2t, 2t + 1) into
+        // TMEM columns 16 t ..; the others wait for their completion
+        if (tid == 0) {
+            tc_fence_after_sync();
+            const uint32_t id = idesc_tf32(128, kTcN);
+            const uint64_t bh = smem_desc_kmajor(sBh, kTcLboB, kTcSboB), bl = smem_desc_kmajor(sBl, kTcLboB, kTcSboB);
+            for (int t = 0; t < TE / 2; ++t) {
+                const size_t off = (size_t)t * 16 * kTcSboA;
+                const uint64_t ah = smem_desc_kmajor(sAh + off, kTcLboA, kTcSboA);
+                const uint64_t al = smem_desc_kmajor(sAl + off, kTcLboA, kTcSboA);
+                const uint32_t d = tmem + (uint32_t)(t * kTcN);
+                mma_tf32(d, ah, bh, id, false);
+                mma_tf32(d, ah, bl, id, true);
+                mma_tf32(d, al, bh, id, true);
+            }
+            mma_commit(sBar);
+        }
+        const bool ok = mbar_wait(sBar, 0, kBulkWaitCycles);
+        if (!__syncthreads_and(ok)) {
+            // give up: latch the error, let the MMAs finish (bounded), free TMEM, store nothing
+            if (tid == 0) {
+                atomicOr(A.err, kErrTimeout);
+                mbar_wait(sBar, 0, kBulkWaitCycles);
+            }
+            tc_fence_before_sync();
+            __syncthreads();
+            if (warp == 0) {
+                tc_fence_after_sync();
+                tmem_dealloc(tmem, kTmemCols);
+            }
+            return;
+        }
+        tc_fence_after_sync();
+        // warp w reads lanes 32 (w % 4) .. of the tiles t = w / 4, w / 4 + TE / 4: row
+        // m = 32 (w % 4) + lane of tile t is element 2t + m / 64, point (m % 64) / 4, variable m % 4
+        const int quad = warp & 3;
+        for (int t = warp >> 2; t < TE / 2; t += TE / 4) {
+            float acc[8];
+            tmem_ld8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(t * kTcN), acc);
+            const int m = 32 * quad + lane;
+            const int tel = 2 * t + (m >> 6), j = (m & 63) >> 2, sv = m & 3;
+            if (tel < ne) {
+                T* dst = A.do_filter ? sTile + tel * elsz : uout + gbase + (size_t)tel * elsz;
+                const T* base = sK.use_base ? ubase + gbase + (size_t)tel * elsz : nullptr;
+                const AccTerm<T> X = acc_term<T>(A, gbase + (size_t)tel * elsz, sK);
+#pragma unroll
+                for (int k = 0; k < MC; ++k) {
+                    const int o = (j * M + k) * S + sv;
+                    const T uo = sTile[tel * elsz + o];
+                    T val = cb * uo + cc * acc[k];
+                    if (sK.use_base) val += ca * base[o];
+                    dst[o] = val;
+                    bad |= !finite_val(val);
+                    if (X.dst) {
+                        T w = X.b * uo + X.c * acc[k];
+                        if (X.src) w += X.a * X.src[o];
+                        X.dst[o] = w;
+                    }
+                }
+            }
+        }
+        tc_fence_before_sync();
+    } else if (active) {
         T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
         // the SSP base is read once, straight from global memory
         const T* base = sK.use_base ? ubase + gbase + (size_t)te * elsz : nullptr;
@@ -379,18 +515,27 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     }
     if (A.do_filter) {
         __syncthreads();
-        bad = detector_filter_store<T, NP, S>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tl, N1,
+        // TC: the G operand is free again (the MMAs have completed) and holds the modal scratch
+        T* mod = TC ? reinterpret_cast<T*>(sAh) : sG;
+        bad = detector_filter_store<T, NP, S>(A, sTile, mod, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tl, N1,
                                               active, true, e0 + te, true,
-                                              uout + gbase + (size_t)te * elsz, sK.det, M);
+                                              uout + gbase + (size_t)te * elsz, sK.det, M) || bad;
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
+    if constexpr (TC) {
+        __syncthreads();
+        if (warp == 0) {
+            tc_fence_after_sync();
+            tmem_dealloc(tmem, kTmemCols);
+        }
+    }
 }
 
-template <typename T, int N1, int MC, int QC>
+template <typename T, int N1, int MC, int QC, bool TC = false>
 cudaError_t launch2d_mq(const StageArgs& A, cudaStream_t st) {
     const int TE = A.TE;
-    const size_t smem = smem2d_bytes_t<T>(TE, N1, A.M, A.Q, 4);
-    auto kern = stage2d_kernel<T, N1, 4, MC, QC>;
+    const size_t smem = smem2d_bytes_t<T>(TE, N1, A.M, A.Q, 4, TC);
+    auto kern = stage2d_kernel<T, N1, 4, MC, QC, TC>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -420,16 +565,34 @@ cudaError_t launch2d_np(const frsg_config& cfg, const StageArgs& A, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
+// The FP32_TC form: P = 3, Q = 8, M <= 8 (modes compiled in), tiles of 4 or 8 elements
+// (whole 128-row MMA tiles, read back by warps covering all four TMEM lane quarters).
+cudaError_t launch2d_tc(const StageArgs& A, cudaStream_t st) {
+    if (A.Q != 8 || (A.TE != 4 && A.TE != 8)) return cudaErrorInvalidValue;
+    switch (A.M) {
+        case 1: return launch2d_mq<float, 4, 1, 8, true>(A, st);
+        case 2: return launch2d_mq<float, 4, 2, 8, true>(A, st);
+        case 3: return launch2d_mq<float, 4, 3, 8, true>(A, st);
+        case 4: return launch2d_mq<float, 4, 4, 8, true>(A, st);
+        case 5: return launch2d_mq<float, 4, 5, 8, true>(A, st);
+        case 6: return launch2d_mq<float, 4, 6, 8, true>(A, st);
+        case 7: return launch2d_mq<float, 4, 7, 8, true>(A, st);
+        case 8: return launch2d_mq<float, 4, 8, 8, true>(A, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
-size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S) {
-    return fp64 ? smem2d_bytes_t<double>(TE, n1, M, Q, S) : smem2d_bytes_t<float>(TE, n1, M, Q, S);
+size_t stage2d_smem_bytes(bool fp64, int TE, int n1, int M, int Q, int S, bool tc) {
+    return fp64 ? smem2d_bytes_t<double>(TE, n1, M, Q, S, false) : smem2d_bytes_t<float>(TE, n1, M, Q, S, tc);
 }
 
 cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A, cudaStream_t st) {
     if (cfg.equation != FRSG_EQ_EULER) return cudaErrorInvalidValue;
     StageArgs B = A;
     prepare_float_scalars(B);
+    if (cfg.precision == FRSG_FP32_TC) return cfg.P == 3 ? launch2d_tc(B, st) : cudaErrorInvalidValue;
     return fp64 ? launch2d_np<double>(cfg, B, st) : launch2d_np<float>(cfg, B, st);
 }
 

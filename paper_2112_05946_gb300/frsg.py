@@ -19,7 +19,7 @@ BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 EQUATION = {"advection": 0, "burgers": 1, "euler": 2}
 FILTER = {"none": 0, "exp": 1, "l2": 2, "lasso": 3}
 FLUX = {"llf": 0, "hll": 1}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_tc": 2}
 HOST, DEVICE = 0, 1
 
 

@@ -29,6 +29,11 @@ WINDOWS = [(0, 48, 40, 88), (56, 72, 0, 24), (232, 256, 104, 128)]
 # differ from the oracle by about 1e-5 of their deviation from the mean.
 TOL = {("fp64", "ic"): 1e-12, ("fp64", "perturbed"): 1e-12, ("fp32", "ic"): 1e-6, ("fp32", "perturbed"): 1e-5}
 COEF = {("fp64", "ic"): 1e-12, ("fp64", "perturbed"): 1e-12, ("fp32", "ic"): 2e-6, ("fp32", "perturbed"): 5e-5}
+# the FP32_TC form (projection on the tensor cores, 3xTF32) is held to the FP32 form's bounds
+for _k in list(TOL):
+    if _k[0] == "fp32":
+        TOL["fp32_tc", _k[1]] = TOL[_k]
+        COEF["fp32_tc", _k[1]] = COEF[_k]
 TOL_FP32_20 = 2e-5                           # FP32, 20 steps, 48 x 24 mesh, relative L2
 
 
@@ -87,10 +92,14 @@ def _run_gpu(case, precision, start):
 
 
 def _compare(case, precision, start, got, flags):
+    # each variable's largest |value| over the whole input state: inside one window a variable
+    # can be tiny (the y-momentum far from the vortex is about 1e-9), and rounding of the O(1)
+    # pressure terms in its residual is then large next to it but not next to the variable
+    inp = case["u0"] if start == "ic" else case["up"]
+    scale = np.max(np.abs(inp), axis=(0, 1, 2))
     for (full, ref, rec), box in zip(case["refs"][start], WINDOWS):
         g = got[full]
         assert rel_l2(g, ref) < TOL[precision, start], (box, rel_l2(g, ref))
-        scale = np.max(np.abs(ref), axis=(0, 1, 2))           # per variable
         worst = np.max(np.abs(g - ref) / scale)
         assert worst < COEF[precision, start], (box, worst)
         if precision == "fp64":
@@ -99,7 +108,7 @@ def _compare(case, precision, start, got, flags):
             assert np.mean(flags[:, full] != rec) < 0.01, box
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tc"])
 @pytest.mark.parametrize("start", ["ic", "perturbed"])
 def test_full_size_step_matches_oracle_windows(full_case, precision, start):
     got, flags, beta, tile = _run_gpu(full_case, precision, start)
@@ -113,14 +122,15 @@ def test_full_size_step_matches_oracle_windows(full_case, precision, start):
         assert any(rec.any() for _, _, rec in full_case["refs"]["perturbed"])
 
 
-def test_fp32_twenty_steps_against_whole_mesh_oracle():
+@pytest.mark.parametrize("precision", ["fp32", "fp32_tc"])
+def test_fp32_twenty_steps_against_whole_mesh_oracle(precision):
     wl = workloads.shock_vortex_2d(nx=48, ny=24)
     prob = oracle_problem(wl)
     tabs = prob.tabs()
     u0 = oracle_initial(prob, wl)
     dt = integrate.cfl_dt(prob, tabs, u0, 0.05)
     ref = integrate.run(prob, u0, dt, 20)
-    s = solver(wl, precision="fp32")
+    s = solver(wl, precision=precision)
     s.autotune()
     gpu_initial(s, wl)
     s.rk_step(dt, 20, graph=True)
