@@ -197,7 +197,8 @@ frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt);
 
 /* Events (cudaEvent_t, created by the caller) that fr_sg_stage records on the context's
  * stream: before_limiter before the limiter launch (§4.3), before_stage between it and the
- * stage kernel, after_stage after the stage kernel, so that a caller can time each kernel of
+ * stage kernel, after_stage after the stage kernel (before the float forms' cell-mean update,
+ * which follows it), so that a caller can time each kernel of
  * a stage with the same launches as fr_sg_rk_step (replayed decisions are not consumed while
  * events are set).  Any may be NULL; all NULL (the default) records nothing.  The events are
  * borrowed until they are replaced. */
@@ -212,6 +213,18 @@ frsg_status fr_sg_limit(frsg_ctx* ctx);
 /* Mean and variance over z at each solution point: mean = uhat_0, var = sum_{k>=1} uhat_k^2
  * (orthonormal basis, §2.1, Eq. 3).  mean, var: double [E][Np][S], HOST or DEVICE. */
 frsg_status fr_sg_moments(frsg_ctx* ctx, double* mean, double* var, int where);
+
+/* FP64 cell means of the gPC mean mode: mbar[e][s] = sum_j (w_j / 2^dim) uhat[e][j][0][s], the
+ * element mean over r (and s) and z (§4.3), host or device double [E][S].  In the float forms
+ * (FRSG_FP32, FRSG_FP32_TC) these means are carried in FP64 from step to step: every SSP-RK3
+ * stage moves them by the difference of the interface fluxes' mean-mode projections on the
+ * element's faces, one stored value per face (so that the sum over a periodic mesh is conserved
+ * to FP64 rounding: the filter keeps the mean, §4.1, Lambda_00 = 1, and the limiter scales about
+ * it, §4.3), and the float state's mean mode is shifted by a constant per element and variable
+ * to match them.  A state written directly (fr_sg_set_state, fr_sg_set_initial_nodal,
+ * fr_sg_advance, fr_sg_filter), an RK4 step or a batch step re-anchors them on the float state.
+ * In FRSG_FP64 they are computed from the state.  A HOST call synchronises. */
+frsg_status fr_sg_cell_means(frsg_ctx* ctx, double* mbar, int where);
 
 /* dt = cfl * h / lambda_max, lambda_max the largest flux-Jacobian spectral radius over
  * solution points and z-nodes of the current state, h the smallest element width.

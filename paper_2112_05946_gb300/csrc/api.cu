@@ -68,6 +68,12 @@ struct frsg_ctx {
     int graph_kernels = 0;
     // caller's events recorded around the kernels of fr_sg_stage (fr_sg_set_timing_events)
     cudaEvent_t ev_lim = nullptr, ev_stage = nullptr, ev_end = nullptr;
+    // FP64 cell means of mode 0 of the three state buffers [3][E][S] (float forms: accumulated
+    // stage by stage from the owned face values d_ff [3][faces][S]; double form: computed on demand)
+    double* d_mbar = nullptr;
+    float* d_ff = nullptr;
+    size_t nfaces = 0;
+    bool mean_valid = false;   // d_mbar holds the means of the buffers' current float states
 };
 
 namespace {
@@ -299,6 +305,62 @@ cudaError_t launch_stage(frsg_ctx* c, const StageArgs& A) {
     return frsg::launch_stage2d(c->cfg, c->fp64, A, c->stream);
 }
 
+// The FP64 cell means of the float forms (§4.1 / §4.3 keep the element mean; the SSP stages
+// move it by the interface fluxes only): used by every stage-wise and one-launch 1D layout and by
+// the 2D kernel.  RK4, the batch and direct writes of a state re-anchor the means from the state.
+bool mean64(const frsg_ctx* c) { return !c->fp64; }
+
+double* mbar_of(frsg_ctx* c, int buf) { return c->d_mbar + (size_t)buf * c->E * c->S; }
+
+// Anchor the means of all three buffers on their current states (outside any graph capture).
+cudaError_t anchor_means(frsg_ctx* c) {
+    if (!mean64(c) || c->mean_valid) return cudaSuccess;
+    void* bufs[3] = {c->d_u, c->d_u1, c->d_u2};
+    for (int b = 0; b < 3; ++b) {
+        cudaError_t e = frsg::launch_mean_init(false, bufs[b], mbar_of(c, b), c->E, c->Np, c->M, c->S,
+                                               c->d_tab + c->off.w, c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 1;
+    }
+    c->mean_valid = true;
+    return cudaSuccess;
+}
+
+frsg::MeanArgs mean_args(frsg_ctx* c) {
+    frsg::MeanArgs M{};
+    M.dtp = c->d_dt;
+    M.E = c->E;
+    M.nx = c->cfg.nx;
+    M.ny = c->cfg.dim == 2 ? c->cfg.ny : 1;
+    M.dim = c->cfg.dim;
+    M.Np = c->Np;
+    M.M = c->M;
+    M.S = c->S;
+    M.xper = c->cfg.bc[0] == FRSG_BC_PERIODIC;
+    M.yper = c->cfg.dim == 2 && c->cfg.bc[2] == FRSG_BC_PERIODIC;
+    M.invJx = 2.0 * c->cfg.nx / (c->cfg.x1 - c->cfg.x0);
+    M.invJy = c->cfg.dim == 2 ? 2.0 * c->cfg.ny / (c->cfg.y1 - c->cfg.y0) : 0.0;
+    M.wf = c->d_tabf + c->off.w;
+    return M;
+}
+
+// After stage s (buffers in = s, out = s + 1 mod 3): mbar_out = a mbar_0 + b mbar_in + c dt mean(L).
+cudaError_t launch_stage_mean(frsg_ctx* c, int s, double a, double b, double cc) {
+    frsg::MeanArgs M = mean_args(c);
+    void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
+    M.u = static_cast<float*>(bufs_out[s]);
+    M.mbar0 = mbar_of(c, 0);
+    M.mbar_in = mbar_of(c, s);
+    M.mbar_out = mbar_of(c, (s + 1) % 3);
+    M.F[0] = c->d_ff;
+    M.a[0] = a;
+    M.b[0] = b;
+    M.c[0] = cc;
+    M.nst = 1;
+    c->launches += 1;
+    return frsg::launch_mean64(M, c->stream);
+}
+
 cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
     LimitArgs L{};
     L.u = u;
@@ -323,7 +385,7 @@ cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
 // uout = a_s u^n + b_s (uin + dt L(uin)) followed by detector + filter.
 //   s = 0: u -> u1,  s = 1: u1 -> u2,  s = 2: u2 -> u (in place on u^n, element-local).
 cudaError_t issue_stage_ex(frsg_ctx* c, int s, double dt, uint8_t* flags_out, const uint8_t* replay_in,
-                           bool with_limiter = true) {
+                           bool with_limiter = true, bool with_mean = true) {
     const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
     void* bufs_in[3] = {c->d_u, c->d_u1, c->d_u2};
     void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
@@ -345,7 +407,10 @@ cudaError_t issue_stage_ex(frsg_ctx* c, int s, double dt, uint8_t* flags_out, co
     A.do_filter = filt ? 1 : 0;
     A.flags = flags_out;
     A.replay = replay_in;
-    return launch_stage(c, A);
+    A.fface = mean64(c) ? c->d_ff : nullptr;
+    cudaError_t e = launch_stage(c, A);
+    if (e == cudaSuccess && mean64(c) && with_mean) e = launch_stage_mean(c, s, ca[s], cb[s], cb[s]);
+    return e;
 }
 
 cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
@@ -374,7 +439,10 @@ cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
         A.replay = c->d_replay + (size_t)c->replay_pos * c->E;
         c->replay_pos += 1;
     }
-    return launch_stage(c, A);
+    A.fface = mean64(c) ? c->d_ff : nullptr;
+    cudaError_t e = launch_stage(c, A);
+    if (e == cudaSuccess && mean64(c)) e = launch_stage_mean(c, s, ca[s], cb[s], cb[s]);
+    return e;
 }
 
 cudaError_t set_dt(frsg_ctx* c, double dt) {
@@ -417,8 +485,27 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
                 A.replay = c->d_replay + (size_t)c->replay_pos * c->E;
                 c->replay_pos += 1;
             }
+            A.fface = mean64(c) ? c->d_ff + (size_t)s * c->nfaces * c->S : nullptr;
             A3[s] = A;
         }
+        // the step's mean update from the three stages' face values, after the launch
+        auto step_mean = [&]() -> cudaError_t {
+            if (!mean64(c)) return cudaSuccess;
+            frsg::MeanArgs M = mean_args(c);
+            M.u = static_cast<float*>(c->d_u);
+            M.mbar0 = mbar_of(c, 0);
+            M.mbar_in = nullptr;
+            M.mbar_out = mbar_of(c, 0);
+            for (int s = 0; s < 3; ++s) {
+                M.F[s] = c->d_ff + (size_t)s * c->nfaces * c->S;
+                M.a[s] = ca[s];
+                M.b[s] = cb[s];
+                M.c[s] = cb[s];
+            }
+            M.nst = 3;
+            c->launches += 1;
+            return frsg::launch_mean64(M, c->stream);
+        };
         c->launches += 1;
         if (c->wide == 3) {
             for (int s = 0; s < 3; ++s) {
@@ -438,9 +525,10 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
                 c->tok_te = 0;
                 c->tok_reset_next = false;
             }
-            return e;
+            return e == cudaSuccess ? step_mean() : e;
         }
-        return frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
+        cudaError_t e = frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
+        return e == cudaSuccess ? step_mean() : e;
     }
     for (int s = 0; s < 3; ++s) {
         cudaError_t e = issue_stage(c, s, dt, use_replay);
@@ -622,6 +710,12 @@ frsg_status fr_sg_init(const frsg_config* cfg, void* stream, frsg_ctx** out) {
     if ((e = cudaMalloc(&ctx->d_beta, 4 * sizeof(double) * ctx->E)) != cudaSuccess) return cleanup_fail(e, "beta");
     if ((e = cudaMalloc(&ctx->d_err, sizeof(unsigned))) != cudaSuccess) return cleanup_fail(e, "err");
     if ((e = cudaMalloc(&ctx->d_speed, sizeof(unsigned long long))) != cudaSuccess) return cleanup_fail(e, "speed");
+    ctx->nfaces = cfg->dim == 1 ? (size_t)ctx->E + 1
+                                : (size_t)cfg->ny * (cfg->nx + 1) + (size_t)(cfg->ny + 1) * cfg->nx;
+    if ((e = cudaMalloc(&ctx->d_mbar, 3 * sizeof(double) * ctx->E * ctx->S)) != cudaSuccess)
+        return cleanup_fail(e, "cell means");
+    if (!ctx->fp64 && (e = cudaMalloc(&ctx->d_ff, 3 * sizeof(float) * ctx->nfaces * ctx->S)) != cudaSuccess)
+        return cleanup_fail(e, "face values");
     e = cudaMemcpyAsync(ctx->d_tab, ctx->htab.data(), sizeof(double) * ctx->off.total, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_ghost, 0, sizeof(double) * 4 * ctx->M * ctx->S, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_u, 0, ctx->esz * nstate, ctx->stream);
@@ -668,6 +762,8 @@ void fr_sg_destroy(frsg_ctx* ctx) {
     cudaFree(ctx->d_beta);
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_speed);
+    cudaFree(ctx->d_mbar);
+    cudaFree(ctx->d_ff);
     cudaFree(ctx->d_replay);
     cudaFree(ctx->d_ckpt);
     cudaFree(ctx->d_log);
@@ -747,6 +843,7 @@ frsg_status fr_sg_set_boundary_nodal(frsg_ctx* ctx, int side, const double* g) {
 }
 
 frsg_status fr_sg_set_initial_nodal(frsg_ctx* ctx, const double* u0, int where) {
+    if (ctx) ctx->mean_valid = false;   // the state is written directly: re-anchor its FP64 means
     if (!ctx) return FRSG_E_INVAL;
     if (!u0) return fail(ctx, FRSG_E_INVAL, "null input");
     const size_t n = (size_t)ctx->E * ctx->Np * ctx->Q * ctx->S;
@@ -796,6 +893,7 @@ frsg_status fr_sg_project_transpose(frsg_ctx* ctx, const double* gbar, double* g
 }
 
 frsg_status fr_sg_set_state(frsg_ctx* ctx, const double* uhat, int where) {
+    if (ctx) ctx->mean_valid = false;   // the state is written directly: re-anchor its FP64 means
     if (!ctx) return FRSG_E_INVAL;
     if (!uhat) return fail(ctx, FRSG_E_INVAL, "null state");
     const size_t n = (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
@@ -849,9 +947,11 @@ frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt) {
 frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     if (!ctx) return FRSG_E_INVAL;
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
-    const int kernels_per_step = one_launch_step(ctx) ? 1 : 3 * (ctx->cfg.limiter ? 2 : 1);
+    const int kernels_per_step = one_launch_step(ctx) ? 1 + (mean64(ctx) ? 1 : 0)
+                                                      : 3 * (1 + (ctx->cfg.limiter ? 1 : 0) + (mean64(ctx) ? 1 : 0));
     if (nsteps == 0) return FRSG_OK;
     CK(set_dt(ctx, dt));
+    CK(anchor_means(ctx));
     for (int n = 0; n < nsteps; ++n) {
         const bool replaying = ctx->replay_pos < ctx->replay_rows;
         if (use_graph && !replaying && !one_launch_step(ctx)) {
@@ -912,6 +1012,7 @@ frsg_status fr_sg_advance(frsg_ctx* ctx, const double* uhat_in, double* uhat_out
         return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
     };
     // in: straight into the state (FP64) or through the double staging buffer (FP32)
+    ctx->mean_valid = false;
     if (ctx->fp64) {
         CK(cudaMemcpyAsync(ctx->d_u, uhat_in, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                            ctx->stream));
@@ -954,6 +1055,7 @@ frsg_status fr_sg_rk4_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) 
     }
     CK(set_dt(ctx, dt));
     const int kernels_per_step = 4 * (ctx->cfg.limiter ? 2 : 1);
+    ctx->mean_valid = false;   // RK4 carries no FP64 means: re-anchored before the next SSP step
     for (int n = 0; n < nsteps; ++n) {
         const bool replaying = ctx->replay_pos < ctx->replay_rows;
         if (use_graph && !replaying) {
@@ -999,6 +1101,7 @@ frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt) {
     if (stage < 0 || stage > 2 || !(dt > 0.0) || !std::isfinite(dt))
         return fail(ctx, FRSG_E_INVAL, "need stage in 0..2 and dt > 0");
     CK(set_dt(ctx, dt));
+    CK(anchor_means(ctx));
     if (!ctx->ev_lim && !ctx->ev_stage && !ctx->ev_end) {
         CK(issue_stage(ctx, stage, dt, true));
         return FRSG_OK;
@@ -1010,8 +1113,30 @@ frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt) {
         CK(launch_limiter(ctx, bufs_in[stage], ctx->d_beta + (size_t)stage * ctx->E));
     }
     if (ctx->ev_stage) CK(cudaEventRecord(ctx->ev_stage, ctx->stream));
-    CK(issue_stage_ex(ctx, stage, dt, ctx->d_flags + (size_t)stage * ctx->E, nullptr, false));
+    CK(issue_stage_ex(ctx, stage, dt, ctx->d_flags + (size_t)stage * ctx->E, nullptr, false, false));
     if (ctx->ev_end) CK(cudaEventRecord(ctx->ev_end, ctx->stream));
+    if (mean64(ctx)) {
+        const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+        const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+        CK(launch_stage_mean(ctx, stage, ca[stage], cb[stage], cb[stage]));
+    }
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_cell_means(frsg_ctx* ctx, double* mbar, int where) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!mbar || (where != FRSG_HOST && where != FRSG_DEVICE)) return fail(ctx, FRSG_E_INVAL, "need mbar and HOST/DEVICE");
+    if (mean64(ctx)) {
+        CK(anchor_means(ctx));
+    } else {
+        CK(frsg::launch_mean_init(true, ctx->d_u, mbar_of(ctx, 0), ctx->E, ctx->Np, ctx->M, ctx->S,
+                                  ctx->d_tab + ctx->off.w, ctx->stream));
+        ctx->launches += 1;
+    }
+    const size_t n = (size_t)ctx->E * ctx->S;
+    CK(cudaMemcpyAsync(mbar, mbar_of(ctx, 0), sizeof(double) * n,
+                       where == FRSG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream));
+    if (where == FRSG_HOST) CK(cudaStreamSynchronize(ctx->stream));
     return FRSG_OK;
 }
 
@@ -1024,6 +1149,7 @@ frsg_status fr_sg_set_timing_events(frsg_ctx* ctx, void* before_limiter, void* b
 }
 
 frsg_status fr_sg_filter(frsg_ctx* ctx, double dt) {
+    if (ctx) ctx->mean_valid = false;   // the state is written directly: re-anchor its FP64 means
     if (!ctx) return FRSG_E_INVAL;
     if (ctx->cfg.filter == FRSG_FILTER_NONE) return FRSG_OK;
     StageArgs A = base_args(ctx);
@@ -1293,6 +1419,7 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
     const int best_te = nfin ? cand[t1[win].second].second : ctx->TE;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->launches = 0;
+    ctx->mean_valid = false;   // the state was restored from the saved copy
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
     ctx->wide = best_w;
     ctx->TE = best_te;
@@ -1492,6 +1619,8 @@ static cudaError_t batch_issue_step(frsg_batch* b) {
 }
 
 frsg_status fr_sg_batch_rk_step(frsg_batch* b, const double* dt, int nsteps, int use_graph) {
+    if (b)
+        for (frsg_ctx* m : b->ctx) m->mean_valid = false;   // the batch carries no FP64 means
     if (!b || !dt || nsteps < 0) return FRSG_E_INVAL;
     const int n = (int)b->ctx.size();
     bool changed = false;

@@ -172,6 +172,33 @@ struct PairWalk {
     }
 };
 
+// Sum of v[s] over the n threads lt = 0..n-1 of group g (consecutive threads of the block,
+// groups aligned to n); every thread of the block calls it.  With shfl (n a power of two of
+// at most 32, the block whole warps) the sum is a butterfly of shuffles; otherwise the
+// participating threads' values go through scr (S * n floats per group) between two block
+// barriers.  Deterministic (fixed order); valid in lt == 0 of each group.
+template <int S>
+__device__ inline void group_sum(float (&v)[S], int lt, int n, int g, bool participate, bool shfl, float* scr) {
+    if (shfl) {
+        for (int o = n >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int s = 0; s < S; ++s) v[s] += __shfl_xor_sync(0xffffffffu, v[s], o);
+        return;
+    }
+    if (participate)
+#pragma unroll
+        for (int s = 0; s < S; ++s) scr[(g * S + s) * n + lt] = v[s];
+    __syncthreads();
+    if (participate && lt == 0)
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float a = 0.f;
+            for (int i = 0; i < n; ++i) a += scr[(g * S + s) * n + i];
+            v[s] = a;
+        }
+    __syncthreads();
+}
+
 // Second output of a stage, element-offset global pointers (see StageArgs::acc_out).
 template <typename T>
 struct AccTerm {

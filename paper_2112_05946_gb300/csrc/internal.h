@@ -70,6 +70,12 @@ struct StageArgs {
     int TE;                // elements per block
     int wide;              // 1D: one thread per (z-node, point) instead of per z-node
     long long wait_cycles; // bound of the one-launch step's neighbour wait in SM cycles (0: default)
+    // float forms: the mode-0 projection of the interface flux on the faces this element owns,
+    // F = sum_q wz_q f^I(z_q) (2D: also summed over the face's lines with weight w_line / 2),
+    // for the FP64 cell-mean accumulation; null = not written.  1D: [E + 1][S], face e the left
+    // face of element e (face E the right boundary).  2D: x faces [ny][nx + 1][S] (face ex the
+    // left face of element ex), then y faces [ny + 1][nx][S] (face ey the bottom face of row ey).
+    float* fface;
     // optional second output of the same residual (the RK4 weighted sum of the L's):
     // acc_out = acc_a*acc_in + acc_b*uin + acc_c*dt*L(uin), unfiltered; null = none
     void* acc_out;
@@ -177,5 +183,29 @@ cudaError_t launch_adjoint_stage1d(int P, int equation, const double* v, const d
 double detector_ratio(double s0, double kappa);
 
 cudaError_t launch_convert(const void* src, void* dst, size_t n, bool to_float, cudaStream_t st);
+
+// FP64 cell means of mode 0 for the float forms (§4.1: the filter keeps the mean, Lambda_00 = 1;
+// §4.3: the limiter scales about it).  nst stages of one step, stage s of coefficients
+// (a[s], b[s], c[s] dt): mbar_{s+1} = a[s] mbar_0 + b[s] mbar_s + c[s] dt mean(L_s), mean(L_s) the
+// flux difference of the owned face values F[s] (telescoping: each face has one value); then the
+// float state's mode 0 is shifted per element and variable so that its mean is mbar_nst.
+struct MeanArgs {
+    float* u;              // float state [E][Np][M][S] after the stage(s), shifted in place
+    const double* mbar0;   // [E][S] means of the step's input u^n (the SSP base)
+    const double* mbar_in; // [E][S] means of the stage input (nst == 1; null: mbar0)
+    double* mbar_out;      // [E][S] means of u (may be mbar0 or mbar_in: read before written)
+    const float* F[3];     // face values of each stage (layout of StageArgs::fface)
+    double a[3], b[3], c[3];
+    const double* dtp;     // device step size
+    int nst, E, nx, ny, dim, Np, M, S;
+    int xper, yper;
+    double invJx, invJy;
+    const float* wf;       // float table: w_j / 2^dim at the solution points
+};
+cudaError_t launch_mean64(const MeanArgs& A, cudaStream_t st);
+// mbar[e][s] = sum_j (w_j / 2^dim) u[e][j][0][s] in double from a float (fp64 = false) or double
+// state: the anchor after a write of the state, and the means of a double state
+cudaError_t launch_mean_init(bool fp64, const void* u, double* mbar, int E, int Np, int M, int S, const double* w,
+                             cudaStream_t st);
 
 }  // namespace frsg

@@ -39,7 +39,14 @@ __host__ __device__ inline size_t smem1d_bytes(int TE, int NP, int M, int Q, int
     n += (size_t)NP * NP + 4 * NP;                   // D, lm, lp, dhL, dhR
     n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;  // Vf, Vfinv, Lam, Top
     n += (size_t)2 * TE * Q;                         // Red
+    if (sizeof(T) == 4) n += (size_t)TE * S * Q;      // face-flux sums of the FP64 mean
     return n * sizeof(T) + (size_t)TE * sizeof(int) + 16;
+}
+
+// Whether the Q z-node threads of an element form shuffle groups (a power of two of at most 32,
+// the block whole warps).
+__device__ __forceinline__ bool q_groups_shuffle(int Q, int nthr) {
+    return (Q & (Q - 1)) == 0 && Q <= 32 && (nthr & 31) == 0 && (int)(blockDim.x * blockDim.y * blockDim.z) == nthr;
 }
 
 // One tile: elements e0 .. e0+ne-1 (ne <= A.TE) of one problem.  (tq, te): this thread's
@@ -75,6 +82,8 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     T* sLam = p; p += NP * M;
     T* sTop = p; p += NP;
     T* sRed = p; p += 2 * TE * Q;
+    float* sFs = reinterpret_cast<float*>(p);
+    if (sizeof(T) == 4) p += (size_t)TE * S * Q;
     int* sFlag = reinterpret_cast<int*>(p);
 
     // ---- one sweep of independent loads: tables, halo + tile, SSP base
@@ -195,6 +204,10 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
     __syncthreads();
 
     // ---- a3 + a6 + a7: flux, interface fluxes, total-flux derivative (nodal in z)
+    const bool mean64 = sizeof(T) == 4 && A.fface != nullptr;
+    float cF0[S], cF1[S];   // face-sum contributions wz_q f^I: left / right face
+#pragma unroll
+    for (int s = 0; s < S; ++s) cF0[s] = cF1[s] = 0.f;
     if (active) {
         T f[NP][S];
 #pragma unroll
@@ -215,6 +228,14 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
         }
         face_flux<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma, A.flux);
         face_flux<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma, A.flux);
+        if (mean64) {
+            const float wz = (float)sPz[tq];   // Pz[0][q] = wz_q (Phi_0 = 1)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                cF0[s] = wz * (float)fIL[s];
+                cF1[s] = wz * (float)fIR[s];
+            }
+        }
         const T invJ = sK.invJx;
 #pragma unroll
         for (int j = 0; j < NP; ++j)
@@ -225,6 +246,20 @@ __device__ __forceinline__ void stage1d_tile(const StageArgs& A, int e0, int ne,
                 for (int m = 0; m < NP; ++m) d += sD[j * NP + m] * f[m][s];
                 sG[(te * NP + j) * GR + s * Q + tq] = -invJ * d;
             }
+    }
+    if (mean64) {
+        // the element owns its left face; the last element of a non-periodic mesh also its right
+        const bool shfl = q_groups_shuffle(Q, nthr);
+        group_sum<S>(cF0, tq, Q, te, active, shfl, sFs);
+        if (active && tq == 0)
+#pragma unroll
+            for (int s = 0; s < S; ++s) A.fface[(size_t)(e0 + te) * S + s] = cF0[s];
+        if (!periodic && e0 + ne == E) {
+            group_sum<S>(cF1, tq, Q, te, active && te == ne - 1, shfl, sFs);
+            if (active && te == ne - 1 && tq == 0)
+#pragma unroll
+                for (int s = 0; s < S; ++s) A.fface[(size_t)E * S + s] = cF1[s];
+        }
     }
     __syncthreads();
 
@@ -264,6 +299,7 @@ __host__ __device__ inline size_t smem1d_wide_bytes(int TE, int NP, int M, int Q
     n += (size_t)NP * NP + 4 * NP;                   // D, lm, lp, dhL, dhR
     n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;  // Vf, Vfinv, Lam, Top
     n += (size_t)2 * TE * Q * NP;                    // Red
+    if (sizeof(T) == 4) n += (size_t)TE * S * Q;      // face-flux sums of the FP64 mean
     return n * sizeof(T) + (size_t)TE * sizeof(int) + 16;
 }
 
@@ -302,6 +338,8 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     T* sLam = p; p += NP * M;
     T* sTop = p; p += NP;
     T* sRed = p; p += 2 * TE * Q * NP;
+    float* sFs = reinterpret_cast<float*>(p);
+    if (sizeof(T) == 4) p += (size_t)TE * S * Q;
     int* sFlag = reinterpret_cast<int*>(p);
 
     // tables, then (after the wait) the state: asynchronous copies, in flight together
@@ -375,6 +413,10 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
     __syncthreads();
 
     // ---- a5 + a6 + a7: traces, interface fluxes, derivative row j (nodal in z)
+    const bool mean64 = sizeof(T) == 4 && A.fface != nullptr;
+    float cF0[S], cF1[S];   // face-sum contributions wz_q f^I (point-0 threads): left / right face
+#pragma unroll
+    for (int s = 0; s < S; ++s) cF0[s] = cF1[s] = 0.f;
     if (active) {
         auto trace = [&](const T* src, const T* w, int s) {
             T acc = T(0);
@@ -423,6 +465,14 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
         }
         face_flux<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma, A.flux);
         face_flux<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma, A.flux);
+        if (mean64 && tj == 0) {
+            const float wz = (float)sPz[tq];   // Pz[0][q] = wz_q (Phi_0 = 1)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                cF0[s] = wz * (float)fIL[s];
+                cF1[s] = wz * (float)fIR[s];
+            }
+        }
         const T invJ = sK.invJx;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -430,6 +480,20 @@ __global__ void __launch_bounds__(256) stage1d_wide_kernel(const StageArgs A) {
 #pragma unroll
             for (int m = 0; m < NP; ++m) d += sD[tj * NP + m] * fown[(m * S + s) * Q + tq];
             sG[(te * NP + tj) * GR + s * Q + tq] = -invJ * d;
+        }
+    }
+    if (mean64) {
+        // the element owns its left face; the last element of a non-periodic mesh also its right
+        const bool shfl = q_groups_shuffle(Q, nthr);
+        group_sum<S>(cF0, tq, Q, te, active && tj == 0, shfl, sFs);
+        if (active && tj == 0 && tq == 0)
+#pragma unroll
+            for (int s = 0; s < S; ++s) A.fface[(size_t)(e0 + te) * S + s] = cF0[s];
+        if (!periodic && e0 + ne == E) {
+            group_sum<S>(cF1, tq, Q, te, active && tj == 0 && te == ne - 1, shfl, sFs);
+            if (active && tj == 0 && te == ne - 1 && tq == 0)
+#pragma unroll
+                for (int s = 0; s < S; ++s) A.fface[(size_t)E * S + s] = cF1[s];
         }
     }
     __syncthreads();

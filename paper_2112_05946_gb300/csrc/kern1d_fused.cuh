@@ -42,6 +42,7 @@ __host__ __device__ inline size_t smem1d_fused_bytes(int TE, int NP, int M, int 
     n += (size_t)NP * NP + 4 * NP;                    // D, lm, lp, dhL, dhR
     n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;   // Vf, Vfinv, Lam, Top
     n += 2 * W * Q * NP;                              // Red
+    if (sizeof(T) == 4) n += W * S * Q;               // face-flux sums of the FP64 mean
     return n * sizeof(T) + W * sizeof(int) + 16;
 }
 
@@ -104,6 +105,8 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
     T* sLam = p; p += NP * M;
     T* sTop = p; p += NP;
     T* sRed = p; p += 2 * W * Q * NP;
+    float* sFs = reinterpret_cast<float*>(p);
+    if (sizeof(T) == 4) p += (size_t)W * S * Q;
     int* sFlag = reinterpret_cast<int*>(p);
 
     // slot -> element of the problem; -1 beyond a physical boundary or past the slots the
@@ -258,6 +261,10 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         __syncthreads();
 
         // ---- a5 + a6 + a7: traces, interface fluxes, derivative row j (nodal in z)
+        const bool mean64 = sizeof(T) == 4 && A.fface != nullptr;
+        float cF0[S], cF1[S];   // face-sum contributions wz_q f^I (point-0 threads): left / right face
+#pragma unroll
+        for (int s = 0; s < S; ++s) cF0[s] = cF1[s] = 0.f;
         if (out_valid) {
             auto trace = [&](const T* src, const T(&w)[NP], int s) {
                 T acc = T(0);
@@ -305,12 +312,37 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
             }
             face_flux<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma, A.flux);
             face_flux<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma, A.flux);
+            if (mean64 && tj == 0) {
+                const float wz = (float)sPz[tq];   // Pz[0][q] = wz_q (Phi_0 = 1)
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    cF0[s] = wz * (float)fIL[s];
+                    cF1[s] = wz * (float)fIR[s];
+                }
+            }
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 T d = (fIL[s] - fDL[s]) * rdhL + (fIR[s] - fDR[s]) * rdhR;
 #pragma unroll
                 for (int m = 0; m < NP; ++m) d += rD[m] * fown[(m * S + s) * Q + tq];
                 sG[(r * NP + tj) * GR + s * Q + tq] = -invJ * d;
+            }
+        }
+        if (mean64) {
+            // an owned element writes its left face of this stage; the last element of a
+            // non-periodic mesh also its right face
+            const bool shfl = (Q & (Q - 1)) == 0 && Q <= 32 && (nthr & 31) == 0;
+            const bool mine = owned && out_valid && tj == 0;
+            group_sum<S>(cF0, tq, Q, r, mine, shfl, sFs);
+            if (mine && tq == 0)
+#pragma unroll
+                for (int s = 0; s < S; ++s) A.fface[(size_t)g_r * S + s] = cF0[s];
+            if (!periodic && e0 + ne == E) {
+                const bool last = mine && g_r == E - 1;
+                group_sum<S>(cF1, tq, Q, r, last, shfl, sFs);
+                if (last && tq == 0)
+#pragma unroll
+                    for (int s = 0; s < S; ++s) A.fface[(size_t)E * S + s] = cF1[s];
             }
         }
         __syncthreads();

@@ -58,6 +58,9 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
     n += (size_t)n1 * n1 + 4 * n1;          // D, lm, lp, dhL, dhR
     n += 2 * (size_t)Np * Np + (size_t)Np * M + Np;   // Vf, Vfinv, Lam, Top
     n += (size_t)2 * TE * n1 * Q;           // Red
+    const int nel = Q * n1;
+    if (sizeof(T) == 4 && !((nel & (nel - 1)) == 0 && nel <= 32 && (nel * TE) % 32 == 0))
+        n += (size_t)TE * S * nel;          // face-flux sums of the FP64 mean (no shuffle path)
     return n;
 }
 
@@ -134,6 +137,11 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     T* sLam = p; p += NP * M;
     T* sTop = p; p += NP;
     T* sRed = p; p += 2 * TE * N1 * Q;
+    // the FP64 mean of the float forms: face values F of the owned faces (see StageArgs::fface)
+    const int nel = Q * N1, lt = tl * Q + tq;
+    const bool gshfl = (nel & (nel - 1)) == 0 && nel <= 32 && (nthr & 31) == 0;
+    float* sFs = reinterpret_cast<float*>(p);
+    if (sizeof(T) == 4 && !gshfl) p += (size_t)TE * S * nel;
     int* sFlag = reinterpret_cast<int*>(p);
     // TC: the MMA completion barrier (16-byte aligned after the flags) and the TMEM address
     uint64_t* sBar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(sFlag + TE) + 15) & ~(uintptr_t)15);
@@ -241,6 +249,17 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
 
     const bool active = te < ne;
     const int ex = ex0 + te;
+    const bool mean64 = sizeof(T) == 4 && A.fface != nullptr;
+    float fw = 0.f;   // w_line / 2 * wz_q: the face sum's weight of this thread's (line, z-node)
+    if (mean64) {
+        const T* w2 = table_block<T>(A) + A.off.w;   // w_a w_b / 4; a line's w_l / 2 is a row sum
+        float wl = 0.f;
+#pragma unroll
+        for (int a = 0; a < N1; ++a) wl += (float)w2[tl * N1 + a];
+        fw = wl * (float)sPz[tq];   // Pz[0][q] = wz_q (Phi_0 = 1)
+    }
+    float* Fx = A.fface;
+    float* Fy = A.fface ? A.fface + (size_t)ny * (nx + 1) * S : nullptr;
     // the S variables of one (point, z-node) sit together, consecutive z-nodes in consecutive
     // vectors: one vector access per thread, conflict-free across the lines of a warp
     auto un_at = [&](int pt) { return sUn + ((size_t)(te * NP + pt) * Q + tq) * S; };
@@ -343,6 +362,9 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     __syncthreads();
 
     // ---- x-sweep on row b = tl
+    float cF0[S], cF1[S];   // face-sum contributions: left / right (x), bottom / top (y)
+#pragma unroll
+    for (int s = 0; s < S; ++s) cF0[s] = cF1[s] = 0.f;
     if (active) {
         const int b = tl;
         T f[N1][S];
@@ -368,6 +390,12 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
         ldv<T, S>(tx_at(te + 2, 0, b), nR);
         face_flux<T, EQ, S, 2, 0>(nL, tL, fIL, adv, gamma, A.flux);
         face_flux<T, EQ, S, 2, 0>(tR, nR, fIR, adv, gamma, A.flux);
+        if (mean64)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                cF0[s] = fw * (float)fIL[s];
+                cF1[s] = fw * (float)fIR[s];
+            }
         const T invJ = sK.invJx;
 #pragma unroll
         for (int a = 0; a < N1; ++a)
@@ -379,6 +407,21 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
                 if constexpr (TC) *g_at(sAh, (te * NP + b * N1 + a) * S + s, tq) = -invJ * d;
                 else sG[(te * NP + b * N1 + a) * GR + s * Q + tq] = -invJ * d;
             }
+    }
+    if (mean64) {
+        // the element owns its left face; the element at a non-periodic right end also its right
+        group_sum<S>(cF0, lt, nel, te, active, gshfl, sFs);
+        if (active && lt == 0)
+#pragma unroll
+            for (int s = 0; s < S; ++s) Fx[((size_t)ey * (nx + 1) + ex) * S + s] = cF0[s];
+        if (!xper && ex0 + ne == nx) {
+            group_sum<S>(cF1, lt, nel, te, te == ne - 1, gshfl, sFs);
+            if (te == ne - 1 && lt == 0)
+#pragma unroll
+                for (int s = 0; s < S; ++s) Fx[((size_t)ey * (nx + 1) + nx) * S + s] = cF1[s];
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) cF0[s] = cF1[s] = 0.f;
     }
     __syncthreads();
 
@@ -413,6 +456,12 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             ghost_from_interior<T, EQ, S, 1>(A.bc[3], tT, ytop);
         face_flux<T, EQ, S, 2, 1>(ybot, tB, gIB, adv, gamma, A.flux);
         face_flux<T, EQ, S, 2, 1>(tT, ytop, gIT, adv, gamma, A.flux);
+        if (mean64)
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                cF0[s] = fw * (float)gIB[s];
+                cF1[s] = fw * (float)gIT[s];
+            }
         const T invJ = sK.invJy;
 #pragma unroll
         for (int b = 0; b < N1; ++b)
@@ -432,6 +481,19 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
                     sG[(te * NP + b * N1 + a) * GR + s * Q + tq] -= invJ * d;
                 }
             }
+    }
+    if (mean64) {
+        // the element owns its bottom face; the top row of a non-periodic mesh also its top face
+        group_sum<S>(cF0, lt, nel, te, active, gshfl, sFs);
+        if (active && lt == 0)
+#pragma unroll
+            for (int s = 0; s < S; ++s) Fy[((size_t)ey * nx + ex) * S + s] = cF0[s];
+        if (!yper && ey == ny - 1) {
+            group_sum<S>(cF1, lt, nel, te, active, gshfl, sFs);
+            if (active && lt == 0)
+#pragma unroll
+                for (int s = 0; s < S; ++s) Fy[((size_t)ny * nx + ex) * S + s] = cF1[s];
+        }
     }
     if constexpr (TC) fence_async_shared();   // the operand stores, to the tensor cores
     __syncthreads();

@@ -504,6 +504,96 @@ __global__ void convert_kernel(const void* src, void* dst, size_t n, int to_floa
     }
 }
 
+// One warp per element: lane l holds the mode-0 values of the (point, variable) pairs l and l + 32
+// (consecutive lanes, consecutive variables: coalesced), lane s < S the FP64 data of variable s;
+// every load is issued before any arithmetic, so a warp pays one memory latency.  The weighted
+// sums per variable come from shuffles; lane s forms the FP64 mean update of MeanArgs (the face
+// difference of each stage telescopes over the mesh: every face has one stored value) and the
+// shift of the float mode 0 to it, which every lane applies.  S <= 4, Np * S <= 64.
+__global__ void __launch_bounds__(256) mean64_kernel(const MeanArgs A) {
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int S = A.S, NS = A.Np * A.S;
+    const bool live = e < A.E;
+    float* ue = A.u + (size_t)(live ? e : 0) * A.Np * A.M * S;
+    const int p0 = lane, p1 = lane + 32;
+    const bool h0 = live && p0 < NS, h1 = live && p1 < NS;
+    const int j0 = p0 / S, s0 = p0 - j0 * S, j1 = p1 / S, s1 = p1 - j1 * S;
+    const float w0 = h0 ? A.wf[j0] : 0.f, w1 = h1 ? A.wf[j1] : 0.f;
+    const bool own = live && lane < S;    // this lane updates variable s = lane
+    size_t xl = 0, xr = 0, yb = 0, yt = 0, yoff = 0;
+    if (own) {
+        if (A.dim == 1) {
+            xl = (size_t)e;
+            xr = e == A.E - 1 ? (A.xper ? 0 : (size_t)A.E) : (size_t)e + 1;
+        } else {
+            const int ex = e % A.nx, ey = e / A.nx;
+            xl = (size_t)ey * (A.nx + 1) + ex;
+            xr = (size_t)ey * (A.nx + 1) + (ex == A.nx - 1 ? (A.xper ? 0 : A.nx) : ex + 1);
+            yb = (size_t)ey * A.nx + ex;
+            yt = (size_t)(ey == A.ny - 1 ? (A.yper ? 0 : A.ny) : ey + 1) * A.nx + ex;
+            yoff = (size_t)A.ny * (A.nx + 1) * S;
+        }
+    }
+    pdl_wait();
+    // ---- loads
+    const float v0 = h0 ? ue[(size_t)j0 * A.M * S + s0] : 0.f;
+    const float v1 = h1 ? ue[(size_t)j1 * A.M * S + s1] : 0.f;
+    double m0 = 0.0, min = 0.0, dt = 0.0;
+    float fx[3][2] = {}, fy[3][2] = {};
+    if (own) {
+        const size_t idx = (size_t)e * S + lane;
+        m0 = A.mbar0[idx];
+        min = A.mbar_in ? A.mbar_in[idx] : m0;
+        dt = *A.dtp;
+        for (int st = 0; st < A.nst; ++st) {
+            fx[st][0] = A.F[st][xl * S + lane];
+            fx[st][1] = A.F[st][xr * S + lane];
+            if (A.dim == 2) {
+                fy[st][0] = A.F[st][yoff + yb * S + lane];
+                fy[st][1] = A.F[st][yoff + yt * S + lane];
+            }
+        }
+    }
+    // ---- the float element mean of each variable
+    float mf = 0.f;   // lane s < S: variable s's
+    for (int s = 0; s < S; ++s) {
+        float x = (h0 && s0 == s ? w0 * v0 : 0.f) + (h1 && s1 == s ? w1 * v1 : 0.f);
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == s) mf = x;
+    }
+    // ---- FP64 update: mean of the residual -(1/J) (F_right - F_left) / 2 per direction
+    float delta = 0.f;
+    if (own) {
+        double m = min;
+        for (int st = 0; st < A.nst; ++st) {
+            double lm = -0.5 * A.invJx * ((double)fx[st][1] - (double)fx[st][0]);
+            if (A.dim == 2) lm -= 0.5 * A.invJy * ((double)fy[st][1] - (double)fy[st][0]);
+            m = A.a[st] * m0 + A.b[st] * m + A.c[st] * dt * lm;
+        }
+        delta = (float)(m - (double)mf);
+        A.mbar_out[(size_t)e * S + lane] = m;
+    }
+    // every lane shifts its pairs by its variable's delta
+    const float d0 = __shfl_sync(0xffffffffu, delta, s0 < S ? s0 : 0);
+    const float d1 = __shfl_sync(0xffffffffu, delta, s1 < S ? s1 : 0);
+    if (h0) ue[(size_t)j0 * A.M * S + s0] = v0 + d0;
+    if (h1) ue[(size_t)j1 * A.M * S + s1] = v1 + d1;
+}
+
+template <typename T>
+__global__ void mean_init_kernel(const T* u, double* mbar, int E, int Np, int M, int S, const double* w) {
+    const size_t n = (size_t)E * S;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = i / S;
+        const int s = (int)(i - e * S);
+        double acc = 0.0;
+        for (int j = 0; j < Np; ++j) acc += w[j] * (double)u[(e * Np + j) * M * S + s];
+        mbar[i] = acc;
+    }
+}
+
 int grid_for(size_t n, int threads) {
     size_t g = (n + threads - 1) / threads;
     if (g > 152 * 32) g = 152 * 32;
@@ -616,6 +706,20 @@ cudaError_t launch_max_speed(bool fp64, const void* uhat, int E, int Np, int M, 
                              unsigned long long* out_bits, cudaStream_t st) {
     return fp64 ? max_speed_typed<double>(uhat, E, Np, M, Q, S, dim, equation, adv, gamma, tab + off.VzT, out_bits, st)
                 : max_speed_typed<float>(uhat, E, Np, M, Q, S, dim, equation, adv, gamma, tab + off.VzT, out_bits, st);
+}
+
+cudaError_t launch_mean64(const MeanArgs& A, cudaStream_t st) {
+    if (A.S > 4 || A.Np * A.S > 64) return cudaErrorInvalidValue;
+    const int warps = A.E;   // one warp per element, eight per block
+    return launch_pdl(mean64_kernel, dim3((warps + 7) / 8), dim3(256), 0, st, A);
+}
+
+cudaError_t launch_mean_init(bool fp64, const void* u, double* mbar, int E, int Np, int M, int S, const double* w,
+                             cudaStream_t st) {
+    const int g = grid_for((size_t)E * S, 256);
+    if (fp64) mean_init_kernel<double><<<g, 256, 0, st>>>(static_cast<const double*>(u), mbar, E, Np, M, S, w);
+    else mean_init_kernel<float><<<g, 256, 0, st>>>(static_cast<const float*>(u), mbar, E, Np, M, S, w);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const void* src, void* dst, size_t n, bool to_float, cudaStream_t st) {

@@ -90,6 +90,7 @@ _SIGNATURES = [
     ("fr_sg_set_variant", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_test_fused_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
     ("fr_sg_set_timing_events", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fr_sg_cell_means", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("fr_sg_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     ("fr_sg_forward_record", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
@@ -363,6 +364,12 @@ class Solver:
             where = HOST if isinstance(mean, np.ndarray) else DEVICE
             self._ck(self.lib.fr_sg_moments(self.h, _ptr(mean), _ptr(var), where), "moments")
         return mean, var
+
+    def cell_means(self):
+        """fr_sg_cell_means: FP64 element means of the gPC mean mode, [E, S] (host)."""
+        out = np.zeros((self.E, self.S))
+        self._ck(self.lib.fr_sg_cell_means(self.h, _ptr(out), HOST), "cell_means")
+        return out
 
     def cfl_dt(self, cfl):
         dt = ctypes.c_double()

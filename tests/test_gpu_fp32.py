@@ -3,7 +3,7 @@
 The FP32 form stores and computes the state in float; the limiter, the time-step
 reduction and the moments run in double.  Stated bounds (relative L2 against the FP64
 oracle): residual 1e-5; the Burgers workload over 50 steps 1e-5; the Sod tube over 20
-steps 1e-3 (float rounding near the discontinuity is amplified by the shock dynamics).
+steps 1e-5 (measured 2.4e-6 with the element means carried in FP64; 1e-3 before).
 """
 import numpy as np
 import pytest
@@ -77,4 +77,4 @@ def test_sod_fp32_steps():
         s.set_replay(np.array(rec, dtype=np.uint8))
         s.rk_step(dt, 1, graph=False)
     s.check()
-    assert rel_l2(s.get_state(), u) < 1e-3
+    assert rel_l2(s.get_state(), u) < 1e-5
