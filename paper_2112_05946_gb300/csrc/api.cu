@@ -74,6 +74,11 @@ struct frsg_ctx {
     float* d_ff = nullptr;
     size_t nfaces = 0;
     bool mean_valid = false;   // d_mbar holds the means of the buffers' current float states
+    // the float state's mean mode is shifted onto the FP64 means in the last stage of every
+    // kMeanShiftEvery-th SSP step (between shifts it drifts from them by float rounding only)
+    long long mean_step = 0;   // SSP steps issued so far
+    bool shift_now = false;    // the step being issued shifts
+    cudaGraphExec_t graph_shift = nullptr;   // the step graph with the shift
 };
 
 namespace {
@@ -310,6 +315,15 @@ cudaError_t launch_stage(frsg_ctx* c, const StageArgs& A) {
 // the 2D kernel.  RK4, the batch and direct writes of a state re-anchor the means from the state.
 bool mean64(const frsg_ctx* c) { return !c->fp64; }
 
+constexpr int kMeanShiftEvery = 8;
+
+// Whether the next SSP step shifts the float means; advances the step count.
+bool next_step_shifts(frsg_ctx* c) {
+    const bool sh = c->mean_step % kMeanShiftEvery == kMeanShiftEvery - 1;
+    c->mean_step += 1;
+    return sh;
+}
+
 double* mbar_of(frsg_ctx* c, int buf) { return c->d_mbar + (size_t)buf * c->E * c->S; }
 
 // Anchor the means of all three buffers on their current states (outside any graph capture).
@@ -323,6 +337,7 @@ cudaError_t anchor_means(frsg_ctx* c) {
         c->launches += 1;
     }
     c->mean_valid = true;
+    c->mean_step = 0;   // a state written directly starts the shift count afresh
     return cudaSuccess;
 }
 
@@ -344,7 +359,8 @@ frsg::MeanArgs mean_args(frsg_ctx* c) {
     return M;
 }
 
-// After stage s (buffers in = s, out = s + 1 mod 3): mbar_out = a mbar_0 + b mbar_in + c dt mean(L).
+// After stage s (buffers in = s, out = s + 1 mod 3): mbar_out = a mbar_0 + b mbar_in + c dt mean(L);
+// in the last stage of a shifting step the output state's mean mode also moves onto mbar_out.
 cudaError_t launch_stage_mean(frsg_ctx* c, int s, double a, double b, double cc) {
     frsg::MeanArgs M = mean_args(c);
     void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
@@ -357,6 +373,7 @@ cudaError_t launch_stage_mean(frsg_ctx* c, int s, double a, double b, double cc)
     M.b[0] = b;
     M.c[0] = cc;
     M.nst = 1;
+    M.shift = s == 2 && c->shift_now;
     c->launches += 1;
     return frsg::launch_mean64(M, c->stream);
 }
@@ -503,6 +520,7 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
                 M.c[s] = cb[s];
             }
             M.nst = 3;
+            M.shift = c->shift_now;
             c->launches += 1;
             return frsg::launch_mean64(M, c->stream);
         };
@@ -541,8 +559,10 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
 void drop_graphs(frsg_ctx* c) {
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph_rk4) cudaGraphExecDestroy(c->graph_rk4);
+    if (c->graph_shift) cudaGraphExecDestroy(c->graph_shift);
     c->graph_exec = nullptr;
     c->graph_rk4 = nullptr;
+    c->graph_shift = nullptr;
 }
 
 // Stage s of a classical RK4 step (§5.1 setup table).  Buffers: u = u^n (limited in
@@ -747,6 +767,7 @@ void fr_sg_destroy(frsg_ctx* ctx) {
     if (!ctx) return;
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->graph_rk4) cudaGraphExecDestroy(ctx->graph_rk4);
+    if (ctx->graph_shift) cudaGraphExecDestroy(ctx->graph_shift);
     cudaFree(ctx->d_u3);
     cudaFree(ctx->d_tab);
     cudaFree(ctx->d_tabf);
@@ -954,8 +975,11 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     CK(anchor_means(ctx));
     for (int n = 0; n < nsteps; ++n) {
         const bool replaying = ctx->replay_pos < ctx->replay_rows;
+        ctx->shift_now = mean64(ctx) && next_step_shifts(ctx);
+        // two cached graphs: without and with the shift of the float means
+        cudaGraphExec_t& gx = ctx->shift_now ? ctx->graph_shift : ctx->graph_exec;
         if (use_graph && !replaying && !one_launch_step(ctx)) {
-            if (!ctx->graph_exec) {
+            if (!gx) {
                 cudaStream_t cap = ctx->stream;
                 bool own = false;
                 if (cap == nullptr) {
@@ -974,7 +998,7 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
                 }
                 ctx->launches = before;
                 ctx->stream = saved;
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, graph, 0);
                 if (graph) cudaGraphDestroy(graph);
                 if (own) {
                     cudaStreamSynchronize(cap);
@@ -983,7 +1007,7 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
                 ctx->graph_kernels = kernels_per_step;
             }
-            CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+            CK(cudaGraphLaunch(gx, ctx->stream));
             ctx->launches += ctx->graph_kernels;
         } else {
             CK(issue_step(ctx, dt, true));
@@ -1102,6 +1126,8 @@ frsg_status fr_sg_stage(frsg_ctx* ctx, int stage, double dt) {
         return fail(ctx, FRSG_E_INVAL, "need stage in 0..2 and dt > 0");
     CK(set_dt(ctx, dt));
     CK(anchor_means(ctx));
+    // the SSP step count advances with stage 0; stage 2 shifts when that step does
+    if (stage == 0) ctx->shift_now = mean64(ctx) && next_step_shifts(ctx);
     if (!ctx->ev_lim && !ctx->ev_stage && !ctx->ev_end) {
         CK(issue_stage(ctx, stage, dt, true));
         return FRSG_OK;

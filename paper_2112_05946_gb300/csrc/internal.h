@@ -140,6 +140,10 @@ cudaError_t launch_stage2d(const frsg_config& cfg, bool fp64, const StageArgs& A
 cudaError_t launch_stage1d_batched(bool fp64, int equation, const StageArgs* args, const int4* tiles, int ntiles,
                                    size_t smem, int grid, cudaStream_t st);
 int stage1d_batched_blocks_per_sm(bool fp64, int equation, size_t smem);
+// The batched launch of a recorded run (double states): problem pointers moved by seg_j steps of
+// three state slots, decision rows (flags, replay) by log_n steps of three rows.
+cudaError_t launch_stage1d_batched_rec(int equation, const StageArgs* args, const int4* tiles, int ntiles,
+                                       size_t smem, int grid, int seg_j, int log_n, cudaStream_t st);
 // One SSP-RK3 step (stage arguments A3[0..2]) as one cooperative launch with grid barriers;
 // bar: two zeroed device words (arrival count, generation).
 cudaError_t launch_step1d(const frsg_config& cfg, bool fp64, const StageArgs* A3, unsigned* bar, int* grid,
@@ -179,6 +183,45 @@ cudaError_t launch_adjoint_stage1d(int P, int equation, const double* v, const d
                                    const double* tab, TabOff off, int E, int M, int Q, int TE, double invJx,
                                    double adv, cudaStream_t st);
 
+// Batched discrete adjoint (kadjoint_batch.cu): many 1D scalar double problems of a batch,
+// every member and every cotangent set in one persistent launch per reverse stage.
+struct AdjMember {
+    const double* tab;
+    TabOff off;
+    int E, M, Q, Np;
+    int filter;            // FRSG_FILTER_NONE: no transpose; else the recorded decisions apply F^T
+    double invJx, adv, dt, alpha_dt;
+    const double* u;       // the member's state (checkpointed by the record; the QoIs' input)
+    double* ckpt;          // [checkpoints][ns]
+    double* seg;           // [3 k][ns]: stage inputs of one recomputed segment
+    const uint8_t* log;    // [steps][3][E]: filter decisions of every stage
+    double* work;          // role r of cotangent set c at work + (4 c + r) * wstride
+    long long ns;          // E * Np * M
+};
+// One reverse stage: v = seg slot `slot`, decisions row `row`; roles of the work arena:
+// mu (the stage output's cotangent), lv (receives b y + c dt L'(v)^T y; -1: none), lb (the SSP
+// base's cotangent: set to a y when base_init, else a y added; with accumulate, lv's value is
+// added to lb instead of stored), y = F^T mu.
+struct AdjStage {
+    int slot, row, mu, lv, lb;
+    double a, b, c;
+    int base_init, accumulate;
+    long long wstride;     // doubles between roles: the sum of ns over the members
+};
+cudaError_t launch_adjoint_batched(int equation, const AdjMember* mem, const int4* tiles, int ntiles, int nset,
+                                   const AdjStage& S, size_t smem, int grid, cudaStream_t st);
+size_t adjoint_batched_smem(int Np, int M, int Q, int rows);
+int adjoint_batched_blocks_per_sm(int equation, size_t smem);
+// Copies per member (and set): what = 0 checkpoint idx <- u; 1 seg slot 0 <- checkpoint idx;
+// 2 role 0 of set c <- ptrs[c n + i]; 3 ptrs[c n + i] <- role idx of set c.
+cudaError_t launch_adjoint_copy(const AdjMember* mem, int n, int what, int idx, double* const* ptrs, int nset,
+                                long long wstride, long long max_ns, cudaStream_t st);
+// Per member: q[2 i] = E[int u dx], q[2 i + 1] = Var[int u dx] over z (orthonormal gPC: the mean is
+// mode 0, the variance the sum of the squares of the other modes) and their gradients with
+// respect to the state, written to dmean[i] / dvar[i] (either table may be null).
+cudaError_t launch_integral_moments(const AdjMember* mem, int n, double* q, double* const* dmean,
+                                   double* const* dvar, cudaStream_t st);
+
 // 10^(s0 - (2 kappa / pi) asin(0.98)): the S_e at which theta of §4.2, Eq. 47 equals 0.99.
 double detector_ratio(double s0, double kappa);
 
@@ -199,6 +242,8 @@ struct MeanArgs {
     const double* dtp;     // device step size
     int nst, E, nx, ny, dim, Np, M, S;
     int xper, yper;
+    int shift;             // 1: also shift the float mode 0 of u to the new means (one pass over
+                           // the state's mean mode); 0: update the FP64 means only
     double invJx, invJy;
     const float* wf;       // float table: w_j / 2^dim at the solution points
 };

@@ -504,82 +504,69 @@ __global__ void convert_kernel(const void* src, void* dst, size_t n, int to_floa
     }
 }
 
-// One warp per element: lane l holds the mode-0 values of the (point, variable) pairs l and l + 32
-// (consecutive lanes, consecutive variables: coalesced), lane s < S the FP64 data of variable s;
-// every load is issued before any arithmetic, so a warp pays one memory latency.  The weighted
-// sums per variable come from shuffles; lane s forms the FP64 mean update of MeanArgs (the face
-// difference of each stage telescopes over the mesh: every face has one stored value) and the
-// shift of the float mode 0 to it, which every lane applies.  S <= 4, Np * S <= 64.
+constexpr int kMeanElems = 64;   // elements per CTA of mean64_kernel
+
+// kMeanElems elements per CTA of 256 threads: one thread per (element, variable) forms the FP64
+// mean update of MeanArgs (the face difference of each stage telescopes over the mesh: every
+// face has one stored value).  With A.shift, first the mode-0 values of the CTA's elements go
+// to shared memory (consecutive threads on consecutive values), the same thread also forms the
+// float element mean and the shift to the new mean, and the shifted values go back.  Every FP64 instruction runs on
+// full warps: on this part the FP64 pipe costs a warp instruction the same whatever its mask.
+// S <= 4, Np * S <= 64.
 __global__ void __launch_bounds__(256) mean64_kernel(const MeanArgs A) {
+    __shared__ float sv[kMeanElems * 64];
+    __shared__ float sd[kMeanElems * 4];
     pdl_trigger();
-    const int lane = threadIdx.x & 31;
-    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int S = A.S, NS = A.Np * A.S;
-    const bool live = e < A.E;
-    float* ue = A.u + (size_t)(live ? e : 0) * A.Np * A.M * S;
-    const int p0 = lane, p1 = lane + 32;
-    const bool h0 = live && p0 < NS, h1 = live && p1 < NS;
-    const int j0 = p0 / S, s0 = p0 - j0 * S, j1 = p1 / S, s1 = p1 - j1 * S;
-    const float w0 = h0 ? A.wf[j0] : 0.f, w1 = h1 ? A.wf[j1] : 0.f;
-    const bool own = live && lane < S;    // this lane updates variable s = lane
-    size_t xl = 0, xr = 0, yb = 0, yt = 0, yoff = 0;
-    if (own) {
+    const int e0 = blockIdx.x * kMeanElems;
+    const int ne = min(kMeanElems, A.E - e0);
+    const int tid = threadIdx.x;
+    const size_t esz = (size_t)A.Np * A.M * S;
+    pdl_wait();
+    if (A.shift) {
+        for (int i = tid; i < ne * NS; i += blockDim.x) {
+            const int e = i / NS, r = i - e * NS, j = r / S, v = r - j * S;
+            sv[i] = A.u[(size_t)(e0 + e) * esz + (size_t)j * A.M * S + v];
+        }
+        __syncthreads();
+    }
+    if (tid < ne * S) {
+        const int e = tid / S, s = tid - e * S, eg = e0 + e;
+        float mf = 0.f;
+        if (A.shift)
+            for (int j = 0; j < A.Np; ++j) mf += A.wf[j] * sv[e * NS + j * S + s];
+        size_t xl, xr, yb = 0, yt = 0, yoff = 0;
         if (A.dim == 1) {
-            xl = (size_t)e;
-            xr = e == A.E - 1 ? (A.xper ? 0 : (size_t)A.E) : (size_t)e + 1;
+            xl = (size_t)eg;
+            xr = eg == A.E - 1 ? (A.xper ? 0 : (size_t)A.E) : (size_t)eg + 1;
         } else {
-            const int ex = e % A.nx, ey = e / A.nx;
+            const int ex = eg % A.nx, ey = eg / A.nx;
             xl = (size_t)ey * (A.nx + 1) + ex;
             xr = (size_t)ey * (A.nx + 1) + (ex == A.nx - 1 ? (A.xper ? 0 : A.nx) : ex + 1);
             yb = (size_t)ey * A.nx + ex;
             yt = (size_t)(ey == A.ny - 1 ? (A.yper ? 0 : A.ny) : ey + 1) * A.nx + ex;
             yoff = (size_t)A.ny * (A.nx + 1) * S;
         }
-    }
-    pdl_wait();
-    // ---- loads
-    const float v0 = h0 ? ue[(size_t)j0 * A.M * S + s0] : 0.f;
-    const float v1 = h1 ? ue[(size_t)j1 * A.M * S + s1] : 0.f;
-    double m0 = 0.0, min = 0.0, dt = 0.0;
-    float fx[3][2] = {}, fy[3][2] = {};
-    if (own) {
-        const size_t idx = (size_t)e * S + lane;
-        m0 = A.mbar0[idx];
-        min = A.mbar_in ? A.mbar_in[idx] : m0;
-        dt = *A.dtp;
+        const size_t idx = (size_t)eg * S + s;
+        const double m0 = A.mbar0[idx];
+        double m = A.mbar_in ? A.mbar_in[idx] : m0;
+        const double dt = *A.dtp;
         for (int st = 0; st < A.nst; ++st) {
-            fx[st][0] = A.F[st][xl * S + lane];
-            fx[st][1] = A.F[st][xr * S + lane];
-            if (A.dim == 2) {
-                fy[st][0] = A.F[st][yoff + yb * S + lane];
-                fy[st][1] = A.F[st][yoff + yt * S + lane];
-            }
-        }
-    }
-    // ---- the float element mean of each variable
-    float mf = 0.f;   // lane s < S: variable s's
-    for (int s = 0; s < S; ++s) {
-        float x = (h0 && s0 == s ? w0 * v0 : 0.f) + (h1 && s1 == s ? w1 * v1 : 0.f);
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == s) mf = x;
-    }
-    // ---- FP64 update: mean of the residual -(1/J) (F_right - F_left) / 2 per direction
-    float delta = 0.f;
-    if (own) {
-        double m = min;
-        for (int st = 0; st < A.nst; ++st) {
-            double lm = -0.5 * A.invJx * ((double)fx[st][1] - (double)fx[st][0]);
-            if (A.dim == 2) lm -= 0.5 * A.invJy * ((double)fy[st][1] - (double)fy[st][0]);
+            const float* F = A.F[st];
+            // mean of the residual over the element: -(1/J) (F_right - F_left) / 2 per direction
+            double lm = -0.5 * A.invJx * ((double)F[xr * S + s] - (double)F[xl * S + s]);
+            if (A.dim == 2) lm -= 0.5 * A.invJy * ((double)F[yoff + yt * S + s] - (double)F[yoff + yb * S + s]);
             m = A.a[st] * m0 + A.b[st] * m + A.c[st] * dt * lm;
         }
-        delta = (float)(m - (double)mf);
-        A.mbar_out[(size_t)e * S + lane] = m;
+        if (A.shift) sd[tid] = (float)(m - (double)mf);
+        A.mbar_out[idx] = m;
     }
-    // every lane shifts its pairs by its variable's delta
-    const float d0 = __shfl_sync(0xffffffffu, delta, s0 < S ? s0 : 0);
-    const float d1 = __shfl_sync(0xffffffffu, delta, s1 < S ? s1 : 0);
-    if (h0) ue[(size_t)j0 * A.M * S + s0] = v0 + d0;
-    if (h1) ue[(size_t)j1 * A.M * S + s1] = v1 + d1;
+    if (!A.shift) return;
+    __syncthreads();
+    for (int i = tid; i < ne * NS; i += blockDim.x) {
+        const int e = i / NS, r = i - e * NS, j = r / S, v = r - j * S;
+        A.u[(size_t)(e0 + e) * esz + (size_t)j * A.M * S + v] = sv[i] + sd[e * S + v];
+    }
 }
 
 template <typename T>
@@ -710,8 +697,7 @@ cudaError_t launch_max_speed(bool fp64, const void* uhat, int E, int Np, int M, 
 
 cudaError_t launch_mean64(const MeanArgs& A, cudaStream_t st) {
     if (A.S > 4 || A.Np * A.S > 64) return cudaErrorInvalidValue;
-    const int warps = A.E;   // one warp per element, eight per block
-    return launch_pdl(mean64_kernel, dim3((warps + 7) / 8), dim3(256), 0, st, A);
+    return launch_pdl(mean64_kernel, dim3((A.E + kMeanElems - 1) / kMeanElems), dim3(256), 0, st, A);
 }
 
 cudaError_t launch_mean_init(bool fp64, const void* u, double* mbar, int E, int Np, int M, int S, const double* w,
