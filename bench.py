@@ -66,7 +66,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads' lines")
     ap.add_argument("--only", default=None,
-                    choices=["shock_vortex", "advection", "burgers", "sod", "batch", "adjoint", "peak"],
+                    choices=["shock_vortex", "advection", "burgers", "sod", "batch", "adjoint", "batch_adjoint", "peak"],
                     help="measure one workload alone and print its result (profiling runs)")
     return ap.parse_args(argv)
 
@@ -651,6 +651,88 @@ def measure_adjoint(torch, frsg, stream, nsteps=64, k=16):
                 adjoint_ms=a, ratio=a / p, ratio_vs_recording_forward=a / f)
 
 
+def measure_batch_adjoint(torch, frsg, stream, nsteps=64, k=16, fd_h=1e-6):
+    """The batched workload in FP64 (256 uneven Burgers problems): mean and variance over z of
+    the integral of u after nsteps steps and their gradients with respect to every member's
+    initial gPC coefficients (fr_sg_batch_forward_record, checkpoints every k steps;
+    fr_sg_batch_integral_moments; fr_sg_batch_adjoint with both cotangent sets in one sweep),
+    timed against the plain graph-replayed batched forward run of the same steps; a central
+    finite-difference check of both QoIs along one seeded direction per member (decisions
+    replayed, Richardson's combination of steps h and h / 2)."""
+    wls = workloads.burgers_batch()
+    members = []
+    for wl in wls:
+        sv = frsg.Solver(stream=stream.cuda_stream, precision="fp64", **wl["solver"])
+        set_initial(sv, wl)
+        members.append(sv)
+    dts = np.array([wl["cfl"] * (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"] / wl["lam0"]
+                    for wl in wls])
+    u0 = [torch.empty(sv.state_shape, dtype=torch.float64, device="cuda") for sv in members]
+    for sv, u in zip(members, u0):
+        sv.get_state(u)
+    b = frsg.Batch(members, stream=stream.cuda_stream)
+    lam = [[torch.empty_like(u) for u in u0] for _ in range(2)]
+    grad = [[torch.empty_like(u) for u in u0] for _ in range(2)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    plain, rec, adj, tot = [], [], [], []
+    with torch.cuda.stream(stream):
+        for rep in range(4):
+            for sv, u in zip(members, u0):
+                sv.set_state(u)
+            b.rk_step(dts, nsteps, graph=True)
+            for sv, u in zip(members, u0):
+                sv.set_state(u)
+            stream.synchronize()
+            ev[0].record(stream)
+            b.rk_step(dts, nsteps, graph=True)
+            ev[1].record(stream)
+            for sv, u in zip(members, u0):
+                sv.set_state(u)
+            ev[2].record(stream)
+            b.forward_record(dts, nsteps, k)
+            ev[3].record(stream)
+            q = b.integral_moments(lam[0], lam[1])     # synchronises
+            ev[4].record(stream)
+            b.adjoint(lam, grad)
+            ev[5].record(stream)
+            stream.synchronize()
+            if rep > 0:
+                plain.append(ev[0].elapsed_time(ev[1]))
+                rec.append(ev[2].elapsed_time(ev[3]))
+                adj.append(ev[4].elapsed_time(ev[5]))
+                tot.append(ev[2].elapsed_time(ev[3]) + ev[4].elapsed_time(ev[5]))
+        # central differences of both QoIs along one seeded direction per member, the perturbed
+        # runs replaying the recorded decisions (the frozen-decision map the adjoint differentiates)
+        rng = np.random.default_rng(2024)
+        dirs = [torch.tensor(rng.standard_normal(tuple(u.shape)), device="cuda") * u.abs().max() for u in u0]
+
+        def central(h):
+            qs = []
+            for sign in (1.0, -1.0):
+                for sv, u, d in zip(members, u0, dirs):
+                    sv.set_state(u + sign * h * d)
+                b.forward_replay(nsteps)
+                qs.append(b.integral_moments())
+            return (qs[0] - qs[1]) / (2 * h)
+        # Richardson's combination of h and h / 2 removes the h^2 term of the differences
+        fd = (4.0 * central(fd_h / 2) - central(fd_h)) / 3.0
+        stream.synchronize()
+    ad = np.array([[float(torch.sum(grad[c][i] * dirs[i])) for c in range(2)] for i in range(len(members))])
+    rel = np.abs(ad - fd) / np.maximum(np.maximum(np.abs(ad), np.abs(fd)), 1e-300)
+    for sv in members:
+        sv.check()
+    launches = b.launch_count()
+    b.close()
+    for sv in members:
+        sv.close()
+    p, r, a = float(np.median(plain)), float(np.median(rec)), float(np.median(adj))
+    return dict(workload="burgers_batch0: 256 problems, E 64-2048, P 1-4, N 2-10, Q 2N, FP64", steps=nsteps,
+                checkpoint_every=k, qois="E[int u dx], Var[int u dx] over z, both in one reverse sweep",
+                forward_ms=p, recording_forward_ms=r, adjoint_ms=a, ratio=a / p, ratio_per_qoi=a / (2 * p),
+                ratio_record_plus_adjoint=(r + a) / p, fd_step=fd_h, fd_max_rel_mean=float(rel[:, 0].max()),
+                fd_max_rel_var=float(rel[:, 1].max()), q_sample=q[:2].tolist(), launches_total=launches)
+
+
 def measure_peaks():
     """Roofline denominators: the measured HBM copy bandwidth (MEASURED_PEAKS.json, else
     the fallback figure) and this repository's FMA microbenchmark (libfrsg_peak.so)."""
@@ -723,7 +805,7 @@ def run_ours(args):
         oracle_dt, oracle_win, scale = job_windows(("shock_vortex_2d", {}, {}), CFL_2D, 1)
     forms = {p: measure_headline(torch, frsg, p, args, stream, flush, peaks, oracle_dt, oracle_win, scale)
              for p in ("fp64", "fp32", "fp32_tc")}
-    extra, batch, adj = {}, {}, None
+    extra, batch, adj, adj_batch = {}, {}, None, None
     if not args.no_extra and rank == 0:
         xsteps = max(3, min(args.steps, 50))
         for name, (spec, n, rule) in OTHER_1D.items():
@@ -742,6 +824,7 @@ def run_ours(args):
         batch = {p: measure_batch(torch, frsg, p, max(3, min(args.steps, 20)), 3, stream, flush, brefs)
                  for p in ("fp64", "fp32")}
         adj = measure_adjoint(torch, frsg, stream)
+        adj_batch = measure_batch_adjoint(torch, frsg, stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -788,6 +871,7 @@ def run_ours(args):
         "clocks": clocks,
         "batched": {"workload": "burgers_batch0: 256 problems, E 64-2048, P 1-4, N 2-10, Q 2N", **batch},
         "adjoint": adj,
+        "batched_adjoint": adj_batch,
         "other_workloads": extra,
     }
     if rank == 0:
@@ -815,6 +899,8 @@ def run_only(args):
         out = {p: measure_batch(torch, frsg, p, args.steps, args.warmup, stream, flush, []) for p in ("fp64", "fp32")}
     elif args.only == "adjoint":
         out = measure_adjoint(torch, frsg, stream)
+    elif args.only == "batch_adjoint":
+        out = measure_batch_adjoint(torch, frsg, stream)
     else:
         wl = workloads.ALL[args.only]()
         out = {}

@@ -264,6 +264,33 @@ uint64_t fr_sg_batch_launch_count(const frsg_batch* b);
 /* Tile count, persistent grid size and dynamic shared memory per CTA of the batched launch. */
 frsg_status fr_sg_batch_info(const frsg_batch* b, int* ntiles, int* grid, size_t* smem);
 
+/* Batched discrete adjoint (the adjoint below for every member of a batch at once): members
+ * FRSG_FP64, periodic, LLF flux, no filter or the exponential / L2 filter (FRSG_E_UNSUPPORTED
+ * otherwise).
+ * fr_sg_batch_forward_record advances every member by nsteps SSP-RK3 steps, member i with step
+ * size dt[i] (host array of n), one persistent launch per stage over all members' tiles, and
+ * keeps on the device each member's state every checkpoint_every steps and the filter decision
+ * of every stage (arenas owned by the batch, grown on demand).
+ * fr_sg_batch_adjoint maps nset cotangent sets at once: lambda_T[c n + i] (DEVICE double
+ * [E_i][Np_i][M_i], member i of set c) to grad_u0[c n + i] (same layout; host arrays of nset n
+ * device pointers, 1 <= nset <= 64).  Each segment between checkpoints is recomputed for all
+ * members with the recorded decisions, then walked back: one launch per stage covers every
+ * member and every set, the filter transpose applied to the cotangent tile in shared memory.
+ * The members' states are not touched.
+ * fr_sg_batch_forward_replay advances every member from its current state by nsteps <= the
+ * recorded steps with the recorded step sizes and filter decisions (the frozen-decision forward
+ * map the adjoint differentiates; for finite-difference checks), keeping nothing.
+ * fr_sg_batch_integral_moments: per member i, q[2 i] = E[I] and q[2 i + 1] = Var[I] of
+ * I(z) = integral of u(x, z) over the domain for the members' current states (host array of
+ * 2 n; the orthonormal gPC basis of §2.1, Eq. 3: E[I] is mode 0 of I, Var[I] the sum of the
+ * squares of its other modes), and their gradients with respect to the gPC coefficients in
+ * dmean[i] / dvar[i] (device pointers, layout of the state; either table may be NULL).  Needs a
+ * recorded run (its member tables); synchronises the batch's stream. */
+frsg_status fr_sg_batch_forward_record(frsg_batch* b, const double* dt, int nsteps, int checkpoint_every);
+frsg_status fr_sg_batch_forward_replay(frsg_batch* b, int nsteps);
+frsg_status fr_sg_batch_adjoint(frsg_batch* b, int nset, double* const* lambda_T, double* const* grad_u0);
+frsg_status fr_sg_batch_integral_moments(frsg_batch* b, double* q, double* const* dmean, double* const* dvar);
+
 /* Discrete adjoint of fr_sg_rk_step for 1D FRSG_FP64 contexts with no filter, the
  * exponential or the L2 filter: periodic advection / Burgers with the LLF flux, or Euler with
  * the LLF or HLL flux, any 1D boundary kind, with or without the positivity limiter

@@ -18,7 +18,7 @@ PEAK_OUT = os.path.join(HERE, "libfrsg_peak.so")   # FMA throughput microbenchma
 BUILD = os.path.join(HERE, "_build")
 
 SOURCES = ["api.cu", "tables.cpp", "kern1d.cu", "kern1d_f32.cu", "kern1d_f64.cu", "kern2d.cu", "kmisc.cu", "noalloc.cu",
-           "kadjoint.cu", "kadjoint_euler.cu"]
+           "kadjoint.cu", "kadjoint_euler.cu", "kadjoint_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

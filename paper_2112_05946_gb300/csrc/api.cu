@@ -502,7 +502,12 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
                 A.replay = c->d_replay + (size_t)c->replay_pos * c->E;
                 c->replay_pos += 1;
             }
-            A.fface = mean64(c) ? c->d_ff + (size_t)s * c->nfaces * c->S : nullptr;
+            // the cooperative step writes the stages' face values for the step's mean kernel; the
+            // halo-recomputing step updates the means itself (StageArgs::mbar)
+            A.fface = mean64(c) && c->wide == 2 ? c->d_ff + (size_t)s * c->nfaces * c->S : nullptr;
+            A.mbar = mean64(c) && c->wide == 3 && s == 0 ? mbar_of(c, 0) : nullptr;
+            A.wmean = c->d_tabf ? c->d_tabf + c->off.w : nullptr;
+            A.mshift = c->shift_now ? 1 : 0;
             A3[s] = A;
         }
         // the step's mean update from the three stages' face values, after the launch
@@ -543,7 +548,7 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
                 c->tok_te = 0;
                 c->tok_reset_next = false;
             }
-            return e == cudaSuccess ? step_mean() : e;
+            return e;
         }
         cudaError_t e = frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
         return e == cudaSuccess ? step_mean() : e;
@@ -968,7 +973,7 @@ frsg_status fr_sg_rhs(frsg_ctx* ctx, const void* u, void* dudt) {
 frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     if (!ctx) return FRSG_E_INVAL;
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
-    const int kernels_per_step = one_launch_step(ctx) ? 1 + (mean64(ctx) ? 1 : 0)
+    const int kernels_per_step = one_launch_step(ctx) ? 1 + (mean64(ctx) && ctx->wide == 2 ? 1 : 0)
                                                       : 3 * (1 + (ctx->cfg.limiter ? 1 : 0) + (mean64(ctx) ? 1 : 0));
     if (nsteps == 0) return FRSG_OK;
     CK(set_dt(ctx, dt));
@@ -1538,6 +1543,25 @@ struct frsg_batch {
     uint64_t launches = 0;
     cudaGraphExec_t graph = nullptr;
     std::vector<double> dt_set;
+    // recorded run of the batched adjoint (double members): arenas shared by all members
+    int rec_nsteps = 0, rec_k = 0;
+    std::vector<double> rec_dt;
+    size_t sum_ns = 0, sum_E = 0;
+    long long max_ns = 0;
+    double* a_ckpt = nullptr;       // [checkpoints][sum_ns]
+    double* a_seg = nullptr;        // [3 k][sum_ns]
+    uint8_t* a_log = nullptr;       // [steps][3][sum_E]
+    double* a_work = nullptr;       // [sets][4][sum_ns]
+    double* d_q = nullptr;          // [n][2] integral moments
+    double** d_ptrs = nullptr;      // pointer tables of the adjoint / moment calls
+    size_t cap_ckpt = 0, cap_seg = 0, cap_log = 0, cap_work = 0, cap_ptrs = 0;
+    frsg::AdjMember* d_mem = nullptr;
+    frsg::StageArgs* d_args_rec = nullptr;   // [3][n] the record: member buffers, decisions to the log
+    frsg::StageArgs* d_args_re = nullptr;    // [3][n] the recompute: segment slots, decisions from the log
+    frsg::StageArgs* d_args_rp = nullptr;    // [3][n] a replayed run: member buffers, decisions from the log
+    std::vector<frsg::AdjMember> mem;
+    size_t adj_smem = 0;
+    int adj_grid = 1;
 };
 
 frsg_status fr_sg_batch_create(frsg_ctx* const* ctxs, int n, void* stream, frsg_batch** out) {
@@ -1628,6 +1652,16 @@ frsg_status fr_sg_batch_create(frsg_ctx* const* ctxs, int n, void* stream, frsg_
 void fr_sg_batch_destroy(frsg_batch* b) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->a_ckpt);
+    cudaFree(b->a_seg);
+    cudaFree(b->a_log);
+    cudaFree(b->a_work);
+    cudaFree(b->d_q);
+    cudaFree(b->d_ptrs);
+    cudaFree(b->d_mem);
+    cudaFree(b->d_args_rec);
+    cudaFree(b->d_args_re);
+    cudaFree(b->d_args_rp);
     cudaFree(b->d_args);
     cudaFree(b->d_tiles);
     cudaFree(b->d_dt);
@@ -1696,6 +1730,318 @@ frsg_status fr_sg_batch_rk_step(frsg_batch* b, const double* dt, int nsteps, int
 }
 
 uint64_t fr_sg_batch_launch_count(const frsg_batch* b) { return b ? b->launches : 0; }
+
+// Device buffer of at least `want` bytes (contents not kept when it grows).
+static cudaError_t grow_bytes(void** p, size_t* cap, size_t want) {
+    if (want <= *cap) return cudaSuccess;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, want);
+    if (e == cudaSuccess) *cap = want;
+    return e;
+}
+
+static frsg_status batch_adjoint_supported(const frsg_batch* b) {
+    if (!b->fp64) {
+        std::fprintf(stderr, "the batched adjoint needs FRSG_FP64 members\n");
+        return FRSG_E_UNSUPPORTED;
+    }
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const frsg_config& c = b->ctx[i]->cfg;
+        if (c.flux != FRSG_FLUX_LLF || c.bc[0] != FRSG_BC_PERIODIC || c.filter == FRSG_FILTER_LASSO) {
+            std::fprintf(stderr, "batched adjoint: member %zu must be periodic with the LLF flux and no Lasso filter\n",
+                         i);
+            return FRSG_E_UNSUPPORTED;
+        }
+    }
+    return FRSG_OK;
+}
+
+static cudaError_t batch_push_members(frsg_batch* b) {
+    return cudaMemcpyAsync(b->d_mem, b->mem.data(), sizeof(frsg::AdjMember) * b->mem.size(), cudaMemcpyHostToDevice,
+                           b->stream);
+}
+
+frsg_status fr_sg_batch_forward_record(frsg_batch* b, const double* dt, int nsteps, int checkpoint_every) {
+    if (!b || !dt || nsteps < 1 || checkpoint_every < 1) return FRSG_E_INVAL;
+    frsg_status st = batch_adjoint_supported(b);
+    if (st != FRSG_OK) return st;
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i)
+        if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return FRSG_E_INVAL;
+    auto cuda = [](cudaError_t e) { return e == cudaErrorMemoryAllocation ? FRSG_E_NOMEM : FRSG_E_CUDA; };
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda(e);
+    // step sizes (shared with fr_sg_batch_rk_step's array)
+    e = cudaMemcpyAsync(b->d_dt, dt, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda(e);
+    b->dt_set.assign(dt, dt + n);
+    b->rec_dt.assign(dt, dt + n);
+    // member slices of the arenas
+    b->sum_ns = 0;
+    b->sum_E = 0;
+    b->max_ns = 0;
+    std::vector<size_t> off_ns(n), off_E(n);
+    for (int i = 0; i < n; ++i) {
+        const frsg_ctx* c = b->ctx[i];
+        const size_t ns = (size_t)c->E * c->Np * c->M;
+        off_ns[i] = b->sum_ns;
+        off_E[i] = b->sum_E;
+        b->sum_ns += ns;
+        b->sum_E += c->E;
+        b->max_ns = std::max(b->max_ns, (long long)ns);
+    }
+    const int nck = (nsteps + checkpoint_every - 1) / checkpoint_every;
+    e = grow_bytes((void**)&b->a_ckpt, &b->cap_ckpt, sizeof(double) * nck * b->sum_ns);
+    if (e == cudaSuccess) e = grow_bytes((void**)&b->a_seg, &b->cap_seg, sizeof(double) * 3 * checkpoint_every * b->sum_ns);
+    if (e == cudaSuccess) e = grow_bytes((void**)&b->a_log, &b->cap_log, (size_t)3 * nsteps * b->sum_E);
+    if (e == cudaSuccess && !b->d_mem) e = cudaMalloc(&b->d_mem, sizeof(frsg::AdjMember) * n);
+    if (e == cudaSuccess && !b->d_args_rec) e = cudaMalloc(&b->d_args_rec, sizeof(frsg::StageArgs) * 3 * n);
+    if (e == cudaSuccess && !b->d_args_re) e = cudaMalloc(&b->d_args_re, sizeof(frsg::StageArgs) * 3 * n);
+    if (e == cudaSuccess && !b->d_args_rp) e = cudaMalloc(&b->d_args_rp, sizeof(frsg::StageArgs) * 3 * n);
+    if (e == cudaSuccess && !b->d_q) e = cudaMalloc(&b->d_q, sizeof(double) * 2 * n);
+    if (e != cudaSuccess) return cuda(e);
+    // per member: the table of the adjoint kernels and the stage arguments of the record and
+    // of the recompute (log rows [step][stage][E]: stage s of step 0 at s E, moved by the kernel)
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    std::vector<frsg::StageArgs> rec(3 * (size_t)n), re(3 * (size_t)n), rp(3 * (size_t)n);
+    b->mem.assign(n, frsg::AdjMember{});
+    b->adj_smem = 0;
+    for (int i = 0; i < n; ++i) {
+        frsg_ctx* c = b->ctx[i];
+        const size_t ns = (size_t)c->E * c->Np * c->M;
+        uint8_t* log = b->a_log + (size_t)3 * nsteps * off_E[i];
+        // the log of member i holds nsteps rows of 3 E: base it at its own slice
+        double* seg = b->a_seg + (size_t)3 * checkpoint_every * off_ns[i];
+        frsg::AdjMember& m = b->mem[i];
+        m.tab = c->d_tab;
+        m.off = c->off;
+        m.E = c->E;
+        m.M = c->M;
+        m.Q = c->Q;
+        m.Np = c->Np;
+        m.filter = c->cfg.filter;
+        m.invJx = 2.0 * c->cfg.nx / (c->cfg.x1 - c->cfg.x0);
+        m.adv = c->cfg.adv_speed;
+        m.dt = dt[i];
+        m.alpha_dt = c->cfg.f_alpha * dt[i];
+        m.u = static_cast<const double*>(c->d_u);
+        m.ckpt = b->a_ckpt + (size_t)nck * off_ns[i];
+        m.seg = seg;
+        m.log = log;
+        m.work = nullptr;
+        m.ns = (long long)ns;
+        const int rows = std::max(1, 256 / c->Q);
+        b->adj_smem = std::max(b->adj_smem, frsg::adjoint_batched_smem(c->Np, c->M, c->Q, rows));
+        void* bin[3] = {c->d_u, c->d_u1, c->d_u2};
+        void* bout[3] = {c->d_u1, c->d_u2, c->d_u};
+        for (int s = 0; s < 3; ++s) {
+            frsg::StageArgs A = base_args(c);
+            A.a = ca[s];
+            A.b = cb[s];
+            A.c = cb[s];
+            A.dtp = b->d_dt + i;
+            A.do_filter = c->cfg.filter != FRSG_FILTER_NONE ? 1 : 0;
+            A.TE = rows;
+            A.fface = nullptr;
+            frsg::StageArgs R = A;
+            A.uin = bin[s];
+            A.ubase = c->d_u;
+            A.uout = bout[s];
+            A.flags = log + (size_t)s * c->E;
+            A.replay = nullptr;
+            R.uin = seg + (size_t)s * ns;
+            R.ubase = seg;
+            R.uout = seg + (size_t)(s + 1) * ns;
+            R.flags = nullptr;
+            R.replay = log + (size_t)s * c->E;
+            frsg::prepare_float_scalars(A);
+            frsg::prepare_float_scalars(R);
+            rec[(size_t)s * n + i] = A;
+            re[(size_t)s * n + i] = R;
+            A.flags = nullptr;
+            A.replay = log + (size_t)s * c->E;
+            rp[(size_t)s * n + i] = A;
+        }
+    }
+    if (b->adj_smem > 220 * 1024) return FRSG_E_UNSUPPORTED;
+    // each step's rows are 3 E_i apart in member i's own log slice: the kernel moves the
+    // pointers by log_n * 3 E_i, so member i's slice holds nsteps consecutive triples
+    e = cudaMemcpyAsync(b->d_args_rec, rec.data(), sizeof(frsg::StageArgs) * rec.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_args_re, re.data(), sizeof(frsg::StageArgs) * re.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_args_rp, rp.data(), sizeof(frsg::StageArgs) * rp.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = batch_push_members(b);
+    if (e != cudaSuccess) return cuda(e);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->adj_grid = std::max(1, frsg::adjoint_batched_blocks_per_sm(b->equation, b->adj_smem) * sms);
+    for (int k = 0; k < nsteps; ++k) {
+        if (k % checkpoint_every == 0) {
+            e = frsg::launch_adjoint_copy(b->d_mem, n, 0, k / checkpoint_every, nullptr, 1, 0, b->max_ns, b->stream);
+            if (e != cudaSuccess) return cuda(e);
+            b->launches += 1;
+        }
+        for (int s = 0; s < 3; ++s) {
+            e = frsg::launch_stage1d_batched_rec(b->equation, b->d_args_rec + (size_t)s * n, b->d_tiles, b->ntiles,
+                                                 b->smem, b->grid, 0, k, b->stream);
+            if (e != cudaSuccess) return cuda(e);
+            b->launches += 1;
+        }
+    }
+    for (frsg_ctx* m : b->ctx) m->mean_valid = false;
+    b->rec_nsteps = nsteps;
+    b->rec_k = checkpoint_every;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_batch_forward_replay(frsg_batch* b, int nsteps) {
+    if (!b || nsteps < 1) return FRSG_E_INVAL;
+    if (b->rec_nsteps < nsteps) {
+        std::fprintf(stderr, "fr_sg_batch_forward_replay: %d steps asked, %d recorded\n", nsteps, b->rec_nsteps);
+        return FRSG_E_INVAL;
+    }
+    const int n = (int)b->ctx.size();
+    cudaError_t e = cudaSuccess;
+    // the recorded step sizes (fr_sg_batch_rk_step may have changed the shared array since)
+    if (b->dt_set != b->rec_dt) {
+        e = cudaMemcpyAsync(b->d_dt, b->rec_dt.data(), sizeof(double) * n, cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return FRSG_E_CUDA;
+        b->dt_set = b->rec_dt;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        for (int s = 0; s < 3; ++s) {
+            e = frsg::launch_stage1d_batched_rec(b->equation, b->d_args_rp + (size_t)s * n, b->d_tiles, b->ntiles,
+                                                 b->smem, b->grid, 0, k, b->stream);
+            if (e != cudaSuccess) return FRSG_E_CUDA;
+            b->launches += 1;
+        }
+    }
+    for (frsg_ctx* m : b->ctx) m->mean_valid = false;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_batch_adjoint(frsg_batch* b, int nset, double* const* lambda_T, double* const* grad_u0) {
+    if (!b || nset < 1 || nset > 64 || !lambda_T || !grad_u0) return FRSG_E_INVAL;
+    if (b->rec_nsteps < 1) {
+        std::fprintf(stderr, "fr_sg_batch_adjoint: no recorded run (call fr_sg_batch_forward_record first)\n");
+        return FRSG_E_INVAL;
+    }
+    const int n = (int)b->ctx.size();
+    for (size_t i = 0; i < (size_t)nset * n; ++i)
+        if (!lambda_T[i] || !grad_u0[i]) return FRSG_E_INVAL;
+    auto cuda = [](cudaError_t e) { return e == cudaErrorMemoryAllocation ? FRSG_E_NOMEM : FRSG_E_CUDA; };
+    cudaError_t e = cudaStreamSynchronize(b->stream);   // the tables below are rewritten
+    if (e != cudaSuccess) return cuda(e);
+    const size_t want = sizeof(double) * 4 * nset * b->sum_ns;
+    const bool moved = want > b->cap_work;
+    e = grow_bytes((void**)&b->a_work, &b->cap_work, want);
+    if (e == cudaSuccess) e = grow_bytes((void**)&b->d_ptrs, &b->cap_ptrs, sizeof(double*) * 2 * nset * n);
+    if (e != cudaSuccess) return cuda(e);
+    if (moved || b->mem[0].work == nullptr) {
+        size_t off = 0;
+        for (int i = 0; i < n; ++i) {
+            b->mem[i].work = b->a_work + off;
+            off += (size_t)b->mem[i].ns;
+        }
+        e = batch_push_members(b);
+        if (e != cudaSuccess) return cuda(e);
+    }
+    std::vector<double*> tab(2 * (size_t)nset * n);
+    for (size_t i = 0; i < (size_t)nset * n; ++i) {
+        tab[i] = lambda_T[i];
+        tab[(size_t)nset * n + i] = grad_u0[i];
+    }
+    // pageable source: staged before the call returns
+    e = cudaMemcpyAsync(b->d_ptrs, tab.data(), sizeof(double*) * tab.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda(e);
+    const long long ws = (long long)b->sum_ns;
+    e = frsg::launch_adjoint_copy(b->d_mem, n, 2, 0, b->d_ptrs, nset, ws, b->max_ns, b->stream);
+    if (e != cudaSuccess) return cuda(e);
+    b->launches += 1;
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const int nsteps = b->rec_nsteps, k = b->rec_k;
+    const int nseg = (nsteps + k - 1) / k;
+    int p = 0;   // role of the current step output's cotangent (0 or 1); the other receives the input's
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int n0 = sg * k, n1 = std::min(nsteps, n0 + k);
+        e = frsg::launch_adjoint_copy(b->d_mem, n, 1, sg, nullptr, 1, ws, b->max_ns, b->stream);
+        if (e != cudaSuccess) return cuda(e);
+        b->launches += 1;
+        // recompute the segment's stage inputs with the recorded decisions (the last step's
+        // third stage output is the next checkpoint: not needed)
+        for (int j = 0; j < n1 - n0; ++j) {
+            for (int s = 0; s < 3; ++s) {
+                if (j == n1 - n0 - 1 && s == 2) break;
+                e = frsg::launch_stage1d_batched_rec(b->equation, b->d_args_re + (size_t)s * n, b->d_tiles, b->ntiles,
+                                                     b->smem, b->grid, j, n0 + j, b->stream);
+                if (e != cudaSuccess) return cuda(e);
+                b->launches += 1;
+            }
+        }
+        for (int j = n1 - n0 - 1; j >= 0; --j) {
+            const int step = n0 + j;
+            for (int s = 2; s >= 0; --s) {
+                frsg::AdjStage S{};
+                S.slot = 3 * j + s;
+                S.row = 3 * step + s;
+                S.a = ca[s];
+                S.b = cb[s];
+                S.c = cb[s];
+                S.wstride = ws;
+                S.lb = 1 - p;
+                S.base_init = s == 2;
+                S.accumulate = s == 0;
+                S.mu = s == 2 ? p : (s == 1 ? 2 : 3);
+                S.lv = s == 2 ? 2 : (s == 1 ? 3 : -1);
+                e = frsg::launch_adjoint_batched(b->equation, b->d_mem, b->d_tiles, b->ntiles, nset, S, b->adj_smem,
+                                                 b->adj_grid, b->stream);
+                if (e != cudaSuccess) return cuda(e);
+                b->launches += 1;
+            }
+            p = 1 - p;
+        }
+    }
+    e = frsg::launch_adjoint_copy(b->d_mem, n, 3, p, b->d_ptrs + (size_t)nset * n, nset, ws, b->max_ns, b->stream);
+    if (e != cudaSuccess) return cuda(e);
+    b->launches += 1;
+    return FRSG_OK;
+}
+
+frsg_status fr_sg_batch_integral_moments(frsg_batch* b, double* q, double* const* dmean, double* const* dvar) {
+    if (!b || !q) return FRSG_E_INVAL;
+    const int n = (int)b->ctx.size();
+    if (b->mem.size() != (size_t)n) {
+        std::fprintf(stderr, "fr_sg_batch_integral_moments: no recorded run (call fr_sg_batch_forward_record first)\n");
+        return FRSG_E_INVAL;
+    }
+    auto cuda = [](cudaError_t e) { return e == cudaErrorMemoryAllocation ? FRSG_E_NOMEM : FRSG_E_CUDA; };
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = grow_bytes((void**)&b->d_ptrs, &b->cap_ptrs, sizeof(double*) * 2 * n);
+    if (e != cudaSuccess) return cuda(e);
+    std::vector<double*> tab(2 * (size_t)n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        tab[i] = dmean ? dmean[i] : nullptr;
+        tab[(size_t)n + i] = dvar ? dvar[i] : nullptr;
+    }
+    e = cudaMemcpyAsync(b->d_ptrs, tab.data(), sizeof(double*) * tab.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = frsg::launch_integral_moments(b->d_mem, n, b->d_q, dmean ? b->d_ptrs : nullptr,
+                                          dvar ? b->d_ptrs + n : nullptr, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q, b->d_q, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda(e);
+    b->launches += 1;
+    return FRSG_OK;
+}
 
 frsg_status fr_sg_batch_info(const frsg_batch* b, int* ntiles, int* grid, size_t* smem) {
     if (!b) return FRSG_E_INVAL;

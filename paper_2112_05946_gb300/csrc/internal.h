@@ -76,6 +76,12 @@ struct StageArgs {
     // face of element e (face E the right boundary).  2D: x faces [ny][nx + 1][S] (face ex the
     // left face of element ex), then y faces [ny + 1][nx][S] (face ey the bottom face of row ey).
     float* fface;
+    // the one-launch step (1D layout 3, float forms) updates the FP64 means itself: mbar [E][S]
+    // holds the means of u^n on entry and of u^{n+1} on exit (null = no means); wmean: the float
+    // table w_j / 2; mshift: also move the float mean mode of u^{n+1} onto them
+    double* mbar;
+    const float* wmean;
+    int mshift;
     // optional second output of the same residual (the RK4 weighted sum of the L's):
     // acc_out = acc_a*acc_in + acc_b*uin + acc_c*dt*L(uin), unfiltered; null = none
     void* acc_out;

@@ -16,38 +16,13 @@
 // being differentiated along the branch the forward values take.
 #include <cuda_runtime.h>
 
+#include "adjoint.cuh"
 #include "epilogue.cuh"
 #include "internal.h"
 #include "physics.cuh"
 
 namespace frsg {
 namespace {
-
-template <typename T, int EQ>
-__device__ __forceinline__ T dflux(T u, T adv) {
-    if constexpr (EQ == FRSG_EQ_ADVECTION) return adv;
-    else return u;
-}
-
-// d LLF / d uL and d LLF / d uR at (uL, uR) for a scalar flux.
-template <typename T, int EQ>
-__device__ __forceinline__ void dllf(T a, T b, T adv, T* da, T* db) {
-    T alpha, dal = T(0), dbl = T(0);
-    if constexpr (EQ == FRSG_EQ_ADVECTION) {
-        alpha = fabs(adv);
-    } else {
-        const T la = fabs(a), lb = fabs(b);
-        if (la >= lb) {
-            alpha = la;
-            dal = a > T(0) ? T(1) : (a < T(0) ? T(-1) : T(0));
-        } else {
-            alpha = lb;
-            dbl = b > T(0) ? T(1) : (b < T(0) ? T(-1) : T(0));
-        }
-    }
-    *da = T(0.5) * dflux<T, EQ>(a, adv) + T(0.5) * alpha - T(0.5) * (b - a) * dal;
-    *db = T(0.5) * dflux<T, EQ>(b, adv) - T(0.5) * alpha - T(0.5) * (b - a) * dbl;
-}
 
 // mu' = F^T mu per element with the recorded decision; thread per (element, k, s).
 template <typename T, int NP>

@@ -16,6 +16,8 @@ cudaError_t k1d_batched_f32(int equation, const StageArgs* args, const int4* til
                             cudaStream_t st);
 cudaError_t k1d_batched_f64(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid,
                             cudaStream_t st);
+cudaError_t k1d_batched_rec_f64(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem,
+                                int grid, int seg_j, int log_n, cudaStream_t st);
 int k1d_batched_occ_f32(int equation, size_t smem);
 int k1d_batched_occ_f64(int equation, size_t smem);
 
@@ -41,6 +43,11 @@ cudaError_t launch_stage1d_batched(bool fp64, int equation, const StageArgs* arg
                                    size_t smem, int grid, cudaStream_t st) {
     return fp64 ? k1d_batched_f64(equation, args, tiles, ntiles, smem, grid, st)
                 : k1d_batched_f32(equation, args, tiles, ntiles, smem, grid, st);
+}
+
+cudaError_t launch_stage1d_batched_rec(int equation, const StageArgs* args, const int4* tiles, int ntiles,
+                                       size_t smem, int grid, int seg_j, int log_n, cudaStream_t st) {
+    return k1d_batched_rec_f64(equation, args, tiles, ntiles, smem, grid, seg_j, log_n, st);
 }
 
 cudaError_t launch_step1d(const frsg_config& cfg, bool fp64, const StageArgs* A3, unsigned* bar, int* grid,

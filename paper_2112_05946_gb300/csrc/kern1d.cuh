@@ -609,6 +609,36 @@ __global__ void __launch_bounds__(256) stage1d_batched_kernel(const StageArgs* _
     }
 }
 
+// The same persistent launch for a recorded run of a batch (the discrete adjoint's forward
+// record and its segment recompute): each problem's stage pointers are moved by seg_j steps of
+// three state slots (uin, ubase, uout) and its decision rows by log_n steps of three rows of E
+// bytes (flags, replay), so that one argument array serves every step of the run.
+template <typename T, int S, int EQ>
+__global__ void __launch_bounds__(256) stage1d_batched_rec_kernel(const StageArgs* __restrict__ args,
+                                                                  const int4* __restrict__ tiles, int ntiles,
+                                                                  int seg_j, int log_n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tr = tiles[t];
+        StageArgs A = args[tr.x];
+        const size_t shift = (size_t)seg_j * 3 * ((size_t)A.E * tr.w * A.M * S);
+        A.uin = static_cast<const T*>(A.uin) + shift;
+        A.ubase = static_cast<const T*>(A.ubase) + shift;
+        A.uout = static_cast<T*>(A.uout) + shift;
+        const size_t rows = (size_t)log_n * 3 * A.E;
+        if (A.flags) A.flags += rows;
+        if (A.replay) A.replay += rows;
+        const int tq = threadIdx.x % A.Q, te = threadIdx.x / A.Q;
+        switch (tr.w) {
+            case 2: stage1d_tile<T, 2, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+            case 3: stage1d_tile<T, 3, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+            case 4: stage1d_tile<T, 4, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+            case 5: stage1d_tile<T, 5, S, EQ>(A, tr.y, tr.z, tq, te, threadIdx.x, blockDim.x, smem_raw); break;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, int NP, int S, int EQ, int MC, int QC>
 cudaError_t launch_mq(const StageArgs& A, cudaStream_t st) {
     const int TE = A.TE;
@@ -731,6 +761,18 @@ cudaError_t batched_typed(const StageArgs* args, const int4* tiles, int ntiles, 
         if (e != cudaSuccess) return e;
     }
     kern<<<grid, 256, smem, st>>>(args, tiles, ntiles);
+    return cudaGetLastError();
+}
+
+template <typename T, int EQ>
+cudaError_t batched_rec_typed(const StageArgs* args, const int4* tiles, int ntiles, size_t smem, int grid, int seg_j,
+                              int log_n, cudaStream_t st) {
+    auto kern = stage1d_batched_rec_kernel<T, 1, EQ>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, 256, smem, st>>>(args, tiles, ntiles, seg_j, log_n);
     return cudaGetLastError();
 }
 

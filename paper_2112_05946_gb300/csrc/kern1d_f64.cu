@@ -24,6 +24,15 @@ cudaError_t k1d_batched_f64(int equation, const StageArgs* args, const int4* til
     return cudaErrorInvalidValue;
 }
 
+cudaError_t k1d_batched_rec_f64(int equation, const StageArgs* args, const int4* tiles, int ntiles, size_t smem,
+                                int grid, int seg_j, int log_n, cudaStream_t st) {
+    if (equation == FRSG_EQ_ADVECTION)
+        return batched_rec_typed<double, FRSG_EQ_ADVECTION>(args, tiles, ntiles, smem, grid, seg_j, log_n, st);
+    if (equation == FRSG_EQ_BURGERS)
+        return batched_rec_typed<double, FRSG_EQ_BURGERS>(args, tiles, ntiles, smem, grid, seg_j, log_n, st);
+    return cudaErrorInvalidValue;
+}
+
 int k1d_batched_occ_f64(int equation, size_t smem) {
     if (equation == FRSG_EQ_ADVECTION) return batched_occ<double, FRSG_EQ_ADVECTION>(smem);
     return batched_occ<double, FRSG_EQ_BURGERS>(smem);

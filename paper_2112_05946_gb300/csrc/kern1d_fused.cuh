@@ -43,6 +43,7 @@ __host__ __device__ inline size_t smem1d_fused_bytes(int TE, int NP, int M, int 
     n += 2 * (size_t)NP * NP + (size_t)NP * M + NP;   // Vf, Vfinv, Lam, Top
     n += 2 * W * Q * NP;                              // Red
     if (sizeof(T) == 4) n += W * S * Q;               // face-flux sums of the FP64 mean
+    if (sizeof(T) == 4) n += 3 * (W + 2) * S;         // their per-stage values: left faces, right boundary
     return n * sizeof(T) + W * sizeof(int) + 16;
 }
 
@@ -107,6 +108,10 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
     T* sRed = p; p += 2 * W * Q * NP;
     float* sFs = reinterpret_cast<float*>(p);
     if (sizeof(T) == 4) p += (size_t)W * S * Q;
+    // FP64 means: per stage st, the face value of the left face of slot r at sFst[(st (W + 2) + r) S]
+    // and that of the right boundary face (non-periodic, last element) at slot W + 1
+    float* sFst = reinterpret_cast<float*>(p);
+    if (sizeof(T) == 4) p += (size_t)3 * (W + 2) * S;
     int* sFlag = reinterpret_cast<int*>(p);
 
     // slot -> element of the problem; -1 beyond a physical boundary or past the slots the
@@ -220,6 +225,7 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
     unsigned long long seen = 0;
     bool bad = false;
 
+    const bool mean64 = sizeof(T) == 4 && a0.mbar != nullptr;
 #pragma unroll 1
     for (int st = 0; st < 3; ++st) {
         const StageArgs& A = st == 0 ? a0 : (st == 1 ? a1 : a2);
@@ -261,27 +267,25 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
         __syncthreads();
 
         // ---- a5 + a6 + a7: traces, interface fluxes, derivative row j (nodal in z)
-        const bool mean64 = sizeof(T) == 4 && A.fface != nullptr;
         float cF0[S], cF1[S];   // face-sum contributions wz_q f^I (point-0 threads): left / right face
 #pragma unroll
         for (int s = 0; s < S; ++s) cF0[s] = cF1[s] = 0.f;
-        if (out_valid) {
-            auto trace = [&](const T* src, const T(&w)[NP], int s) {
-                T acc = T(0);
+        // the FP64 means need, in the last stage, the left face of the first slot after the
+        // owned ones too: the right face of the last owned element as the next tile's owner of
+        // that face computes it (the same code path on the same values)
+        const bool extra = mean64 && st == 2 && r == H + ne && present && tj == 0;
+        auto trace = [&](const T* src, const T(&w)[NP], int s) {
+            T acc = T(0);
 #pragma unroll
-                for (int m = 0; m < NP; ++m) acc += w[m] * src[(m * S + s) * Q + tq];
-                return acc;
-            };
-            const T* own = sUn + (size_t)r * nsz;
-            const T* fown = sF + (size_t)r * nsz;
-            T uLf[S], uRf[S], nL[S], nR[S], fDL[S], fDR[S], fIL[S], fIR[S];
+            for (int m = 0; m < NP; ++m) acc += w[m] * src[(m * S + s) * Q + tq];
+            return acc;
+        };
+        const T* own = sUn + (size_t)r * nsz;
+        T fIL[S];   // the left face's interface flux
+        if (out_valid || extra) {
+            T uLf[S], nL[S];
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-                uLf[s] = trace(own, rlm, s);
-                uRf[s] = trace(own, rlp, s);
-                fDL[s] = trace(fown, rlm, s);
-                fDR[s] = trace(fown, rlp, s);
-            }
+            for (int s = 0; s < S; ++s) uLf[s] = trace(own, rlm, s);
             if (hasL) {
 #pragma unroll
                 for (int s = 0; s < S; ++s) nL[s] = trace(sUn + (size_t)(r - 1) * nsz, rlp, s);
@@ -295,6 +299,22 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
                 }
             } else {
                 ghost_from_interior<T, EQ, S, 0>(A.bc[0], uLf, nL);
+            }
+            face_flux<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma, A.flux);
+            if (mean64 && tj == 0) {
+                const float wz = (float)sPz[tq];   // Pz[0][q] = wz_q (Phi_0 = 1)
+#pragma unroll
+                for (int s = 0; s < S; ++s) cF0[s] = wz * (float)fIL[s];
+            }
+        }
+        if (out_valid) {
+            const T* fown = sF + (size_t)r * nsz;
+            T uRf[S], nR[S], fDL[S], fDR[S], fIR[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                uRf[s] = trace(own, rlp, s);
+                fDL[s] = trace(fown, rlm, s);
+                fDR[s] = trace(fown, rlp, s);
             }
             if (hasR) {
 #pragma unroll
@@ -310,15 +330,11 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
             } else {
                 ghost_from_interior<T, EQ, S, 0>(A.bc[1], uRf, nR);
             }
-            face_flux<T, EQ, S, 1, 0>(nL, uLf, fIL, adv, gamma, A.flux);
             face_flux<T, EQ, S, 1, 0>(uRf, nR, fIR, adv, gamma, A.flux);
             if (mean64 && tj == 0) {
-                const float wz = (float)sPz[tq];   // Pz[0][q] = wz_q (Phi_0 = 1)
+                const float wz = (float)sPz[tq];
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    cF0[s] = wz * (float)fIL[s];
-                    cF1[s] = wz * (float)fIR[s];
-                }
+                for (int s = 0; s < S; ++s) cF1[s] = wz * (float)fIR[s];
             }
 #pragma unroll
             for (int s = 0; s < S; ++s) {
@@ -329,20 +345,21 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
             }
         }
         if (mean64) {
-            // an owned element writes its left face of this stage; the last element of a
-            // non-periodic mesh also its right face
+            // the face values of this stage, summed over the z-nodes: the left faces of the owned
+            // slots and of the slot after them; the right boundary face of a non-periodic mesh
             const bool shfl = (Q & (Q - 1)) == 0 && Q <= 32 && (nthr & 31) == 0;
-            const bool mine = owned && out_valid && tj == 0;
+            const bool face_slot = r >= H && r <= H + ne && present;
+            const bool mine = face_slot && (out_valid || extra) && tj == 0;
             group_sum<S>(cF0, tq, Q, r, mine, shfl, sFs);
             if (mine && tq == 0)
 #pragma unroll
-                for (int s = 0; s < S; ++s) A.fface[(size_t)g_r * S + s] = cF0[s];
+                for (int s = 0; s < S; ++s) sFst[((size_t)st * (W + 2) + r) * S + s] = cF0[s];
             if (!periodic && e0 + ne == E) {
-                const bool last = mine && g_r == E - 1;
+                const bool last = owned && out_valid && tj == 0 && g_r == E - 1;
                 group_sum<S>(cF1, tq, Q, r, last, shfl, sFs);
                 if (last && tq == 0)
 #pragma unroll
-                    for (int s = 0; s < S; ++s) A.fface[(size_t)E * S + s] = cF1[s];
+                    for (int s = 0; s < S; ++s) sFst[((size_t)st * (W + 2) + W + 1) * S + s] = cF1[s];
             }
         }
         __syncthreads();
@@ -360,6 +377,39 @@ __global__ void __maxnreg__((sizeof(T) == 4 && S == 1) ? 72 : 64)
                                                    out_valid, out_valid, g_r, owned, sU + (size_t)r * elsz, sK.det, M);
         }
         __syncthreads();
+    }
+
+    if (mean64) {
+        // FP64 means of the owned elements (§4.1, §4.3: the stages move an element's mean by its
+        // face fluxes only): stage st of coefficients (a, b, c dt) maps m to
+        // a m0 + b m - (c dt / 2) invJx (F_right - F_left), the face values' difference exact in
+        // double; both sides of a face use one value, so the means telescope over the mesh.
+        // Then, when asked, the float mean mode of u^{n+1} moves onto them.
+        const double invJx = a0.invJx;
+        for (int i = tid; i < ne * S; i += nthr) {
+            const int e = i / S, s = i - e * S, rr = H + e;
+            const size_t gi = (size_t)(e0 + e) * S + s;
+            const bool right_elem = slot_elem(rr + 1) >= 0;
+            const double m0 = a0.mbar[gi];
+            double m = m0;
+#pragma unroll
+            for (int st = 0; st < 3; ++st) {
+                const StageArgs& A = st == 0 ? a0 : (st == 1 ? a1 : a2);
+                const float* Fs = sFst + (size_t)st * (W + 2) * S;
+                const double FL = (double)Fs[rr * S + s];
+                const double FR = (double)Fs[(right_elem ? rr + 1 : W + 1) * S + s];
+                const double cdt = A.dtp ? A.c * dt_raw : A.c;
+                m = A.a * m0 + A.b * m + cdt * (-0.5 * invJx * (FR - FL));
+            }
+            a0.mbar[gi] = m;
+            if (a0.mshift) {
+                T* ue = sU + (size_t)rr * elsz + s;
+                float mf = 0.f;
+                for (int j = 0; j < NP; ++j) mf += a0.wmean[j] * (float)ue[(size_t)j * M * S];
+                const float d = (float)(m - (double)mf);
+                for (int j = 0; j < NP; ++j) ue[(size_t)j * M * S] += (T)d;
+            }
+        }
     }
 
     // The step ends in shared memory (the owned slots).  Before the store over u^n, make sure

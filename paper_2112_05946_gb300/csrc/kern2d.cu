@@ -66,8 +66,8 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
 
 template <typename T>
 size_t smem2d_bytes_t(int TE, int n1, int M, int Q, int S, bool tc) {
-    // the flags, then (TC) the MMA barrier and the TMEM address
-    return smem2d_elems<T>(TE, n1, M, Q, S, tc) * sizeof(T) + (size_t)TE * sizeof(int) + 16 + (tc ? 32 : 0);
+    // the flags, then (16-byte aligned) the MMA barrier, the TMEM address and the tile's barrier
+    return smem2d_elems<T>(TE, n1, M, Q, S, tc) * sizeof(T) + (size_t)TE * sizeof(int) + 16 + 32;
 }
 
 // A neighbour's trace at z-node q from its modal face trace ft [k][s] (one line of a face):
@@ -143,9 +143,11 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     float* sFs = reinterpret_cast<float*>(p);
     if (sizeof(T) == 4 && !gshfl) p += (size_t)TE * S * nel;
     int* sFlag = reinterpret_cast<int*>(p);
-    // TC: the MMA completion barrier (16-byte aligned after the flags) and the TMEM address
+    // TC: the MMA completion barrier (16-byte aligned after the flags) and the TMEM address;
+    // then the barrier of the tile's bulk copy
     uint64_t* sBar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(sFlag + TE) + 15) & ~(uintptr_t)15);
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 2);
+    uint64_t* sTileBar = sBar + 3;
     const int warp = tid >> 5, lane = tid & 31;
     const uint32_t kTmemCols = TE <= 4 ? 32 : 64;   // TE/2 tiles x 16 columns (a power of two >= 32)
 
@@ -171,6 +173,15 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     }
     const T* ubase = static_cast<const T*>(A.ubase);
     const bool xper = A.bc[0] == FRSG_BC_PERIODIC, yper = A.bc[2] == FRSG_BC_PERIODIC;
+    // the tile (elements e0 .. e0 + ne - 1, contiguous) as one bulk copy when it starts on a
+    // 16-byte boundary; else per-element asynchronous copies
+    const unsigned tile_bytes = (unsigned)((size_t)ne * elsz * sizeof(T));
+    const bool bulk = ((size_t)elsz * sizeof(T)) % 16 == 0 && (reinterpret_cast<uintptr_t>(uin) & 15) == 0 &&
+                      tile_bytes < (1u << 20);
+    if (bulk && tid == 0) {
+        mbar_init(sTileBar, 1);
+        mbar_init_fence();
+    }
     pdl_wait();
     {
         // the tile, and the neighbours' modal face traces straight from global memory: face 0
@@ -181,7 +192,14 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
         const int nl = ex0 - 1, nr = ex0 + ne;
         const bool hasL = nl >= 0 || xper, hasR = nr < nx || xper;
         const T* srcT = uin + (size_t)e0 * elsz;
-        for (int i = tid; i < ne * elsz; i += nthr) cp_async(sU + i, srcT + i);
+        if (bulk) {
+            if (tid == 0) {
+                mbar_arrive_expect_tx(sTileBar, tile_bytes);
+                bulk_load(sU, srcT, tile_bytes, sTileBar);
+            }
+        } else {
+            for (int i = tid; i < ne * elsz; i += nthr) cp_async(sU + i, srcT + i);
+        }
         const int fpairs = N1 * M;
         for (int idx = tid; idx < (2 + 2 * ne) * fpairs; idx += nthr) {
             const int f = idx / fpairs, r = idx - f * fpairs;
@@ -220,6 +238,18 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     }
     cp_async_wait_all();
     __syncthreads();
+    if (bulk) {
+        const bool ok = mbar_wait(sTileBar, 0, kBulkWaitCycles);
+        if (!__syncthreads_and(ok)) {
+            // give up: latch the error, wait (bounded) once more for the copy in flight, leave
+            if (tid == 0) {
+                atomicOr(A.err, kErrTimeout);
+                mbar_wait(sTileBar, 0, kBulkWaitCycles);
+            }
+            __syncthreads();
+            return;
+        }
+    }
     const StageConsts<T> sK = make_consts<T>(A, dt_raw);
     const T gamma = sK.gamma, adv = sK.adv;
     if (A.do_filter) finish_filter_strengths<T>(A, NP, sLam, tid, nthr, sK.adt);   // read after later barriers

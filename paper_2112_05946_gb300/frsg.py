@@ -100,6 +100,13 @@ _SIGNATURES = [
     ("fr_sg_batch_destroy", None, [ctypes.c_void_p]),
     ("fr_sg_batch_rk_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_batch_launch_count", ctypes.c_uint64, [ctypes.c_void_p]),
+    ("fr_sg_batch_forward_record", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_batch_forward_replay", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("fr_sg_batch_adjoint", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    ("fr_sg_batch_integral_moments", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.POINTER(ctypes.c_void_p),
+                                                    ctypes.POINTER(ctypes.c_void_p)]),
     ("fr_sg_batch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_size_t)]),
     ("fr_sg_rk_step_noalloc", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p,
@@ -445,6 +452,63 @@ class Batch:
         st = self.lib.fr_sg_batch_rk_step(self.h, _ptr(d), int(nsteps), int(bool(graph)))
         if st != OK:
             raise FrsgError(st, "fr_sg_batch_rk_step failed")
+
+    def forward_record(self, dts, nsteps, checkpoint_every):
+        """fr_sg_batch_forward_record: nsteps steps of every member, checkpoints every
+        checkpoint_every steps and the decisions of every stage kept on the device."""
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        st = self.lib.fr_sg_batch_forward_record(self.h, _ptr(d), int(nsteps), int(checkpoint_every))
+        if st != OK:
+            raise FrsgError(st, "fr_sg_batch_forward_record failed (details on stderr)")
+
+    def forward_replay(self, nsteps):
+        """fr_sg_batch_forward_replay: nsteps steps from the members' current states with the
+        recorded step sizes and filter decisions."""
+        st = self.lib.fr_sg_batch_forward_replay(self.h, int(nsteps))
+        if st != OK:
+            raise FrsgError(st, "fr_sg_batch_forward_replay failed (details on stderr)")
+
+    @staticmethod
+    def _ptr_table(tensors):
+        for t in tensors:
+            if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous()):
+                raise ValueError("cotangents and gradients must be contiguous CUDA float64 tensors")
+        return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+    def adjoint(self, lambda_sets, grad_sets):
+        """fr_sg_batch_adjoint for len(lambda_sets) cotangent sets; lambda_sets[c][i] and
+        grad_sets[c][i] are member i's tensors of the state's shape (CUDA float64)."""
+        n = len(self.solvers)
+        if len(lambda_sets) != len(grad_sets) or any(len(x) != n for x in list(lambda_sets) + list(grad_sets)):
+            raise ValueError("one tensor per member in every set")
+        for c in range(len(lambda_sets)):
+            for i, sv in enumerate(self.solvers):
+                for t in (lambda_sets[c][i], grad_sets[c][i]):
+                    if tuple(t.shape) != tuple(sv.state_shape):
+                        raise ValueError(f"member {i}: tensor shape {tuple(t.shape)} != {tuple(sv.state_shape)}")
+        lam = self._ptr_table([t for ts in lambda_sets for t in ts])
+        grd = self._ptr_table([t for ts in grad_sets for t in ts])
+        st = self.lib.fr_sg_batch_adjoint(self.h, len(lambda_sets), lam, grd)
+        if st != OK:
+            raise FrsgError(st, "fr_sg_batch_adjoint failed (details on stderr)")
+
+    def integral_moments(self, dmean=None, dvar=None):
+        """fr_sg_batch_integral_moments: [n, 2] array of (E[I], Var[I]), I the integral of u over
+        the domain; gradients into the given per-member tensors (CUDA float64, state shape)."""
+        n = len(self.solvers)
+        q = np.empty((n, 2), dtype=np.float64)
+        tabs = []
+        for g in (dmean, dvar):
+            if g is None:
+                tabs.append(None)
+                continue
+            if len(g) != n or any(tuple(t.shape) != tuple(sv.state_shape) for t, sv in zip(g, self.solvers)):
+                raise ValueError("one gradient tensor of the state's shape per member")
+            tabs.append(self._ptr_table(list(g)))
+        st = self.lib.fr_sg_batch_integral_moments(self.h, _ptr(q), tabs[0], tabs[1])
+        if st != OK:
+            raise FrsgError(st, "fr_sg_batch_integral_moments failed (details on stderr)")
+        return q
 
     def info(self):
         nt, gr, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()

@@ -26,7 +26,7 @@ def _dts(members):
 
 
 # FP32: a single context carries its element means in FP64 and shifts the float mean mode to
-# them after every stage; the batch members do not, so the two agree to float rounding only
+# them every 8th step; the batch members do not, so the two agree to float rounding only
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 5e-6)])
 @pytest.mark.parametrize("graph", [True, False])
 def test_batch_matches_single_contexts(precision, tol, graph):
