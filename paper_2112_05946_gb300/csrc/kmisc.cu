@@ -96,11 +96,13 @@ __host__ __device__ inline LimLayout lim_layout(int TE, int N1, int dim, int M, 
 // exact test and the limiting in FP64: mean, eps = min(1e-8, rho_bar, p_bar), beta_1 for the
 // density (Eq. 50), beta_2 = the smallest root of p(ubar + beta (u* - ubar)) = eps over the
 // points (Eq. 51), and the modal scaling uhat <- ubar e_0 + beta (uhat - ubar e_0) written back.
-template <typename T, int N1, int DIM, int S>
+// MC, QC: the mode and z-node counts when fixed at compile time (0: taken from A), so that the
+// screen's loops unroll and its index arithmetic folds for the common shapes.
+template <typename T, int N1, int DIM, int S, int MC = 0, int QC = 0>
 __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntiles) {
     constexpr int NL = DIM == 2 ? N1 : 1;
     constexpr int NPT = DIM == 2 ? N1 * N1 : N1;
-    const int Q = A.Q, M = A.M, TE = A.TE;
+    const int Q = QC ? QC : A.Q, M = MC ? MC : A.M, TE = A.TE;
     const int tq = threadIdx.x, tl = threadIdx.y, te = threadIdx.z;
     const int nel = Q * NL;                         // threads per element
     const int lt = tl * Q + tq;                     // thread within its element
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
             for (int a = 0; a < N1; ++a)
 #pragma unroll
                 for (int s = 0; s < S; ++s) v[a][s] = T(0);
+#pragma unroll
             for (int k = 0; k < M; ++k) {
                 const T vz = sVz[k * Q + tq];
 #pragma unroll
@@ -590,7 +593,7 @@ int grid_for(size_t n, int threads) {
 
 // Tile: as many elements as fit 256 threads (Q z-nodes x lines per element), at most 100 KB of
 // shared memory per CTA; persistent grid: the CTAs resident at once, at most one per tile.
-template <typename T, int N1, int DIM, int S>
+template <typename T, int N1, int DIM, int S, int MC = 0, int QC = 0>
 cudaError_t limit_typed(const LimitArgs& Ain, cudaStream_t st) {
     LimitArgs A = Ain;
     const int nel = A.Q * (DIM == 2 ? N1 : 1);
@@ -599,7 +602,7 @@ cudaError_t limit_typed(const LimitArgs& Ain, cudaStream_t st) {
     while (TE > 1 && lim_layout(TE, N1, DIM, A.M, A.Q, S, (int)sizeof(T)).total > 100 * 1024) --TE;
     A.TE = TE;
     const size_t smem = lim_layout(TE, N1, DIM, A.M, A.Q, S, (int)sizeof(T)).total;
-    auto kern = limit_kernel<T, N1, DIM, S>;
+    auto kern = limit_kernel<T, N1, DIM, S, MC, QC>;
     const int threads = nel * TE;
     // occupancy query cached per instantiation, device and launch shape (a stage launches this)
     thread_local int c_dev = -1, c_threads = -1, c_grid = 0;
@@ -629,18 +632,24 @@ cudaError_t limit_typed(const LimitArgs& Ain, cudaStream_t st) {
 
 template <typename T>
 cudaError_t limit_np(const LimitArgs& A, cudaStream_t st) {
+    // compiled-in mode and z-node counts for the shapes of the stage kernels' specialisations:
+    // 1D P = 3 Euler with N = 6, Q = 12 and 2D P = 3 with N = 4, Q = 8
     if (A.dim == 1) {
         switch (A.Np) {
             case 2: return limit_typed<T, 2, 1, 3>(A, st);
             case 3: return limit_typed<T, 3, 1, 3>(A, st);
-            case 4: return limit_typed<T, 4, 1, 3>(A, st);
+            case 4:
+                if (A.M == 7 && A.Q == 12) return limit_typed<T, 4, 1, 3, 7, 12>(A, st);
+                return limit_typed<T, 4, 1, 3>(A, st);
             case 5: return limit_typed<T, 5, 1, 3>(A, st);
         }
     } else {
         switch (A.Np) {
             case 4: return limit_typed<T, 2, 2, 4>(A, st);
             case 9: return limit_typed<T, 3, 2, 4>(A, st);
-            case 16: return limit_typed<T, 4, 2, 4>(A, st);
+            case 16:
+                if (A.M == 5 && A.Q == 8) return limit_typed<T, 4, 2, 4, 5, 8>(A, st);
+                return limit_typed<T, 4, 2, 4>(A, st);
         }
     }
     return cudaErrorInvalidValue;
