@@ -307,14 +307,19 @@ __device__ __noinline__ T lasso_value(const T* me, const T* sVf, const T* sNorm,
 // (replayed and recorded decisions); record: store the decision in A.flags; dst: where the
 // element's final coefficients go (global memory, or back over Us).
 // FSHFL: sum float energies with warp shuffles as well (see below).
-template <typename T, int NP, int S, bool FSHFL = false>
+// WARP: the element's nlt threads are exactly one warp (nlt == 32, lane-aligned), and the
+// caller's barrier before this call is warp-local too: the energies are summed by a full
+// butterfly, every lane takes the decision, and the passes are separated by __syncwarp only
+// (Mod of element te then starts at te * mod_stride, inside the element's own scratch).  Not
+// for the Lasso filter (1D only).
+template <typename T, int NP, int S, bool FSHFL = false, bool WARP = false>
 __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T* Mod, const T* sVf, const T* sVfinv,
                                              const T* sLam, const T* sTop, T* sRed, int* sFlag, int te, int kl,
                                              int nk, int ml, int nm, bool active, bool member, int e, bool record,
-                                             T* dst, T det, int M) {
+                                             T* dst, T det, int M, int mod_stride = 0) {
     const int elsz = NP * M * S;
     const T* ue = Us + te * elsz;
-    T* me = Mod + te * elsz;
+    T* me = Mod + (size_t)te * (WARP ? mod_stride : elsz);
     T tot = T(0), top = T(0);
     // pass A0: modal coefficients of variable 0 for every element; its energies
     if (active) {
@@ -330,6 +335,69 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
         }
     }
     const int lt = ml * nk + kl, nlt = nk * nm;
+    if constexpr (WARP) {
+        // one warp per element: butterfly sums in every lane, the decision in every lane
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            top += __shfl_xor_sync(0xffffffffu, top, o);
+        }
+        int fl = 0;
+        if (active) {
+            if (A.replay) fl = A.replay[e] ? 1 : 0;
+            else if (!A.sensor) fl = 1;
+            else fl = (top > T(0) && top > det * tot) ? 1 : 0;
+            if (A.flags && record && lt == 0) A.flags[e] = (uint8_t)fl;
+        }
+        if constexpr (S > 1) {
+            if (active && fl) {
+                for (PairWalk w(lt, nlt, M); w.r < NP; w.next()) {
+                    const int m = w.r, k = w.k;
+                    T acc[S];
+#pragma unroll
+                    for (int s = 1; s < S; ++s) acc[s] = T(0);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const T vi = sVfinv[m * NP + j];
+#pragma unroll
+                        for (int s = 1; s < S; ++s) acc[s] += vi * ue[(j * M + k) * S + s];
+                    }
+#pragma unroll
+                    for (int s = 1; s < S; ++s) me[(m * M + k) * S + s] = acc[s];
+                }
+            }
+        }
+        __syncwarp();
+        bool bad = false;
+        if (active) {
+            for (PairWalk w(lt, nlt, M); w.r < NP; w.next()) {
+                const int j = w.r, k = w.k;
+                const int o = (j * M + k) * S;
+                T val[S];
+                if (fl) {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) val[s] = T(0);
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) {
+                        const T wv = sVf[j * NP + m] * sLam[m * M + k];
+                        T x[S];
+                        ldv<T, S>(me + (m * M + k) * S, x);
+#pragma unroll
+                        for (int s = 0; s < S; ++s) val[s] += wv * x[s];
+                    }
+                } else {
+                    ldv<T, S>(ue + o, val);
+                }
+                stv<T, S>(dst + o, val);
+#pragma unroll
+                for (int s = 0; s < S; ++s) bad |= !finite_val(val[s]);
+            }
+        }
+        (void)sRed;
+        (void)sFlag;
+        (void)member;
+        return bad;
+    }
     // Energy sums over the element's nlt threads.  The element's threads are consecutive in
     // the block (thread te*nlt + lt), so when nlt is a power of two and the block is whole
     // warps, a group is a lane-aligned piece of a warp (nlt <= 32) or whole warps: shuffle

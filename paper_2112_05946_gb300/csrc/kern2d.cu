@@ -149,6 +149,10 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     uint32_t* sTmem = reinterpret_cast<uint32_t*>(sBar + 2);
     uint64_t* sTileBar = sBar + 3;
     const int warp = tid >> 5, lane = tid & 31;
+    // an element's threads are one warp when Q N1 == 32 (the CUDA-core form of the compiled-in
+    // shape): from the x-sweep on, every phase touches only the element's own rows, residual,
+    // tile and scratch, and its face sums are warp shuffles, so warp-local syncs order them
+    constexpr bool kWarpElem = !TC && QC * N1 == 32;
     const uint32_t kTmemCols = TE <= 4 ? 32 : 64;   // TE/2 tiles x 16 columns (a power of two >= 32)
 
     const T* tab = table_block<T>(A);
@@ -453,7 +457,8 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
 #pragma unroll
         for (int s = 0; s < S; ++s) cF0[s] = cF1[s] = 0.f;
     }
-    __syncthreads();
+    if constexpr (kWarpElem) __syncwarp();
+    else __syncthreads();
 
     // ---- y-sweep on column a = tl
     if (active) {
@@ -526,7 +531,8 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
         }
     }
     if constexpr (TC) fence_async_shared();   // the operand stores, to the tensor cores
-    __syncthreads();
+    if constexpr (kWarpElem) __syncwarp();
+    else __syncthreads();
 
     // ---- projection + SSP combination
     const T ca = sK.ca, cb = sK.cb, cc = sK.cc;
@@ -606,12 +612,20 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
                                          acc_term<T>(A, gbase + (size_t)te * elsz, sK));
     }
     if (A.do_filter) {
-        __syncthreads();
-        // TC: the G operand is free again (the MMAs have completed) and holds the modal scratch
-        T* mod = TC ? reinterpret_cast<T*>(sAh) : sG;
-        bad = detector_filter_store<T, NP, S>(A, sTile, mod, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tl, N1,
-                                              active, true, e0 + te, true,
-                                              uout + gbase + (size_t)te * elsz, sK.det, M) || bad;
+        if constexpr (kWarpElem) {
+            __syncwarp();
+            bad = detector_filter_store<T, NP, S, false, true>(A, sTile, sG, sVf, sVfinv, sLam, sTop, sRed, sFlag, te,
+                                                               tq, Q, tl, N1, active, true, e0 + te, true,
+                                                               uout + gbase + (size_t)te * elsz, sK.det, M,
+                                                               NP * GR) || bad;
+        } else {
+            __syncthreads();
+            // TC: the G operand is free again (the MMAs have completed) and holds the modal scratch
+            T* mod = TC ? reinterpret_cast<T*>(sAh) : sG;
+            bad = detector_filter_store<T, NP, S>(A, sTile, mod, sVf, sVfinv, sLam, sTop, sRed, sFlag, te, tq, Q, tl,
+                                                  N1, active, true, e0 + te, true,
+                                                  uout + gbase + (size_t)te * elsz, sK.det, M) || bad;
+        }
     }
     if (bad) atomicOr(A.err, kErrNonFinite);
     if constexpr (TC) {
