@@ -176,6 +176,13 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph);
  * errors as fr_sg_rk_step. */
 frsg_status fr_sg_advance(frsg_ctx* ctx, const double* uhat_in, double* uhat_out, int where, double dt, int nsteps,
                           int use_graph);
+/* fr_sg_advance with the arrays in the context's own precision: double for FRSG_FP64, float
+ * [E][Np][M][S] for FRSG_FP32 and FRSG_FP32_TC.  The same steps; a float context moves half
+ * the bytes over the host link (it rounds a double input to float anyway, and widening its
+ * float state to double is exact, so nothing is lost).  Host arrays go through the copy
+ * engines (pinned ones without staging).  Errors as fr_sg_advance. */
+frsg_status fr_sg_advance_native(frsg_ctx* ctx, const void* uhat_in, void* uhat_out, int where, double dt, int nsteps,
+                                 int use_graph);
 
 /* Advance the context's state by nsteps steps of size dt of the classical four-stage
  * Runge-Kutta scheme (the integrator of the advection study, §5.1 setup table):

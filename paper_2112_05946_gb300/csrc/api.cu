@@ -1074,6 +1074,25 @@ frsg_status fr_sg_advance(frsg_ctx* ctx, const double* uhat_in, double* uhat_out
     return FRSG_OK;
 }
 
+frsg_status fr_sg_advance_native(frsg_ctx* ctx, const void* uhat_in, void* uhat_out, int where, double dt, int nsteps,
+                                 int use_graph) {
+    if (!ctx) return FRSG_E_INVAL;
+    if (!uhat_in || !uhat_out) return fail(ctx, FRSG_E_INVAL, "null state");
+    if (where != FRSG_HOST && where != FRSG_DEVICE) return fail(ctx, FRSG_E_INVAL, "where must be HOST or DEVICE");
+    if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
+    const size_t bytes = ctx->esz * (size_t)ctx->E * ctx->Np * ctx->M * ctx->S;
+    const bool host = where == FRSG_HOST;
+    ctx->mean_valid = false;   // the state is written directly: re-anchor its FP64 means
+    CK(cudaMemcpyAsync(ctx->d_u, uhat_in, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    const frsg_status st = fr_sg_rk_step(ctx, dt, nsteps, use_graph);
+    if (st != FRSG_OK) return st;
+    CK(cudaMemcpyAsync(uhat_out, ctx->d_u, bytes, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    if (host) CK(cudaStreamSynchronize(ctx->stream));
+    return FRSG_OK;
+}
+
 frsg_status fr_sg_rk4_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     if (!ctx) return FRSG_E_INVAL;
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");

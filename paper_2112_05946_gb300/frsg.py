@@ -73,6 +73,8 @@ _SIGNATURES = [
     ("fr_sg_rk4_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_advance", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_int, ctypes.c_int]),
+    ("fr_sg_advance_native", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     ("fr_sg_tune_cache_save", ctypes.c_int, [ctypes.c_char_p]),
     ("fr_sg_tune_cache_load", ctypes.c_int, [ctypes.c_char_p]),
     ("fr_sg_project", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -331,6 +333,27 @@ class Solver:
                                     1 if graph else 0)
         if st != OK:
             self._ck(st, "advance")
+        return u_out
+
+    def advance_native(self, u_in, u_out, dt, nsteps=1, graph=True):
+        """fr_sg_advance_native: as advance, with the arrays in the context's own precision
+        (float64 for fp64, float32 for the float forms); numpy arrays (host, synchronous) or
+        contiguous CUDA tensors, of the state's size."""
+        host = isinstance(u_in, np.ndarray)
+        if host != isinstance(u_out, np.ndarray):
+            raise TypeError("u_in and u_out must both be host arrays or both device tensors")
+        n = self.E * self.Np * self.M * self.S
+        want = "float64" if self.fp64 else "float32"
+        for a in (u_in, u_out):
+            if host:
+                ok = str(a.dtype) == want and a.flags.c_contiguous and a.size == n
+            else:
+                ok = a.is_cuda and str(a.dtype) == "torch." + want and a.is_contiguous() and a.numel() == n
+            if not ok:
+                raise ValueError(f"states must be contiguous {want} arrays of {n} values")
+        pin, pout = (u_in.ctypes.data, u_out.ctypes.data) if host else (_ptr(u_in), _ptr(u_out))
+        self._ck(self.lib.fr_sg_advance_native(self.h, pin, pout, HOST if host else DEVICE, float(dt), int(nsteps),
+                                               1 if graph else 0), "advance_native")
         return u_out
 
     def project(self, u0, uhat):

@@ -71,3 +71,40 @@ def test_advance_rejects_bad_arguments_and_keeps_the_state():
     with pytest.raises(frsg.FrsgError):
         s.advance(u + 1.0, out, 1e-3, -1)
     np.testing.assert_array_equal(s.get_state(), u)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_advance_native_equals_advance(precision):
+    """fr_sg_advance_native with arrays in the form's own precision gives the state fr_sg_advance
+    gives (a float form rounds a double input to float anyway; widening back is exact)."""
+    import torch
+    wl = workloads.burgers_1d(nx=40)
+    prob = oracle_problem(wl, nx=40)
+    dt = 0.1 * prob.dx / 1.2
+    s = solver(wl, precision=precision)
+    u = _front(s, seed=9)
+    ref = np.empty_like(u)
+    s.advance(u, ref, dt, 3)
+    dt_np = np.float64 if precision == "fp64" else np.float32
+    un = u.astype(dt_np)
+    out = np.empty_like(un)
+    s.advance_native(un, out, dt, 3)
+    s.check()
+    np.testing.assert_array_equal(out.astype(np.float64), ref)
+    # pinned host memory and device tensors, in place
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    pin = torch.tensor(un).pin_memory()
+    s.advance_native(pin.numpy(), pin.numpy(), dt, 3)
+    np.testing.assert_array_equal(pin.numpy().astype(np.float64), ref)
+    dev = torch.tensor(un, device="cuda")
+    s.advance_native(dev, dev, dt, 3)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dev.cpu().numpy().astype(np.float64), ref)
+    # the other precision, or a short array, is rejected before any call
+    wrong = u.astype(np.float32 if precision == "fp64" else np.float64)
+    with pytest.raises(ValueError):
+        s.advance_native(wrong, np.empty_like(wrong), dt, 1)
+    with pytest.raises(ValueError):
+        s.advance_native(un[:-1], out[:-1], dt, 1)
+    assert tdt is not None
+    s.close()
