@@ -228,7 +228,7 @@ __device__ inline AccTerm<T> acc_term(const StageArgs& A, size_t off, const Stag
 template <typename T, int NP, int S, bool ACC>
 __device__ inline bool project_combine_impl(const T* G, int gr, const T* U, const T* B, const T* sPz, T* dst, int M,
                                             int Q, int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
-                                            const AccTerm<T>& X) {
+                                            const AccTerm<T>& X, T* dst2) {
     bool bad = false;
     for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
         const int j = w.r, k = w.k;
@@ -254,6 +254,7 @@ __device__ inline bool project_combine_impl(const T* G, int gr, const T* U, cons
                 for (int s = 0; s < S; ++s) val[s] += ca * bo[s];
             }
             stv<T, S>(dst + o, val);
+            if (dst2) stv<T, S>(dst2 + o, val);
 #pragma unroll
             for (int s = 0; s < S; ++s) bad |= !finite_val(val[s]);
             if constexpr (ACC) {
@@ -272,12 +273,12 @@ __device__ inline bool project_combine_impl(const T* G, int gr, const T* U, cons
 template <typename T, int NP, int S>
 __device__ inline bool project_combine(const T* G, int gr, const T* U, const T* B, const T* sPz, T* dst, int M, int Q,
                                        int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
-                                       const AccTerm<T>& X) {
+                                       const AccTerm<T>& X, T* dst2 = nullptr) {
     if (X.dst)
         return project_combine_impl<T, NP, S, true>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base,
-                                                    X);
+                                                    X, dst2);
     return project_combine_impl<T, NP, S, false>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base,
-                                                 X);
+                                                 X, dst2);
 }
 
 // One Lasso-filtered nodal coefficient (§4.1.3) of a 1D element from its modal coefficients
@@ -310,8 +311,9 @@ __device__ __noinline__ T lasso_value(const T* me, const T* sVf, const T* sNorm,
 // WARP: the element's nlt threads are exactly one warp (nlt == 32, lane-aligned), and the
 // caller's barrier before this call is warp-local too: the energies are summed by a full
 // butterfly, every lane takes the decision, and the passes are separated by __syncwarp only
-// (Mod of element te then starts at te * mod_stride, inside the element's own scratch).  Not
-// for the Lasso filter (1D only).
+// (Mod of element te then starts at te * mod_stride, inside the element's own scratch).  The
+// caller has stored every element's unfiltered coefficients to dst as well as to Us: only
+// flagged elements are written again.  Not for the Lasso filter (1D only).
 template <typename T, int NP, int S, bool FSHFL = false, bool WARP = false>
 __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T* Mod, const T* sVf, const T* sVfinv,
                                              const T* sLam, const T* sTop, T* sRed, int* sFlag, int te, int kl,
@@ -369,24 +371,22 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
         }
         __syncwarp();
         bool bad = false;
-        if (active) {
+        // the caller stored the unfiltered coefficients to dst already: only a flagged element
+        // writes again
+        if (active && fl) {
             for (PairWalk w(lt, nlt, M); w.r < NP; w.next()) {
                 const int j = w.r, k = w.k;
                 const int o = (j * M + k) * S;
                 T val[S];
-                if (fl) {
 #pragma unroll
-                    for (int s = 0; s < S; ++s) val[s] = T(0);
+                for (int s = 0; s < S; ++s) val[s] = T(0);
 #pragma unroll
-                    for (int m = 0; m < NP; ++m) {
-                        const T wv = sVf[j * NP + m] * sLam[m * M + k];
-                        T x[S];
-                        ldv<T, S>(me + (m * M + k) * S, x);
+                for (int m = 0; m < NP; ++m) {
+                    const T wv = sVf[j * NP + m] * sLam[m * M + k];
+                    T x[S];
+                    ldv<T, S>(me + (m * M + k) * S, x);
 #pragma unroll
-                        for (int s = 0; s < S; ++s) val[s] += wv * x[s];
-                    }
-                } else {
-                    ldv<T, S>(ue + o, val);
+                    for (int s = 0; s < S; ++s) val[s] += wv * x[s];
                 }
                 stv<T, S>(dst + o, val);
 #pragma unroll

@@ -604,12 +604,16 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
         }
         tc_fence_before_sync();
     } else if (active) {
-        T* dst = A.do_filter ? sTile + te * elsz : uout + gbase + (size_t)te * elsz;
+        // warp-local epilogue: the new state goes out at once and stays in the tile for the
+        // detector (which rewrites flagged elements only); otherwise to the tile, then out
+        const bool out_now = !A.do_filter || kWarpElem;
+        T* dst = out_now ? uout + gbase + (size_t)te * elsz : sTile + te * elsz;
+        T* dst2 = A.do_filter && kWarpElem ? sTile + te * elsz : nullptr;
         // the SSP base is read once, straight from global memory
         const T* base = sK.use_base ? ubase + gbase + (size_t)te * elsz : nullptr;
         bad |= project_combine<T, NP, S>(sG + te * NP * GR, GR, sTile + te * elsz, base, sPz, dst, M, Q, tq,
                                          Q, tl, N1, ca, cb, cc, sK.use_base != 0,
-                                         acc_term<T>(A, gbase + (size_t)te * elsz, sK));
+                                         acc_term<T>(A, gbase + (size_t)te * elsz, sK), dst2);
     }
     if (A.do_filter) {
         if constexpr (kWarpElem) {
