@@ -225,7 +225,7 @@ __device__ inline AccTerm<T> acc_term(const StageArgs& A, size_t off, const Stag
 // so that threads on different points hit different banks); U, B its stage input and SSP
 // base [NP][M][S].
 // Writes the result to dst (shared memory or global), and the accumulator X if ACC.
-template <typename T, int NP, int S, bool ACC>
+template <typename T, int NP, int S, bool ACC, bool QS>
 __device__ inline bool project_combine_impl(const T* G, int gr, const T* U, const T* B, const T* sPz, T* dst, int M,
                                             int Q, int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
                                             const AccTerm<T>& X, T* dst2) {
@@ -239,8 +239,15 @@ __device__ inline bool project_combine_impl(const T* G, int gr, const T* U, cons
             const T* g = G + j * gr;
             for (int q = 0; q < Q; ++q) {
                 const T pz = sPz[k * Q + q];
+                if constexpr (QS) {
+                    T gv[S];
+                    ldv<T, S>(g + q * S, gv);
 #pragma unroll
-                for (int s = 0; s < S; ++s) acc[s] += pz * g[s * Q + q];
+                    for (int s = 0; s < S; ++s) acc[s] += pz * gv[s];
+                } else {
+#pragma unroll
+                    for (int s = 0; s < S; ++s) acc[s] += pz * g[s * Q + q];
+                }
             }
             const int o = (j * M + k) * S;
             T uo[S], val[S];
@@ -270,15 +277,17 @@ __device__ inline bool project_combine_impl(const T* G, int gr, const T* U, cons
     return bad;
 }
 
-template <typename T, int NP, int S>
+// QS: the residual rows hold [q][s] (the S variables of a z-node together, read as one vector);
+// otherwise [s][q].
+template <typename T, int NP, int S, bool QS = false>
 __device__ inline bool project_combine(const T* G, int gr, const T* U, const T* B, const T* sPz, T* dst, int M, int Q,
                                        int kl, int nk, int ml, int nm, T ca, T cb, T cc, bool use_base,
                                        const AccTerm<T>& X, T* dst2 = nullptr) {
     if (X.dst)
-        return project_combine_impl<T, NP, S, true>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base,
-                                                    X, dst2);
-    return project_combine_impl<T, NP, S, false>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc, use_base,
-                                                 X, dst2);
+        return project_combine_impl<T, NP, S, true, QS>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc,
+                                                        use_base, X, dst2);
+    return project_combine_impl<T, NP, S, false, QS>(G, gr, U, B, sPz, dst, M, Q, kl, nk, ml, nm, ca, cb, cc,
+                                                     use_base, X, dst2);
 }
 
 // One Lasso-filtered nodal coefficient (§4.1.3) of a 1D element from its modal coefficients

@@ -52,7 +52,7 @@ __host__ __device__ inline size_t smem2d_elems(int TE, int n1, int M, int Q, int
     if (tc)                                 // G as the MMA operand, tf32 part and remainder; Pz^T likewise
         n += (2 * tc_a_bytes(TE, Np, S) + 2 * (size_t)kTcN * 8 * sizeof(float)) / sizeof(T);
     else                                    // G (nodal residual, rows padded; later modal coefficients)
-        n += ((size_t)TE * Np * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;
+        n += ((size_t)TE * Np * (S * (Q > M ? Q : M) + (sizeof(T) == 4 ? 4 : 0)) + 3) & ~(size_t)3;
     n += (size_t)(TE + 2) * 2 * n1 * S * Q; // x-face traces [row][side][b][q][s]
     n += 2 * (size_t)M * Q;                 // Vz, Pz
     n += (size_t)n1 * n1 + 4 * n1;          // D, lm, lp, dhL, dhR
@@ -112,14 +112,17 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     T* sU = p; p += (size_t)TE * elsz;
     T* sFT = p; p += (size_t)(2 + 2 * TE) * N1 * M * S;   // [face][line][k][s]
     T* sUn = p; p += (size_t)TE * NP * S * Q;            // [te][point][q][s]
-    const int GR = S * Q + (sizeof(T) == 4 ? 1 : 0);   // row stride of the nodal residual (float: padded)
+    // row stride of the nodal residual [te][point][q][s] (the S variables of one z-node together,
+    // so that a thread moves them with one vector access; float rows padded by 4 words, which
+    // keeps them 16-byte aligned and spreads consecutive points over the banks)
+    const int GR = S * (Q > M ? Q : M) + (sizeof(T) == 4 ? 4 : 0);
     T* sG = p;                                         // CUDA-core projection: [te][point][GR]
     unsigned char* sAh = reinterpret_cast<unsigned char*>(p);   // TC: G, tf32 part / float remainder
     unsigned char* sAl = sAh + tc_a_bytes(TE, NP, S);
     float* sBh = reinterpret_cast<float*>(sAl + tc_a_bytes(TE, NP, S));   // TC: Pz^T, tf32 part / remainder
     float* sBl = sBh + kTcN * 8;
     if constexpr (TC) p += (2 * tc_a_bytes(TE, NP, S) + 2 * (size_t)kTcN * 8 * sizeof(float)) / sizeof(T);
-    else p += ((size_t)TE * NP * (S * (Q > M ? Q : M) + 1) + 3) & ~(size_t)3;
+    else p += ((size_t)TE * NP * (S * (Q > M ? Q : M) + (sizeof(T) == 4 ? 4 : 0)) + 3) & ~(size_t)3;
     // element (row, q) of the G operand: row = (te * NP + j) * S + s
     auto g_at = [&](unsigned char* base, int row, int q) -> float* {
         return reinterpret_cast<float*>(base + kmajor_offset(row, q, kTcLboA, kTcSboA));
@@ -432,15 +435,18 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             }
         const T invJ = sK.invJx;
 #pragma unroll
-        for (int a = 0; a < N1; ++a)
+        for (int a = 0; a < N1; ++a) {
+            T dv[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 T d = (fIL[s] - fDL[s]) * sdhL[a] + (fIR[s] - fDR[s]) * sdhR[a];
 #pragma unroll
                 for (int m = 0; m < N1; ++m) d += sD[a * N1 + m] * f[m][s];
-                if constexpr (TC) *g_at(sAh, (te * NP + b * N1 + a) * S + s, tq) = -invJ * d;
-                else sG[(te * NP + b * N1 + a) * GR + s * Q + tq] = -invJ * d;
+                dv[s] = -invJ * d;
+                if constexpr (TC) *g_at(sAh, (te * NP + b * N1 + a) * S + s, tq) = dv[s];
             }
+            if constexpr (!TC) stv<T, S>(sG + (size_t)(te * NP + b * N1 + a) * GR + tq * S, dv);
+        }
     }
     if (mean64) {
         // the element owns its left face; the element at a non-periodic right end also its right
@@ -499,7 +505,10 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             }
         const T invJ = sK.invJy;
 #pragma unroll
-        for (int b = 0; b < N1; ++b)
+        for (int b = 0; b < N1; ++b) {
+            T* grow = sG + (size_t)(te * NP + b * N1 + a) * GR + tq * S;
+            T gx[S];
+            if constexpr (!TC) ldv<T, S>(grow, gx);
 #pragma unroll
             for (int s = 0; s < S; ++s) {
                 T d = (gIB[s] - gDB[s]) * sdhL[b] + (gIT[s] - gDT[s]) * sdhR[b];
@@ -513,9 +522,11 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
                     *g_at(sAh, row, tq) = hi;
                     *g_at(sAl, row, tq) = gv - hi;
                 } else {
-                    sG[(te * NP + b * N1 + a) * GR + s * Q + tq] -= invJ * d;
+                    gx[s] -= invJ * d;
                 }
             }
+            if constexpr (!TC) stv<T, S>(grow, gx);
+        }
     }
     if (mean64) {
         // the element owns its bottom face; the top row of a non-periodic mesh also its top face
@@ -611,7 +622,7 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
         T* dst2 = A.do_filter && kWarpElem ? sTile + te * elsz : nullptr;
         // the SSP base is read once, straight from global memory
         const T* base = sK.use_base ? ubase + gbase + (size_t)te * elsz : nullptr;
-        bad |= project_combine<T, NP, S>(sG + te * NP * GR, GR, sTile + te * elsz, base, sPz, dst, M, Q, tq,
+        bad |= project_combine<T, NP, S, true>(sG + te * NP * GR, GR, sTile + te * elsz, base, sPz, dst, M, Q, tq,
                                          Q, tl, N1, ca, cb, cc, sK.use_base != 0,
                                          acc_term<T>(A, gbase + (size_t)te * elsz, sK), dst2);
     }
