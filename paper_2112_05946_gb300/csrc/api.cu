@@ -298,6 +298,14 @@ StageArgs base_args(frsg_ctx* c) {
     A.s0 = c->cfg.s0;
     A.kappa = c->cfg.kappa;
     A.det_ratio = frsg::detector_ratio(c->cfg.s0, c->cfg.kappa);
+    if (!c->fp64 && c->n1 <= 5 && !c->htab.empty()) {
+        const int n1 = c->n1;
+        int o = 0;
+        for (int i = 0; i < n1 * n1; ++i) A.frf[o++] = (float)c->htab[c->off.D + i];
+        const int offs[4] = {c->off.lm, c->off.lp, c->off.dhL, c->off.dhR};
+        for (int t = 0; t < 4; ++t)
+            for (int i = 0; i < n1; ++i) A.frf[o++] = (float)c->htab[offs[t] + i];
+    }
     A.err = c->d_err;
     A.TE = stage_tile(c);
     A.wide = (c->wide == 1 || c->wide == 3) ? 1 : 0;

@@ -82,6 +82,9 @@ struct StageArgs {
     double* mbar;
     const float* wmean;
     int mshift;
+    // float forms: the element's FR tables D (N1 x N1), lm, lp, dhL, dhR (N1 each), in that order,
+    // for N1 <= 5 (filled on the host; the 2D kernel reads them as kernel parameters)
+    float frf[45];
     // optional second output of the same residual (the RK4 weighted sum of the L's):
     // acc_out = acc_a*acc_in + acc_b*uin + acc_c*dt*L(uin), unfiltered; null = none
     void* acc_out;

@@ -89,7 +89,7 @@ __device__ inline void face_eval(const T* ft, int M, const T* Vzq_stride, int Q,
 // Blocks hold at most 512 threads.  Float builds are held to 80 registers: with about 35 KB of
 // shared memory per 4-element CTA that lets six CTAs share an SM (at 86 registers, five).
 template <typename T, int N1, int S, int MC = 0, int QC = 0, bool TC = false>
-__global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const StageArgs A) {
+__global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const __grid_constant__ StageArgs A) {
     static_assert(!TC || (sizeof(T) == 4 && N1 == 4 && S == 4 && QC == 8 && MC > 0 && MC <= 8),
                   "the tensor-core projection is built for float, P = 3, four variables, Q = 8, M <= 8");
     constexpr int NP = N1 * N1;
@@ -156,6 +156,20 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
     // shape): from the x-sweep on, every phase touches only the element's own rows, residual,
     // tile and scratch, and its face sums are warp shuffles, so warp-local syncs order them
     constexpr bool kWarpElem = !TC && QC * N1 == 32;
+    // the FR tables of the sweeps: float forms read them as kernel parameters (constant-bank
+    // operands, the same values as the float table block), double forms from shared memory
+    const T* cD = sD;
+    const T* clm = slm;
+    const T* clp = slp;
+    const T* cdhL = sdhL;
+    const T* cdhR = sdhR;
+    if constexpr (sizeof(T) == 4 && N1 <= 5) {
+        cD = A.frf;
+        clm = A.frf + N1 * N1;
+        clp = clm + N1;
+        cdhL = clp + N1;
+        cdhR = cdhL + N1;
+    }
     const uint32_t kTmemCols = TE <= 4 ? 32 : 64;   // TE/2 tiles x 16 columns (a power of two >= 32)
 
     const T* tab = table_block<T>(A);
@@ -331,8 +345,8 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             T l = T(0), r = T(0);
 #pragma unroll
             for (int a = 0; a < N1; ++a) {
-                l += slm[a] * u[a][s];
-                r += slp[a] * u[a][s];
+                l += clm[a] * u[a][s];
+                r += clp[a] * u[a][s];
             }
             tL[s] = l;
             tR[s] = r;
@@ -413,10 +427,10 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             T l = T(0), r = T(0), ul = T(0), ur = T(0);
 #pragma unroll
             for (int a = 0; a < N1; ++a) {
-                l += slm[a] * f[a][s];
-                r += slp[a] * f[a][s];
-                ul += slm[a] * u[a][s];
-                ur += slp[a] * u[a][s];
+                l += clm[a] * f[a][s];
+                r += clp[a] * f[a][s];
+                ul += clm[a] * u[a][s];
+                ur += clp[a] * u[a][s];
             }
             fDL[s] = l;
             fDR[s] = r;
@@ -439,9 +453,9 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             T dv[S];
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                T d = (fIL[s] - fDL[s]) * sdhL[a] + (fIR[s] - fDR[s]) * sdhR[a];
+                T d = (fIL[s] - fDL[s]) * cdhL[a] + (fIR[s] - fDR[s]) * cdhR[a];
 #pragma unroll
-                for (int m = 0; m < N1; ++m) d += sD[a * N1 + m] * f[m][s];
+                for (int m = 0; m < N1; ++m) d += cD[a * N1 + m] * f[m][s];
                 dv[s] = -invJ * d;
                 if constexpr (TC) *g_at(sAh, (te * NP + b * N1 + a) * S + s, tq) = dv[s];
             }
@@ -481,10 +495,10 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             T l = T(0), r = T(0), ul = T(0), ur = T(0);
 #pragma unroll
             for (int b = 0; b < N1; ++b) {
-                l += slm[b] * g[b][s];
-                r += slp[b] * g[b][s];
-                ul += slm[b] * v[b][s];
-                ur += slp[b] * v[b][s];
+                l += clm[b] * g[b][s];
+                r += clp[b] * g[b][s];
+                ul += clm[b] * v[b][s];
+                ur += clp[b] * v[b][s];
             }
             gDB[s] = l;
             gDT[s] = r;
@@ -511,9 +525,9 @@ __global__ void __maxnreg__(sizeof(T) == 4 ? 80 : 128) stage2d_kernel(const Stag
             if constexpr (!TC) ldv<T, S>(grow, gx);
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                T d = (gIB[s] - gDB[s]) * sdhL[b] + (gIT[s] - gDT[s]) * sdhR[b];
+                T d = (gIB[s] - gDB[s]) * cdhL[b] + (gIT[s] - gDT[s]) * cdhR[b];
 #pragma unroll
-                for (int m = 0; m < N1; ++m) d += sD[b * N1 + m] * g[m][s];
+                for (int m = 0; m < N1; ++m) d += cD[b * N1 + m] * g[m][s];
                 if constexpr (TC) {
                     // the final residual, split into its tf32 part and the float remainder
                     const int row = (te * NP + b * N1 + a) * S + s;
