@@ -237,14 +237,31 @@ __device__ inline bool project_combine_impl(const T* G, int gr, const T* U, cons
 #pragma unroll
             for (int s = 0; s < S; ++s) acc[s] = T(0);
             const T* g = G + j * gr;
-            for (int q = 0; q < Q; ++q) {
-                const T pz = sPz[k * Q + q];
-                if constexpr (QS) {
+            if (QS && (Q & 3) == 0) {
+                // four z-nodes' weights per vector load (Q a multiple of 4: the caller's weight
+                // rows and residual rows are then 16-byte aligned)
+                for (int q0 = 0; q0 < Q; q0 += 4) {
+                    T pz[4];
+                    ldv<T, 4>(sPz + k * Q + q0, pz);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        T gv[S];
+                        ldv<T, S>(g + (q0 + qq) * S, gv);
+#pragma unroll
+                        for (int s = 0; s < S; ++s) acc[s] += pz[qq] * gv[s];
+                    }
+                }
+            } else if (QS) {
+                for (int q = 0; q < Q; ++q) {
+                    const T pz = sPz[k * Q + q];
                     T gv[S];
                     ldv<T, S>(g + q * S, gv);
 #pragma unroll
                     for (int s = 0; s < S; ++s) acc[s] += pz * gv[s];
-                } else {
+                }
+            } else {
+                for (int q = 0; q < Q; ++q) {
+                    const T pz = sPz[k * Q + q];
 #pragma unroll
                     for (int s = 0; s < S; ++s) acc[s] += pz * g[s * Q + q];
                 }
@@ -337,8 +354,19 @@ __device__ inline bool detector_filter_store(const StageArgs& A, const T* Us, T*
         for (PairWalk w(ml * nk + kl, nk * nm, M); w.r < NP; w.next()) {
             const int m = w.r, k = w.k;
             T acc = T(0);
+            if constexpr (WARP && NP % 4 == 0) {
+                // the transform's row as vector loads (rows 16-byte aligned)
 #pragma unroll
-            for (int j = 0; j < NP; ++j) acc += sVfinv[m * NP + j] * ue[(j * M + k) * S];
+                for (int j0 = 0; j0 < NP; j0 += 4) {
+                    T vi[4];
+                    ldv<T, 4>(sVfinv + m * NP + j0, vi);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) acc += vi[jj] * ue[((j0 + jj) * M + k) * S];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NP; ++j) acc += sVfinv[m * NP + j] * ue[(j * M + k) * S];
+            }
             me[(m * M + k) * S] = acc;
             const T v2 = acc * acc;
             tot += v2;
