@@ -230,11 +230,9 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
             visit(fL);
             visit(fR);
             if constexpr (DIM == 2) {
+                // a point's S values together: one vector store each
 #pragma unroll
-                for (int a = 0; a < N1; ++a)
-#pragma unroll
-                    for (int s = 0; s < S; ++s)
-                        sRow[(((size_t)te * NPT + row * N1 + a) * Q + tq) * S + s] = v[a][s];
+                for (int a = 0; a < N1; ++a) stv<T, S>(sRow + (((size_t)te * NPT + row * N1 + a) * Q + tq) * S, v[a]);
             }
         }
         if constexpr (DIM == 2) {
@@ -244,16 +242,16 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
                 const int a = tl;   // column
                 T fB[S], fT[S];
 #pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    T l = T(0), r = T(0);
+                for (int s = 0; s < S; ++s) fB[s] = fT[s] = T(0);
 #pragma unroll
-                    for (int b = 0; b < N1; ++b) {
-                        const T x = sRow[(((size_t)te * NPT + b * N1 + a) * Q + tq) * S + s];
-                        l += lmT[b] * x;
-                        r += lpT[b] * x;
+                for (int b = 0; b < N1; ++b) {
+                    T x[S];
+                    ldv<T, S>(sRow + (((size_t)te * NPT + b * N1 + a) * Q + tq) * S, x);
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        fB[s] += lmT[b] * x[s];
+                        fT[s] += lpT[b] * x[s];
                     }
-                    fB[s] = l;
-                    fT[s] = r;
                 }
                 visit(fB);
                 visit(fT);
