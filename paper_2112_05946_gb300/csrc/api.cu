@@ -402,6 +402,7 @@ cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
     L.err = c->d_err;
     L.dim = c->cfg.dim;
     L.TE = c->TE_lim;
+    frsg::fill_limit_tables(L, c->htab.data());
     c->launches += 1;
     return frsg::launch_limit(c->fp64, L, c->stream);
 }

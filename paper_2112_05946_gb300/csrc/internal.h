@@ -121,7 +121,24 @@ struct LimitArgs {
     unsigned* err;
     int dim;
     int TE;
+    // ell(-1) (N1), ell(+1) (N1) and the weights w_j / 2^dim of the element mean (N1^dim), read
+    // by the kernel as parameters: in float for the screen of a float state, in double for the
+    // exact pass and double states (fill_limit_tables)
+    float frl[2 * 5 + 25];
+    double frd[2 * 5 + 25];
 };
+
+// The parameter tables of LimitArgs from a host copy of the table block (L.off, L.Np, L.dim set).
+inline void fill_limit_tables(LimitArgs& L, const double* htab) {
+    const int n1 = L.dim == 2 ? (L.Np == 4 ? 2 : L.Np == 9 ? 3 : L.Np == 16 ? 4 : 5) : L.Np;
+    const int npt = L.dim == 2 ? n1 * n1 : n1;
+    for (int j = 0; j < n1 && j < 5; ++j) {
+        L.frd[j] = htab[L.off.lm + j];
+        L.frd[n1 + j] = htab[L.off.lp + j];
+    }
+    for (int j = 0; j < npt && j < 25; ++j) L.frd[2 * n1 + j] = htab[L.off.w + j];
+    for (int j = 0; j < 2 * 5 + 25; ++j) L.frl[j] = (float)L.frd[j];
+}
 
 // Launch with programmatic stream serialization allowed (the kernel calls pdl_trigger /
 // pdl_wait, see epilogue.cuh): the launch may begin while the previous kernel in the stream

@@ -59,7 +59,7 @@ constexpr int kLimStages = 3;   // tiles in flight per CTA of the limiter
 // Shared-memory layout of limit_kernel: kLimStages barriers and tiles, then the scratch of one
 // tile's screen and exact pass, then Vz.
 struct LimLayout {
-    size_t tile, row, red, el, eps, flag, vz, total;
+    size_t tile, row, red, el, eps, flag, vz, cz, dp, total;
 };
 __host__ __device__ inline LimLayout lim_layout(int TE, int N1, int dim, int M, int Q, int S, int tsz) {
     const int NPT = dim == 2 ? N1 * N1 : N1, nel = Q * (dim == 2 ? N1 : 1);
@@ -79,7 +79,9 @@ __host__ __device__ inline LimLayout lim_layout(int TE, int N1, int dim, int M, 
     L.flag = o;
     o += (size_t)TE * sizeof(int);
     L.vz = a16(o);
-    L.total = L.vz + (size_t)M * Q * tsz;
+    L.cz = L.vz + a16((size_t)M * Q * tsz);
+    L.dp = L.cz + (tsz == 8 ? a16((size_t)(M + 1) * tsz) : 0);
+    L.total = L.dp + (tsz == 8 ? (size_t)TE * NPT * 2 * S * tsz : 0);
     return L;
 }
 
@@ -92,14 +94,17 @@ __host__ __device__ inline LimLayout lim_layout(int TE, int N1, int dim, int M, 
 // the CTA screens one tile while the copy engine fetches the next ones.
 // Screen in the state's precision T over every element; for T = float with a margin of 1e-4
 // of the mean density and energy above eps, far above float rounding, so that a cleared element
-// is admissible and untriggered in exact arithmetic.  Elements the screen cannot clear get the
+// is admissible and untriggered in exact arithmetic.  Double states first bound rho and p over
+// all z-nodes from the gPC modes (the z-spread of each point, the faces' values through
+// ell(+-1)), which clears smooth elements without their z-nodal evaluation; the z-nodal screen
+// then runs for the rest.  Elements the screens cannot clear get the
 // exact test and the limiting in FP64: mean, eps = min(1e-8, rho_bar, p_bar), beta_1 for the
 // density (Eq. 50), beta_2 = the smallest root of p(ubar + beta (u* - ubar)) = eps over the
 // points (Eq. 51), and the modal scaling uhat <- ubar e_0 + beta (uhat - ubar e_0) written back.
 // MC, QC: the mode and z-node counts when fixed at compile time (0: taken from A), so that the
 // screen's loops unroll and its index arithmetic folds for the common shapes.
 template <typename T, int N1, int DIM, int S, int MC = 0, int QC = 0>
-__global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntiles) {
+__global__ void __launch_bounds__(256) limit_kernel(const __grid_constant__ LimitArgs A, int ntiles) {
     constexpr int NL = DIM == 2 ? N1 : 1;
     constexpr int NPT = DIM == 2 ? N1 * N1 : N1;
     const int Q = QC ? QC : A.Q, M = MC ? MC : A.M, TE = A.TE;
@@ -122,24 +127,44 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
     double* sEps = reinterpret_cast<double*>(lsm + L.eps);   // [TE][2]: density / pressure targets
     int* sFlag = reinterpret_cast<int*>(lsm + L.flag);       // [TE]: 1 candidate, 2 admissible, 4 limited
     T* sVz = reinterpret_cast<T*>(lsm + L.vz);               // [M][Q]
+    T* sCz = reinterpret_cast<T*>(lsm + L.cz);               // [M + 1]: z-bounds of the modes
+    T* sDp = reinterpret_cast<T*>(lsm + L.dp);               // [TE][point][2][S]: scales, z-spreads
 
     const double* tab = A.tab;
     const double gamma = A.gamma;
     const T* tabT = sizeof(T) == 4 && A.tabf ? reinterpret_cast<const T*>(A.tabf) : reinterpret_cast<const T*>(tab);
     const bool tab_is_T = sizeof(T) == 8 || A.tabf != nullptr;
     auto tabv = [&](int i) -> T { return tab_is_T ? tabT[i] : (T)tab[i]; };
-    T lmT[N1], lpT[N1], wT[NPT];
-    double lmD[N1], lpD[N1];
-#pragma unroll
-    for (int j = 0; j < N1; ++j) {
-        lmT[j] = tabv(A.off.lm + j);
-        lpT[j] = tabv(A.off.lp + j);
-        lmD[j] = tab[A.off.lm + j];
-        lpD[j] = tab[A.off.lp + j];
-    }
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) wT[j] = tabv(A.off.w + j);
+    // ell(-1), ell(+1) and the mean's weights are kernel parameters (constant-bank operands,
+    // no registers held through the kernel)
+    auto lmT = [&](int a) -> T {
+        if constexpr (sizeof(T) == 4) return A.frl[a];
+        else return A.frd[a];
+    };
+    auto lpT = [&](int a) -> T {
+        if constexpr (sizeof(T) == 4) return A.frl[N1 + a];
+        else return A.frd[N1 + a];
+    };
+    auto wT = [&](int j) -> T {
+        if constexpr (sizeof(T) == 4) return A.frl[2 * N1 + j];
+        else return A.frd[2 * N1 + j];
+    };
+    auto lmD = [&](int a) -> double { return A.frd[a]; };
+    auto lpD = [&](int a) -> double { return A.frd[N1 + a]; };
     for (int i = tid; i < M * Q; i += nthr) sVz[i] = tabv(A.off.VzT + i);
+    // the bound screen runs for double states, where it saves most of the z-nodal screen's FP64
+    // work; for float states the z-nodal screen alone measured faster (its cost there is the
+    // tile pipeline's, not its arithmetic's)
+    constexpr bool kBound = sizeof(T) == 8;
+    // sCz[0] = min_q Phi_0(z_q), sCz[M] = max_q Phi_0(z_q), sCz[k] = max_q |Phi_k(z_q)| (0 < k < M)
+    for (int k = tid; kBound && k <= M; k += nthr) {
+        T c = k == 0 ? T(1e30) : (k == M ? T(-1e30) : T(0));
+        for (int q = 0; q < Q; ++q) {
+            const T v = tabv(A.off.VzT + (k == M ? 0 : k) * Q + q);
+            c = k == 0 ? fmin(c, v) : (k == M ? fmax(c, v) : fmax(c, fabs(v)));
+        }
+        sCz[k] = c;
+    }
     T* u = static_cast<T*>(A.u);
     // one bulk copy per tile when every tile starts on a 16-byte boundary
     const bool bulk = ((size_t)elsz * sizeof(T)) % 16 == 0 && (reinterpret_cast<uintptr_t>(u) & 15) == 0;
@@ -188,14 +213,158 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
             __syncthreads();
         }
 
-        // ---- screen in T
+        const T* ue = sU + (size_t)te * elsz;
+        // the element mean over r (and s) and z: sum_j (w_j / 2^d) uhat_{j,0} (Phi_0 = 1); the
+        // screen's reductions and decision stay in T (double arithmetic is slow on this part)
+        T* sElT = reinterpret_cast<T*>(sEl);
+        T* sRedT = reinterpret_cast<T*>(sRed);
+        T mean_s = T(0);
+        auto take_mean = [&]() {
+            if (active && lt < S) {
+#pragma unroll
+                for (int j = 0; j < NPT; ++j) mean_s += wT(j) * ue[(size_t)j * M * S + lt];
+                if (!in_warp) sElT[te * 8 + lt] = mean_s;
+            }
+        };
+        // the mean in thread lt == 0 (in every lane of the element when it is one warp), after a
+        // barrier that follows take_mean
+        T ub[S];
+        const int base = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) % 32 - lt;
+        auto gather_mean = [&]() {
+            if (in_warp) {
+                // the element's lanes start at lane (lane - lt): its first S lanes hold the mean
+#pragma unroll
+                for (int s = 0; s < S; ++s) ub[s] = __shfl_sync(0xffffffffu, mean_s, base + s);
+            } else if (active && lt == 0) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) ub[s] = sElT[te * 8 + s];
+            }
+        };
+        T pb = T(0);
+        bool clear = false;
+        if constexpr (kBound) {
+            take_mean();
+
+            // ---- bound screen in T: lower bounds of rho and p over all z-nodes at every point of
+            // the element.  At a solution point j the z-spread of variable s is
+            // D_js = sum_{k>0} c_k |uhat_jks| with c_k = max_q |Phi_k(z_q)|, so its values lie in
+            // uhat_j0s Phi_0(z_q) +- D_js; a face value sum_a ell_a u_a (ell = ell(-1) or ell(+1)
+            // along the face's line) lies in T0 Phi_0(z_q) +- sum_a |ell_a| D_as with
+            // T0 = sum_a ell_a uhat_a0s.  From the bounds of rho, E and |m|:
+            // p >= (gamma - 1) (E_lo - |m|_hi^2 / (2 rho_lo)) where rho_lo > 0.  kap widens every
+            // bound by far more than the rounding of its sums.  An element whose bounds clear the
+            // margins of the z-nodal screen below is admissible and untriggered in exact arithmetic;
+            // that screen then runs for the other elements only.
+            const T kap = exact ? T(1e-10) : T(1e-5);
+            constexpr int NF = DIM == 2 ? 4 * N1 : 2;   // face points
+            T rlo = T(1e30), plo = T(1e30);
+            const T c0lo = sCz[0], c0hi = sCz[M], c0abs = fmax(fabs(c0lo), fabs(c0hi));
+            T* sDe = sDp + (size_t)te * NPT * 2 * S;   // [point][|uhat_0| c0abs + D, D] of this element
+            // one point's bounds from its mode-0 value t0 (a point value or a face's T0), its spread
+            // dd and the scale hh >= every term's magnitude (of the rounding)
+            auto point_bound = [&](const T (&t0)[S], const T (&dd)[S], const T (&hh)[S]) {
+                T lo[S], up[S];   // lower bounds, and upper bounds of the magnitudes
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const T w = kap * hh[s];
+                    lo[s] = t0[s] * (t0[s] >= T(0) ? c0lo : c0hi) - dd[s] - w;
+                    up[s] = fabs(t0[s]) * c0abs + dd[s] + w;
+                }
+                T m2 = T(0);
+#pragma unroll
+                for (int d = 1; d < S - 1; ++d) m2 += up[d] * up[d];
+                const T r = lo[0], en = lo[S - 1];
+                T pp = T(-1e30);
+                if (r > T(0)) {
+                    T kin;
+                    if constexpr (sizeof(T) == 4) kin = __fdividef(0.5f * m2, r);
+                    else kin = T(0.5) * m2 / r;
+                    pp = g1 * (en - kin - kap * (fabs(en) + kin));
+                }
+                // a NaN anywhere keeps the element out of the cleared set
+                rlo = fmin(rlo, r == r ? r : T(-1e30));
+                plo = fmin(plo, pp == pp ? pp : T(-1e30));
+            };
+            if (active) {
+                for (int pt = lt; pt < NPT; pt += nel) {
+                    T t0[S], dd[S], hh[S];
+                    ldv<T, S>(ue + (size_t)pt * M * S, t0);
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2) dd[s2] = T(0);
+#pragma unroll
+                    for (int k = 1; k < M; ++k) {
+                        T x[S];
+                        ldv<T, S>(ue + ((size_t)pt * M + k) * S, x);
+                        const T c = sCz[k];
+#pragma unroll
+                        for (int s2 = 0; s2 < S; ++s2) dd[s2] += c * fabs(x[s2]);
+                    }
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2) hh[s2] = fabs(t0[s2]) * c0abs + dd[s2];
+                    point_bound(t0, dd, hh);
+                    stv<T, S>(sDe + (size_t)pt * 2 * S, hh);
+                    stv<T, S>(sDe + (size_t)pt * 2 * S + S, dd);
+                }
+            }
+            if (in_warp) __syncwarp();
+            else __syncthreads();
+            if (active) {
+                for (int f = lt; f < NF; f += nel) {
+                    // 1D side 0 / 1 (r = -1 / +1); 2D side 0 / 1 the x-faces of row b = fi, side
+                    // 2 / 3 the y-faces of column a = fi
+                    const int side = DIM == 2 ? f / N1 : f, fi = DIM == 2 ? f % N1 : 0;
+                    const bool plus = (side & 1) != 0;
+                    T t0[S], dd[S], hh[S];
+#pragma unroll
+                    for (int s2 = 0; s2 < S; ++s2) t0[s2] = dd[s2] = hh[s2] = T(0);
+#pragma unroll
+                    for (int a = 0; a < N1; ++a) {
+                        const int j = DIM == 1 ? a : (side < 2 ? fi * N1 + a : a * N1 + fi);
+                        const T la = plus ? lpT(a) : lmT(a), al = fabs(la);
+                        T x[S], h[S], d[S];
+                        ldv<T, S>(ue + (size_t)j * M * S, x);
+                        ldv<T, S>(sDe + (size_t)j * 2 * S, h);
+                        ldv<T, S>(sDe + (size_t)j * 2 * S + S, d);
+#pragma unroll
+                        for (int s2 = 0; s2 < S; ++s2) {
+                            t0[s2] += la * x[s2];
+                            dd[s2] += al * d[s2];
+                            hh[s2] += al * h[s2];
+                        }
+                    }
+                    point_bound(t0, dd, hh);
+                }
+            }
+            const T rb = element_min<T>(rlo, te, lt, nel, pow2, sRedT);
+            const T pbd = element_min<T>(plo, te, lt, nel, pow2, sRedT);
+            gather_mean();
+            if (active && lt == 0) {
+                pb = pressure_t<T, S>(ub, g1);
+                if (exact) {
+                    const T eps_e = fmin(T(1e-8), fmin(ub[0], pb));
+                    clear = ub[0] > T(0) && pb > T(0) && rb >= eps_e && pbd >= eps_e;
+                } else {
+                    const T mr = T(1e-4) * fabs(ub[0]), me = T(1e-4) * fabs(ub[S - 1]);
+                    clear = ub[0] > mr && pb > me && rb >= T(1e-8) + mr && pbd >= T(1e-8) + me;
+                }
+            }
+            if (in_warp) {
+                clear = __shfl_sync(0xffffffffu, clear, base);
+            } else {
+                if (active && lt == 0) sFlag[te] = clear ? 1 : 0;
+                __syncthreads();
+                clear = active && sFlag[te] != 0;
+            }
+        }
+        const bool scr = active && !clear;
+
+        // ---- z-nodal screen in T, for the elements the bounds did not clear
         T rmin = T(1e30), pmin = T(1e30);
         auto visit = [&](const T (&w)[S]) {
             rmin = fmin(rmin, w[0]);
             pmin = fmin(pmin, pressure_t<T, S>(w, g1));
         };
-        const T* ue = sU + (size_t)te * elsz;
-        if (active) {
+        if (scr) {
             const int row = DIM == 2 ? tl : 0;
             T v[N1][S];
 #pragma unroll
@@ -219,8 +388,8 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
                 T l = T(0), r = T(0);
 #pragma unroll
                 for (int a = 0; a < N1; ++a) {
-                    l += lmT[a] * v[a][s];
-                    r += lpT[a] * v[a][s];
+                    l += lmT(a) * v[a][s];
+                    r += lpT(a) * v[a][s];
                 }
                 fL[s] = l;
                 fR[s] = r;
@@ -238,7 +407,7 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
         if constexpr (DIM == 2) {
             if (in_warp) __syncwarp();
             else __syncthreads();
-            if (active) {
+            if (scr) {
                 const int a = tl;   // column
                 T fB[S], fT[S];
 #pragma unroll
@@ -249,48 +418,31 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
                     ldv<T, S>(sRow + (((size_t)te * NPT + b * N1 + a) * Q + tq) * S, x);
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
-                        fB[s] += lmT[b] * x[s];
-                        fT[s] += lpT[b] * x[s];
+                        fB[s] += lmT(b) * x[s];
+                        fT[s] += lpT(b) * x[s];
                     }
                 }
                 visit(fB);
                 visit(fT);
             }
         }
-        // the element mean over r (and s) and z: sum_j (w_j / 2^d) uhat_{j,0} (Phi_0 = 1); the
-        // screen's reductions and decision stay in T (double arithmetic is slow on this part)
-        T* sElT = reinterpret_cast<T*>(sEl);
-        T mean_s = T(0);
-        if (active && lt < S) {
-#pragma unroll
-            for (int j = 0; j < NPT; ++j) mean_s += wT[j] * ue[(size_t)j * M * S + lt];
-            if (!in_warp) sElT[te * 8 + lt] = mean_s;
-        }
-        T* sRedT = reinterpret_cast<T*>(sRed);
+        if constexpr (!kBound) take_mean();
         const T rm = element_min<T>(rmin, te, lt, nel, pow2, sRedT);
         const T pm = element_min<T>(pmin, te, lt, nel, pow2, sRedT);
-        T ub[S];
-        if (in_warp) {
-            // the element's lanes start at lane (lane - lt): gather the mean from its first S lanes
-            const int base = (int)(threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) % 32 - lt;
-#pragma unroll
-            for (int s = 0; s < S; ++s) ub[s] = __shfl_sync(0xffffffffu, mean_s, base + s);
-        }
+        if constexpr (!kBound) gather_mean();
         if (active && lt == 0) {
-            if (!in_warp) {
-#pragma unroll
-                for (int s = 0; s < S; ++s) ub[s] = sElT[te * 8 + s];
+            if constexpr (!kBound) pb = pressure_t<T, S>(ub, g1);
+            bool c = false;
+            if (!clear) {
+                if (exact) {
+                    const T eps_e = fmin(T(1e-8), fmin(ub[0], pb));
+                    c = !(ub[0] > T(0) && pb > T(0)) || rm < eps_e || pm < eps_e;
+                } else {
+                    const T mr = T(1e-4) * fabs(ub[0]), me = T(1e-4) * fabs(ub[S - 1]);
+                    c = !(ub[0] > mr && pb > me) || rm < T(1e-8) + mr || pm < T(1e-8) + me;
+                }
+                c = c || !(rm == rm) || !(pm == pm) || !(pb == pb);
             }
-            const T pb = pressure_t<T, S>(ub, g1);
-            bool c;
-            if (exact) {
-                const T eps_e = fmin(T(1e-8), fmin(ub[0], pb));
-                c = !(ub[0] > T(0) && pb > T(0)) || rm < eps_e || pm < eps_e;
-            } else {
-                const T mr = T(1e-4) * fabs(ub[0]), me = T(1e-4) * fabs(ub[S - 1]);
-                c = !(ub[0] > mr && pb > me) || rm < T(1e-8) + mr || pm < T(1e-8) + me;
-            }
-            c = c || !(rm == rm) || !(pm == pm) || !(pb == pb);
             sFlag[te] = c ? 1 : 0;
         }
         // one barrier publishes the decisions and tells whether any element needs the exact pass
@@ -325,8 +477,8 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
                     double l = 0.0, r = 0.0;
 #pragma unroll
                     for (int a = 0; a < N1; ++a) {
-                        l += lmD[a] * vd[a][s];
-                        r += lpD[a] * vd[a][s];
+                        l += lmD(a) * vd[a][s];
+                        r += lpD(a) * vd[a][s];
                     }
                     fL[s] = l;
                     fR[s] = r;
@@ -342,8 +494,8 @@ __global__ void __launch_bounds__(256) limit_kernel(const LimitArgs A, int ntile
                         double l = 0.0, r = 0.0;
 #pragma unroll
                         for (int b = 0; b < N1; ++b) {
-                            l += lmD[b] * vd[b][s];
-                            r += lpD[b] * vd[b][s];
+                            l += lmD(b) * vd[b][s];
+                            r += lpD(b) * vd[b][s];
                         }
                         fL[s] = l;
                         fR[s] = r;

@@ -324,6 +324,7 @@ extern "C" frsg_status fr_sg_rk_step_noalloc(const frsg_config* cfg, const doubl
                 L.err = d_err;
                 L.dim = 1;
                 L.TE = 256 / Q > 0 ? 256 / Q : 1;
+                fill_limit_tables(L, g_host_tab);
                 if (launch_limit(true, L, st) != cudaSuccess) return finish(FRSG_E_CUDA);
             }
             A.uin = bin[s];
