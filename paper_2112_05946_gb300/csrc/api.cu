@@ -369,7 +369,7 @@ frsg::MeanArgs mean_args(frsg_ctx* c) {
 
 // After stage s (buffers in = s, out = s + 1 mod 3): mbar_out = a mbar_0 + b mbar_in + c dt mean(L);
 // in the last stage of a shifting step the output state's mean mode also moves onto mbar_out.
-cudaError_t launch_stage_mean(frsg_ctx* c, int s, double a, double b, double cc) {
+frsg::MeanArgs stage_mean_args(frsg_ctx* c, int s, double a, double b, double cc) {
     frsg::MeanArgs M = mean_args(c);
     void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
     M.u = static_cast<float*>(bufs_out[s]);
@@ -382,11 +382,16 @@ cudaError_t launch_stage_mean(frsg_ctx* c, int s, double a, double b, double cc)
     M.c[0] = cc;
     M.nst = 1;
     M.shift = s == 2 && c->shift_now;
-    c->launches += 1;
-    return frsg::launch_mean64(M, c->stream);
+    return M;
 }
 
-cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
+cudaError_t launch_stage_mean(frsg_ctx* c, int s, double a, double b, double cc) {
+    c->launches += 1;
+    return frsg::launch_mean64(stage_mean_args(c, s, a, b, cc), c->stream);
+}
+
+// fold: the mean update of the stage that wrote u, done by the limiter's CTAs (null: none)
+cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta, const frsg::MeanArgs* fold = nullptr) {
     LimitArgs L{};
     L.u = u;
     L.E = c->E;
@@ -403,6 +408,10 @@ cudaError_t launch_limiter(frsg_ctx* c, void* u, double* beta) {
     L.dim = c->cfg.dim;
     L.TE = c->TE_lim;
     frsg::fill_limit_tables(L, c->htab.data());
+    if (fold) {
+        L.mean_fold = 1;
+        L.mean = *fold;
+    }
     c->launches += 1;
     return frsg::launch_limit(c->fp64, L, c->stream);
 }
@@ -439,14 +448,20 @@ cudaError_t issue_stage_ex(frsg_ctx* c, int s, double dt, uint8_t* flags_out, co
     return e;
 }
 
-cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
+// fold_prev: the limiter of this stage also does the FP64 mean update of stage s - 1 (float
+// forms; that stage deferred it); defer_mean: leave this stage's mean update to the next
+// stage's limiter.
+cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay, bool fold_prev = false,
+                        bool defer_mean = false) {
     const bool filt = c->cfg.filter != FRSG_FILTER_NONE;
     void* bufs_in[3] = {c->d_u, c->d_u1, c->d_u2};
     void* bufs_out[3] = {c->d_u1, c->d_u2, c->d_u};
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
     const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
     if (c->cfg.limiter) {
-        cudaError_t e = launch_limiter(c, bufs_in[s], c->d_beta + (size_t)s * c->E);
+        frsg::MeanArgs fm{};
+        if (fold_prev) fm = stage_mean_args(c, s - 1, ca[s - 1], cb[s - 1], cb[s - 1]);
+        cudaError_t e = launch_limiter(c, bufs_in[s], c->d_beta + (size_t)s * c->E, fold_prev ? &fm : nullptr);
         if (e != cudaSuccess) return e;
     }
     StageArgs A = base_args(c);
@@ -467,9 +482,13 @@ cudaError_t issue_stage(frsg_ctx* c, int s, double dt, bool use_replay) {
     }
     A.fface = mean64(c) ? c->d_ff : nullptr;
     cudaError_t e = launch_stage(c, A);
-    if (e == cudaSuccess && mean64(c)) e = launch_stage_mean(c, s, ca[s], cb[s], cb[s]);
+    if (e == cudaSuccess && mean64(c) && !defer_mean) e = launch_stage_mean(c, s, ca[s], cb[s], cb[s]);
     return e;
 }
+
+// Whether an SSP step folds the FP64 mean updates of stages 0 and 1 into the limiters of stages 1
+// and 2 (float forms with the limiter; the last stage's update, which may shift, keeps its launch).
+bool fold_means(const frsg_ctx* c) { return mean64(c) && c->cfg.limiter; }
 
 cudaError_t set_dt(frsg_ctx* c, double dt) {
     if (dt == c->dt_set) return cudaSuccess;
@@ -562,8 +581,9 @@ cudaError_t issue_step(frsg_ctx* c, double dt, bool use_replay) {
         cudaError_t e = frsg::launch_step1d(c->cfg, c->fp64, A3, c->d_bar, nullptr, c->stream);
         return e == cudaSuccess ? step_mean() : e;
     }
+    const bool fold = fold_means(c);
     for (int s = 0; s < 3; ++s) {
-        cudaError_t e = issue_stage(c, s, dt, use_replay);
+        cudaError_t e = issue_stage(c, s, dt, use_replay, fold && s > 0, fold && s < 2);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -983,7 +1003,8 @@ frsg_status fr_sg_rk_step(frsg_ctx* ctx, double dt, int nsteps, int use_graph) {
     if (!ctx) return FRSG_E_INVAL;
     if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, FRSG_E_INVAL, "need dt > 0, nsteps >= 0");
     const int kernels_per_step = one_launch_step(ctx) ? 1 + (mean64(ctx) && ctx->wide == 2 ? 1 : 0)
-                                                      : 3 * (1 + (ctx->cfg.limiter ? 1 : 0) + (mean64(ctx) ? 1 : 0));
+                                                      : 3 * (1 + (ctx->cfg.limiter ? 1 : 0) + (mean64(ctx) ? 1 : 0)) -
+                                                            (fold_means(ctx) ? 2 : 0);
     if (nsteps == 0) return FRSG_OK;
     CK(set_dt(ctx, dt));
     CK(anchor_means(ctx));

@@ -110,6 +110,27 @@ inline void prepare_float_scalars(StageArgs& A) {
     A.fxc = (float)A.acc_c;
 }
 
+// FP64 cell means of mode 0 for the float forms (§4.1: the filter keeps the mean, Lambda_00 = 1;
+// §4.3: the limiter scales about it).  nst stages of one step, stage s of coefficients
+// (a[s], b[s], c[s] dt): mbar_{s+1} = a[s] mbar_0 + b[s] mbar_s + c[s] dt mean(L_s), mean(L_s) the
+// flux difference of the owned face values F[s] (telescoping: each face has one value); then the
+// float state's mode 0 is shifted per element and variable so that its mean is mbar_nst.
+struct MeanArgs {
+    float* u;              // float state [E][Np][M][S] after the stage(s), shifted in place
+    const double* mbar0;   // [E][S] means of the step's input u^n (the SSP base)
+    const double* mbar_in; // [E][S] means of the stage input (nst == 1; null: mbar0)
+    double* mbar_out;      // [E][S] means of u (may be mbar0 or mbar_in: read before written)
+    const float* F[3];     // face values of each stage (layout of StageArgs::fface)
+    double a[3], b[3], c[3];
+    const double* dtp;     // device step size
+    int nst, E, nx, ny, dim, Np, M, S;
+    int xper, yper;
+    int shift;             // 1: also shift the float mode 0 of u to the new means (one pass over
+                           // the state's mean mode); 0: update the FP64 means only
+    double invJx, invJy;
+    const float* wf;       // float table: w_j / 2^dim at the solution points
+};
+
 struct LimitArgs {
     void* u;               // state limited in place
     int E, M, Q, S, Np;
@@ -126,6 +147,10 @@ struct LimitArgs {
     // exact pass and double states (fill_limit_tables)
     float frl[2 * 5 + 25];
     double frd[2 * 5 + 25];
+    // float forms: the FP64 mean update of the stage that wrote u (nst == 1, no shift), done by
+    // the limiter's CTAs for their tiles' elements instead of by a mean64 launch
+    int mean_fold;
+    MeanArgs mean;
 };
 
 // The parameter tables of LimitArgs from a host copy of the table block (L.off, L.Np, L.dim set).
@@ -253,26 +278,6 @@ double detector_ratio(double s0, double kappa);
 
 cudaError_t launch_convert(const void* src, void* dst, size_t n, bool to_float, cudaStream_t st);
 
-// FP64 cell means of mode 0 for the float forms (§4.1: the filter keeps the mean, Lambda_00 = 1;
-// §4.3: the limiter scales about it).  nst stages of one step, stage s of coefficients
-// (a[s], b[s], c[s] dt): mbar_{s+1} = a[s] mbar_0 + b[s] mbar_s + c[s] dt mean(L_s), mean(L_s) the
-// flux difference of the owned face values F[s] (telescoping: each face has one value); then the
-// float state's mode 0 is shifted per element and variable so that its mean is mbar_nst.
-struct MeanArgs {
-    float* u;              // float state [E][Np][M][S] after the stage(s), shifted in place
-    const double* mbar0;   // [E][S] means of the step's input u^n (the SSP base)
-    const double* mbar_in; // [E][S] means of the stage input (nst == 1; null: mbar0)
-    double* mbar_out;      // [E][S] means of u (may be mbar0 or mbar_in: read before written)
-    const float* F[3];     // face values of each stage (layout of StageArgs::fface)
-    double a[3], b[3], c[3];
-    const double* dtp;     // device step size
-    int nst, E, nx, ny, dim, Np, M, S;
-    int xper, yper;
-    int shift;             // 1: also shift the float mode 0 of u to the new means (one pass over
-                           // the state's mean mode); 0: update the FP64 means only
-    double invJx, invJy;
-    const float* wf;       // float table: w_j / 2^dim at the solution points
-};
 cudaError_t launch_mean64(const MeanArgs& A, cudaStream_t st);
 // mbar[e][s] = sum_j (w_j / 2^dim) u[e][j][0][s] in double from a float (fp64 = false) or double
 // state: the anchor after a write of the state, and the means of a double state
