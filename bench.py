@@ -361,6 +361,19 @@ def set_initial(s, wl):
         s.set_initial_nodal(workloads.nodal_values(wl["ic"], nodes[0], nodes[2], nodes[1]))
 
 
+def autotune_on(s, wl, dt, limit=False):
+    """Autotune on the workload's own state and step size (the tuner times steps from the
+    context's state with its last step size), then restart from the initial state."""
+    set_initial(s, wl)
+    if limit:
+        s.limit()
+    s.rk_step(dt, 1, graph=False)
+    set_initial(s, wl)
+    if limit:
+        s.limit()
+    return s.autotune()
+
+
 def time_steps(torch, s, stream, flush, dt, steps, warmup, rk4=False, refresh=None):
     """Per-step CUDA events over `steps` graph-replayed steps after `warmup`, L2 flushed before
     each; refresh(i) may return a new dt (outside the events).  Returns (ms list, launches)."""
@@ -443,7 +456,8 @@ def measure_headline(torch, frsg, precision, args, stream, flush, peaks, oracle_
     E, Np, M, S = workload_sizes(wl)
     dof = E * Np * M * S
     s = new_solver(frsg, wl, stream, precision)
-    variant, tile = s.autotune()
+    set_initial(s, wl)
+    variant, tile = autotune_on(s, wl, s.cfl_dt(CFL_2D))
     set_initial(s, wl)
 
     def refresh(i, dt):
@@ -516,8 +530,11 @@ def measure_1d(torch, frsg, wl, precision, steps, warmup, stream, flush, peaks, 
     E, Np, M, S = workload_sizes(wl)
     dof = E * Np * M * S
     s = new_solver(frsg, wl, stream, precision)
-    variant, tile = s.autotune()
     lim = bool(wl["solver"].get("limiter"))
+    set_initial(s, wl)
+    if lim or limit_first:
+        s.limit()
+    variant, tile = autotune_on(s, wl, fixed_dt if fixed_dt is not None else s.cfl_dt(cfl), limit=lim or limit_first)
     # accuracy first, from the projected initial state, with the oracle's step size
     ref_dt, ref_u, nref = ref
     set_initial(s, wl)
@@ -924,12 +941,13 @@ def run_only(args):
         out = {}
         for p in ("fp64", "fp32") + (("fp32_tc",) if args.only == "shock_vortex" else ()):
             s = new_solver(frsg, wl, stream, p)
-            variant, tile = s.autotune()
+            lim = bool(wl["solver"].get("limiter"))
             set_initial(s, wl)
-            if wl["solver"].get("limiter"):
+            if lim:
                 s.limit()
             dt = s.cfl_dt(CFL_2D if wl["solver"].get("dim", 1) == 2 else 0.05) if wl["lam0"] is None else (
                 wl["cfl"] * (wl["solver"]["x1"] - wl["solver"]["x0"]) / wl["solver"]["nx"] / wl["lam0"])
+            variant, tile = autotune_on(s, wl, dt, limit=lim)
             ms, launches, _ = time_steps(torch, s, stream, flush, dt, args.steps, args.warmup)
             s.check()
             s.close()

@@ -354,12 +354,14 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant);
 frsg_status fr_sg_test_fused_wait(frsg_ctx* ctx, long long wait_cycles, int hold_tile);
 
 /* Autotuner: times graph-replayed SSP-RK3 steps (reps per candidate, default 20; CUDA
- * events on the context's stream) for every layout (1D) and tile that fits, re-times the
- * three fastest in five interleaved rounds, keeps the best and caches the choice per
+ * events on the context's stream around each step, the L2 cache overwritten before it, so that
+ * every candidate reads its state from HBM) for every layout (1D) and tile that fits, re-times
+ * the three fastest in five interleaved rounds, keeps the best and caches the choice per
  * (dim, P, N, Q, S, precision, elements, filter, equation, interface flux, limiter) for the
- * process.  A cached shape is not re-timed.  Saves and restores the state (one temporary
- * device allocation); overwrites the stage buffers and the decision rows; replayed decisions
- * are not consumed.  Synchronises.  variant_out / te_out (may be NULL) receive the choice. */
+ * process.  A cached shape is not re-timed.  Saves and restores the state (two temporary
+ * device allocations: the state and twice the L2 size); overwrites the stage buffers and the
+ * decision rows; replayed decisions are not consumed.  Synchronises.  variant_out / te_out
+ * (may be NULL) receive the choice. */
 frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_out);
 
 /* Write the process-wide autotuner cache to a text file (one line per problem shape), or

@@ -1426,22 +1426,34 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
     CK(cudaMalloc(&saved, nbytes));
     CK(cudaMemcpyAsync(saved, ctx->d_u, nbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void* flush = nullptr;
     // releases the scratch and restores the replay rows on every return path
     struct Scope {
         frsg_ctx* c;
         void* buf;
+        void** fl;
         cudaEvent_t* a;
         cudaEvent_t* b;
         int rows;
         ~Scope() {
             cudaFree(buf);
+            if (*fl) cudaFree(*fl);
             if (*a) cudaEventDestroy(*a);
             if (*b) cudaEventDestroy(*b);
             c->replay_rows = rows;
         }
-    } scope{ctx, saved, &ev0, &ev1, ctx->replay_rows};
+    } scope{ctx, saved, &flush, &ev0, &ev1, ctx->replay_rows};
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
+    // each timed step starts with the L2 cache overwritten (a buffer of twice its size), so that
+    // the candidates are compared with the state coming from HBM, as in a benchmark that flushes
+    // between steps; back-to-back steps of a small problem would otherwise run from L2, where
+    // several candidates are within noise of each other
+    int dev = 0, l2 = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    const size_t flush_bytes = 2 * (size_t)(l2 > 0 ? l2 : 64 << 20);
+    CK(cudaMalloc(&flush, flush_bytes));
     ctx->replay_rows = 0;                 // tuning steps never consume replayed decisions
     // candidates: layout x tile that fit
     std::vector<std::pair<int, int>> cand;
@@ -1463,12 +1475,19 @@ frsg_status fr_sg_autotune(frsg_ctx* ctx, int reps, int* variant_out, int* te_ou
         drop_graphs(ctx);
         frsg_status st = fr_sg_rk_step(ctx, dt, 1, 1);    // capture + warm-up
         if (st != FRSG_OK) return st;
-        CK(cudaEventRecord(ev0, ctx->stream));
-        st = fr_sg_rk_step(ctx, dt, reps, 1);
-        if (st != FRSG_OK) return st;
-        CK(cudaEventRecord(ev1, ctx->stream));
-        CK(cudaEventSynchronize(ev1));
-        CK(cudaEventElapsedTime(ms, ev0, ev1));
+        float total = 0.f;
+        for (int r = 0; r < reps; ++r) {
+            CK(cudaMemsetAsync(flush, r & 0xff, flush_bytes, ctx->stream));
+            CK(cudaEventRecord(ev0, ctx->stream));
+            st = fr_sg_rk_step(ctx, dt, 1, 1);
+            if (st != FRSG_OK) return st;
+            CK(cudaEventRecord(ev1, ctx->stream));
+            CK(cudaEventSynchronize(ev1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ev0, ev1));
+            total += t;
+        }
+        *ms = total;
         CK(cudaMemcpyAsync(ctx->d_u, saved, nbytes, cudaMemcpyDeviceToDevice, ctx->stream));
         return FRSG_OK;
     };
