@@ -353,7 +353,9 @@ frsg_status fr_sg_set_variant(frsg_ctx* ctx, int variant);
  * cached step graphs.  Synchronises. */
 frsg_status fr_sg_test_fused_wait(frsg_ctx* ctx, long long wait_cycles, int hold_tile);
 
-/* Autotuner: times graph-replayed SSP-RK3 steps (reps per candidate, default 20; CUDA
+/* Autotuner: times graph-replayed SSP-RK3 steps from the context's current state with its last
+ * step size (1e-3 if none was set), so it should run on a representative admissible state, e.g.
+ * after the initial state and one step (reps per candidate, default 20; CUDA
  * events on the context's stream around each step, the L2 cache overwritten before it, so that
  * every candidate reads its state from HBM) for every layout (1D) and tile that fits, re-times
  * the three fastest in five interleaved rounds, keeps the best and caches the choice per
