@@ -264,7 +264,8 @@ def job_windows(spec, cfl, nsteps):
 
 
 def job_run_1d(spec, cfl, nsteps, integrator="ssp3", limit_first=False):
-    """The oracle's state after nsteps steps of a 1D workload from the projected initial state.
+    """The oracle's state after nsteps steps of a 1D workload from the projected initial state,
+    with the wall seconds of the steps (the oracle's own timing of this workload).
     cfl: a number (dt from the oracle's CFL condition on the initial state) or None (dt from
     the workload's fixed wave speed lam0)."""
     from oracle import capture, integrate
@@ -278,9 +279,16 @@ def job_run_1d(spec, cfl, nsteps, integrator="ssp3", limit_first=False):
         v = capture.limit(prob, tabs, u) if limit_first else u
         dt = integrate.cfl_dt(prob, tabs, v, cfl)
     step = integrate.rk4_step if integrator == "rk4" else integrate.ssp_rk3_step
+    t0 = time.perf_counter()
     for _ in range(nsteps):
         u = step(prob, tabs, u, dt)
-    return dt, u
+    return dt, u, time.perf_counter() - t0
+
+
+def oracle_rate(dof, stages, nsteps, seconds, sample):
+    """The oracle's throughput in the metric's unit from one worker's timed steps."""
+    return {"value": dof * stages * nsteps / seconds if seconds > 0 else None, "unit": UNIT, "cores": 1,
+            "kind": "oracle", "sample": sample}
 
 
 def job_patch_steps(nsteps, seconds=0.0):
@@ -841,7 +849,7 @@ def run_ours(args):
         xsteps = max(3, min(args.steps, 50))
         for name, (spec, n, rule) in OTHER_1D.items():
             wl = _spec_workload(spec)
-            dt_ref, u_ref = futs[name].result()
+            dt_ref, u_ref, osec = futs[name].result()
             integ = "rk4" if name.endswith("_rk4") else "ssp3"
             fixed = dt_ref if rule == "fixed" else None
             extra[name] = {p: measure_1d(torch, frsg, wl, p, xsteps, 3, stream, flush, peaks, (dt_ref, u_ref, n),
@@ -851,9 +859,19 @@ def run_ours(args):
             if name.startswith("sod") or name.endswith("_lasso"):
                 for p in ("fp32",):
                     extra[name][p]["err_bound"] = ERR_BOUND_SHOCK_FP32
-        brefs = [futs[f"batch{i}"].result() + (10,) for i in range(batch_n)]
+            E, Np, M, S = workload_sizes(wl)
+            extra[name]["oracle"] = oracle_rate(
+                E * Np * M * S, 4 if integ == "rk4" else 3, n, osec,
+                f"numpy FP64 oracle, {n} steps of the whole workload in one process, while up to 12 "
+                f"oracle processes ran side by side on the host")
+        bres = [futs[f"batch{i}"].result() for i in range(batch_n)]
+        brefs = [(r[0], r[1], 10) for r in bres]
         batch = {p: measure_batch(torch, frsg, p, max(3, min(args.steps, 20)), 3, stream, flush, brefs)
                  for p in ("fp64", "fp32")}
+        bdof = sum(math.prod(workload_sizes(workloads.burgers_batch_member(i))) for i in range(batch_n))
+        batch["oracle"] = oracle_rate(bdof, 3, 10, sum(r[2] for r in bres),
+                                      f"numpy FP64 oracle, members 0..{batch_n - 1}, 10 steps each, one "
+                                      f"process per member")
         adj = measure_adjoint(torch, frsg, stream)
         adj_batch = measure_batch_adjoint(torch, frsg, stream)
     torch.cuda.synchronize()
